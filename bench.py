@@ -1,0 +1,348 @@
+"""Benchmark of the radix-tree-forest sampling path on one GB300.
+
+One step = the whole path on the n = 2^24 workload:
+  build (validation + scale, exact integer CDF, keys, forest, guide) of
+  2^24 lognormal(0, 2) weights with 2^20 guide cells,
+  sampling of 2^28 i.i.d. uniform uint32 samples and of the 2^28 sorted
+  radical-inverse samples (index + float32 in-bin position),
+  backward of the i.i.d. positions (dL/dx ~ N(0, 1)) to dL/dw.
+value = samples mapped per second over the whole step (2 x 2^28 samples per
+step; the build and the backward are inside the timed region).  Every input is
+larger than L2, so no L2 flush is needed between steps.
+
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload instead (the paper has no reference implementation to run).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "samples/s & build elem/s at n=2^24 (bit-exact); batched vs looped; % HBM peak"
+N_W = 1 << 24
+M_BITS = 20
+N_S = 1 << 28
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs():
+    from paper_1901_05423_gb300 import workloads as W
+    w = W.lognormal_weights(N_W, seed=0, sigma=2.0)
+    u_iid = W.iid_u32(N_S, seed=1)
+    u_sorted = W.sorted_radical_inverse_u32(N_S)
+    gx = W.normal_f32(N_S, seed=2)
+    return w, u_iid, u_sorted, gx
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------
+
+def time_oracle(w, u_iid, u_sorted, gx, sample_count=1 << 21):
+    from oracle import oracle as orc
+    t0 = time.perf_counter()
+    st = orc.build(w, 1 << M_BITS)
+    t_build = time.perf_counter() - t0
+    ui = u_iid[:sample_count]
+    us = u_sorted[::max(1, N_S // sample_count)][:sample_count]
+    t0 = time.perf_counter()
+    idx_i, _ = orc.sample(st.C, ui)
+    orc.sample(st.C, us)
+    t_sample = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.grad(w, ui, idx_i, gx[:sample_count])
+    t_grad = time.perf_counter() - t0
+    scale = N_S / sample_count
+    step = t_build + t_sample * scale + t_grad * scale
+    return {
+        "step_s": step,
+        "value": 2 * N_S / step,
+        "build_elem_per_s": N_W / t_build,
+        "sample": (f"oracle build of n=2^24 (timed once), index+position on {sample_count} "
+                   f"i.i.d. + {sample_count} sorted samples and the gradient on {sample_count} "
+                   f"samples, scaled linearly to 2^28 samples per set"),
+    }
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, u_iid, u_sorted, gx = make_inputs()
+    times = []
+    res = None
+    for it in range(args.warmup + args.steps):
+        res = time_oracle(w, u_iid, u_sorted, gx, sample_count=1 << 19)
+        if it >= args.warmup:
+            times.append(res["step_s"])
+    step = float(np.mean(times))
+    value = 2 * N_S / step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "n=2^24 lognormal(0,2) weights, 2^20 guide cells, 2^28 iid + "
+                               "2^28 sorted radical-inverse samples, backward on the iid set",
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": res["sample"].replace(str(1 << 21), str(1 << 19))},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def gpu_arm(args):
+    import torch
+    from paper_1901_05423_gb300 import api
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w, u_iid, u_sorted, gx = make_inputs()
+    wd = torch.from_numpy(w).to(dev)
+    ui = api.u32_tensor(u_iid, dev)
+    us = api.u32_tensor(u_sorted, dev)
+    gd = torch.from_numpy(gx).to(dev)
+    idx_i = torch.empty(N_S, dtype=torch.int32, device=dev)
+    pos_i = torch.empty(N_S, dtype=torch.float32, device=dev)
+    idx_s = torch.empty_like(idx_i)
+    pos_s = torch.empty_like(pos_i)
+    grad_w = torch.empty_like(wd)
+    f = api.rtf_build(wd, M_BITS)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    names = ["build", "sample_iid", "sample_sorted", "backward"]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        api.rtf_build(wd, M_BITS, forest=f)
+        if ev is not None:
+            ev[1].record(stream)
+        api.rtf_sample(f, ui, idx_out=idx_i, pos_out=pos_i)
+        if ev is not None:
+            ev[2].record(stream)
+        api.rtf_sample(f, us, idx_out=idx_s, pos_out=pos_s)
+        if ev is not None:
+            ev[3].record(stream)
+        api.rtf_sample_backward(f, wd, ui, None, idx_i, pos_i, gd, grad_w=grad_w)
+        if ev is not None:
+            ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    f.check_status()
+
+    part = {k: [] for k in names}
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = start.elapsed_time(end)
+    for k in range(args.steps):
+        for i, nm in enumerate(names):
+            part[nm].append(evs[k][i].elapsed_time(evs[k][i + 1]))
+    f.check_status()
+    ms = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end-to-end through the API with host buffers (pinned), copies inside
+    h_w = torch.from_numpy(w).pin_memory()
+    h_ui = torch.from_numpy(u_iid.view(np.int32)).pin_memory()
+    h_us = torch.from_numpy(u_sorted.view(np.int32)).pin_memory()
+    h_g = torch.from_numpy(gx).pin_memory()
+    o_idx_i = torch.empty(N_S, dtype=torch.int32).pin_memory()
+    o_pos_i = torch.empty(N_S, dtype=torch.float32).pin_memory()
+    o_idx_s = torch.empty_like(o_idx_i).pin_memory()
+    o_pos_s = torch.empty_like(o_pos_i).pin_memory()
+    o_gw = torch.empty_like(h_w).pin_memory()
+
+    def e2e_step():
+        wd.copy_(h_w, non_blocking=True)
+        ui.copy_(h_ui, non_blocking=True)
+        us.copy_(h_us, non_blocking=True)
+        gd.copy_(h_g, non_blocking=True)
+        step()
+        o_idx_i.copy_(idx_i, non_blocking=True)
+        o_pos_i.copy_(pos_i, non_blocking=True)
+        o_idx_s.copy_(idx_s, non_blocking=True)
+        o_pos_s.copy_(pos_s, non_blocking=True)
+        o_gw.copy_(grad_w, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_step()
+    torch.cuda.synchronize()
+    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    es.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    ee.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = es.elapsed_time(ee) / e2e_steps
+    h2d = w.nbytes + u_iid.nbytes + u_sorted.nbytes + gx.nbytes
+    d2h = 4 * 4 * N_S + w.nbytes
+
+    peak, peak_kind = measured_peaks()
+    avg = {k: float(np.mean(v)) for k, v in part.items()}
+    # algorithmic bytes per launch
+    alg = {
+        "build": 28 * N_W + 4 * (1 << M_BITS),
+        "sample_iid": 12 * N_S,
+        "sample_sorted": 12 * N_S,
+        "backward": 16 * N_S + 24 * N_W,
+    }
+    dom = max(avg, key=avg.get)
+    achieved = alg[dom] / (avg[dom] * 1e-3) / 1e9
+    value = world * 2 * N_S / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": "n=2^24 lognormal(0,2) weights, 2^20 guide cells, 2^28 iid + "
+                               "2^28 sorted radical-inverse samples, backward on the iid set",
+                   "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
+        "breakdown_ms": avg,
+        "build_elem_per_s": N_W / (avg["build"] * 1e-3),
+        "sample_iid_per_s": N_S / (avg["sample_iid"] * 1e-3),
+        "sample_sorted_per_s": N_S / (avg["sample_sorted"] * 1e-3),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind},
+        "fractions_of_hbm": {k: alg[k] / (avg[k] * 1e-3) / 1e9 / peak for k in avg},
+        "e2e": {"value": world * 2 * N_S / (e2e_ms * 1e-3), "unit": "samples/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 10 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = time_oracle(w, u_iid, u_sorted, gx)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "samples/s", "cores": 1,
+                                "kind": "oracle", "sample": cb["sample"],
+                                "build_elem_per_s": cb["build_elem_per_s"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rtf", choices=["rtf", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * rtf.h - C interface of the GB300 radix-tree-forest sampler.
+ *
+ * The library builds, on one GPU, the auxiliary structure of Binder & Keller,
+ * "Massively Parallel Construction of Radix Tree Forests for the Efficient
+ * Sampling of Discrete or Piecewise Constant Probability Distributions"
+ * (arXiv:1901.05423), and maps uniform samples through it:
+ *
+ *   - the prefix-sum CDF of the weights (Sec. 1: P_0 = 0, P_k = sum p_i),
+ *     made exact on 64-bit integers;
+ *   - a guide table of 2^m equal cells over [0, 1) (the Cutpoint method,
+ *     Sec. 2.5) whose entries use the two's complement encoding of Sec. 3.2;
+ *   - one radix tree per cell, all built at once bottom-up (Algorithm 1,
+ *     Sec. 3.2);
+ *   - the monotone mapping of a sample through its guide cell and a tree
+ *     descent (Algorithm 2) to a bin index and an in-bin position (Sec. 5);
+ *   - the gradient of the in-bin position with respect to the weights (not in
+ *     the paper).
+ *
+ * Conventions shared by every call:
+ *   - Every pointer whose name does not say "host" is DEVICE memory of the
+ *     current CUDA device.  The caller allocates and owns all of it; the
+ *     library never allocates, frees or synchronises, so every call may be
+ *     captured into a CUDA graph.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work
+ *     is ordered on it.
+ *   - The return value reports argument errors and launch errors only.  Errors
+ *     that depend on the data (a negative, NaN or infinite weight, a
+ *     distribution whose weights are all zero, a bounded wait that ran out)
+ *     are OR-ed into the device word `rtf_forest.status` as RTF_STATUS_* bits,
+ *     which the caller reads after synchronising.  Outputs are undefined
+ *     unless the call returned RTF_OK and the status word is 0.
+ *
+ * Exact arithmetic (the reading this library takes of P_k and xi):
+ *   - weights are float32, w_i >= 0, finite; a zero weight is an empty,
+ *     unreachable bin;
+ *   - all weights of one distribution (or of one shared-scale group) are
+ *     turned into integers q_i = floor(w_i 2^S) with S = B - 1 - e_max,
+ *     B = 62 - ceil(log2 n_group), e_max = max floor(log2 w_i); the CDF is the
+ *     exact integer prefix sum C_0 = 0, C_{k+1} = C_k + q_k, T = C_n < 2^62;
+ *   - a 32-bit sample u stands for xi = u / 2^32 and selects the bin i with
+ *     C_i <= t < C_{i+1}, t = floor(u T / 2^32);
+ *   - its in-bin position is (u T - C_i 2^32) / (q_i 2^32), returned in
+ *     float32 (within a few ulp of the exact value, clamped below 1).
+ */
+#ifndef RTF_H_
+#define RTF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Synchronous return codes. */
+typedef enum rtf_status {
+  RTF_OK = 0,
+  RTF_EINVAL = 1,     /* a null pointer, a size out of range, a misaligned pointer */
+  RTF_EWORKSPACE = 2, /* the workspace is smaller than the *_workspace_size call says */
+  RTF_ECUDA = 3       /* a CUDA launch or runtime call failed */
+} rtf_status;
+
+/* Bits of the device status word (rtf_forest.status). */
+#define RTF_STATUS_BAD_WEIGHT 0x1u /* a weight is negative, NaN or infinite */
+#define RTF_STATUS_ZERO_TOTAL 0x2u /* a distribution has no positive weight */
+#define RTF_STATUS_TIMEOUT 0x4u    /* a bounded wait inside a kernel ran out */
+#define RTF_STATUS_BAD_PLAN 0x8u   /* batched plan: n_d < 1, m_d outside [0, 31] */
+
+/* rtf_forest.flags */
+#define RTF_FOREST_MARGINAL 0x1 /* the last distribution is the marginal over the
+                                   others (2-D map, Sec. 5); see rtf_build_batched */
+
+/* rtf_sample / rtf_sample_backward modes */
+#define RTF_SAMPLE_1D 0 /* one sample u per output; dist_id selects the distribution */
+#define RTF_SAMPLE_2D 1 /* (u1, u2) pairs; row from the marginal, column from the row */
+
+/*
+ * One node record, 16 bytes, in device memory.  Record j of a distribution
+ * holds the CDF value C_j and the two children of node j.
+ *
+ * Node enumeration (Sec. 3.1): node j splits between leaves j-1 and j, so the
+ * descent compares against the CDF value with the node's own index (Sec. 3.2,
+ * Algorithm 2), which is why the CDF is interleaved with the children (the
+ * layout the paper suggests at the end of Sec. 3.2).  A child reference
+ * c >= 0 is a node index, c < 0 is the leaf (bin) ~c.  The node of the first
+ * leaf j0 of every cell is that cell's root: child[1] is the cell's tree and
+ * child[0] the interval overlapping the cell from the left, ~(j0 - 1), or ~0
+ * for j0 = 0 (caption of Fig. 11).  Indices are local to the distribution.
+ */
+typedef struct rtf_node {
+  uint64_t cdf;      /* C_j (exact integer CDF, local to the distribution) */
+  int32_t child[2];  /* child[0] taken when t < C_j, child[1] otherwise */
+} rtf_node;
+
+/*
+ * Per-distribution parameters, 64 bytes, in device memory.  The build writes
+ * every field; the caller only allocates the array.
+ */
+typedef struct rtf_dist {
+  int64_t elem_off;  /* first weight / node record of the distribution */
+  int64_t n;         /* number of weights (bins) */
+  int64_t guide_off; /* first guide cell */
+  uint64_t total;    /* T = C_n */
+  uint64_t recip;    /* floor((2^128 - 1) / (T << shift)) - 2^64 (key arithmetic) */
+  int32_t m;         /* guide bits: the distribution has 2^m cells */
+  int32_t scale;     /* S of the fixed-point weights (0 for the marginal) */
+  int32_t shift;     /* number of leading zero bits of T */
+  int32_t flags;     /* internal */
+  int64_t reserved;
+} rtf_dist;
+
+/*
+ * A forest: the caller fills this host struct with sizes and device pointers
+ * (all caller-allocated) before a build, and passes it to the sampler.
+ */
+typedef struct rtf_forest {
+  int32_t num_dists; /* D >= 1 */
+  int32_t flags;     /* RTF_FOREST_* */
+  int64_t num_elems; /* N = sum of n_d: length of `nodes` */
+  int64_t num_cells; /* G = sum of 2^m_d: length of `guide` */
+  int32_t max_m;     /* largest m_d (host copy; chooses the shared-memory guide path) */
+  int32_t reserved;
+  rtf_node *nodes;   /* device [N], 16-byte aligned */
+  int32_t *guide;    /* device [G] */
+  rtf_dist *dists;   /* device [D] */
+  uint32_t *status;  /* device [1]: RTF_STATUS_* bits, set to 0 by each build */
+} rtf_forest;
+
+/* Library version string. */
+const char *rtf_version(void);
+
+/* Human-readable name of a return code. */
+const char *rtf_status_string(rtf_status s);
+
+/*
+ * Bytes of workspace rtf_build / rtf_build_batched need for N elements, D
+ * distributions and G guide cells.
+ *
+ * The workspace carries state between builds (an epoch counter that replaces
+ * a per-build reset of the Algorithm 1 synchronisation array), so it must be
+ * zero-filled once before its first use (for example with cudaMemset), and
+ * must not serve two builds that run at the same time.
+ */
+size_t rtf_build_workspace_size(int64_t num_elems, int32_t num_dists,
+                                int64_t num_cells);
+
+/*
+ * Build the structure of one distribution.
+ *
+ *   w        device float32[n], 16-byte aligned: the weights (Sec. 1: p up to
+ *            normalisation), w_i >= 0, finite, at least one positive.
+ *   n        1 <= n <= 2^31 - 2^16.
+ *   m        guide bits, 0 <= m <= 30: 2^m cells (Sec. 2.5, Sec. 3.2).
+ *   f        f->num_dists == 1, f->num_elems == n, f->num_cells == 2^m,
+ *            f->max_m == m; nodes[n], guide[2^m], dists[1], status[1] allocated.
+ *   ws       device workspace of at least rtf_build_workspace_size(n, 1, 2^m)
+ *            bytes, 256-byte aligned, zero-filled before its first use.
+ *
+ * Steps (all on `stream`, no host synchronisation): validation and scale
+ * (max exponent), exact integer CDF by a decoupled-lookback scan, keys
+ * K_j = ceil(C_j 2^32 / T), Algorithm 1 over all cells at once, guide table.
+ * Results: f->nodes, f->guide, f->dists[0] and *f->status.
+ */
+rtf_status rtf_build(const float *w, int64_t n, int32_t m, rtf_forest *f,
+                     void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Build many distributions at once (Sec. 5: several tables and trees are
+ * built together by treating the index boundary of every distribution like a
+ * cell boundary in Algorithm 1).
+ *
+ *   w              device float32[offsets[D_w]], 16-byte aligned, where
+ *                  D_w = D (independent distributions) or D - 1 (marginal mode).
+ *   offsets        device int64[D + 1]: distribution d owns elements
+ *                  [offsets[d], offsets[d+1]); offsets[0] = 0, n_d >= 1.
+ *   m              device int32[D]: guide bits per distribution, 0..30.
+ *   guide_offsets  device int64[D + 1]: guide_offsets[0] = 0,
+ *                  guide_offsets[d+1] = guide_offsets[d] + 2^m[d].
+ *   f              f->num_dists = D, f->num_elems = offsets[D],
+ *                  f->num_cells = guide_offsets[D], f->max_m = max m[d].
+ *
+ * Without RTF_FOREST_MARGINAL each distribution has its own scale
+ * (n_group = n_d).  With RTF_FOREST_MARGINAL in f->flags (a 2-D piecewise
+ * constant map, Sec. 5): distributions 0..D-2 are the rows (conditionals) and
+ * share one scale (n_group = offsets[D-1]); distribution D-1 has n = D - 1
+ * and its integer weights are the exact row totals T_0 .. T_{D-2} (the
+ * marginal); w then holds only the offsets[D-1] row weights.
+ */
+rtf_status rtf_build_batched(const float *w, const int64_t *offsets,
+                             const int32_t *m, const int64_t *guide_offsets,
+                             rtf_forest *f, void *ws, size_t ws_bytes,
+                             void *stream);
+
+/*
+ * Map samples to bins (Algorithm 2, Sec. 3.2) and in-bin positions (Sec. 5).
+ *
+ * RTF_SAMPLE_1D: u is uint32[count]; dist_id is NULL (all samples use
+ *   distribution 0) or int32[count] (distribution of each sample, 0..D-1).
+ *   idx_out int32[count] receives the bin (local to its distribution),
+ *   pos_out float32[count] the position in [0, 1).
+ * RTF_SAMPLE_2D: f must carry RTF_FOREST_MARGINAL; u is uint32[2 count] as
+ *   (u1, u2) pairs, dist_id must be NULL; u1 selects the row through the
+ *   marginal, u2 the column through that row (Sec. 5).  idx_out int32[2 count]
+ *   receives (row, column), pos_out float32[2 count] (row position, column
+ *   position).
+ * u, idx_out and pos_out must be 16-byte aligned; count >= 0.
+ */
+rtf_status rtf_sample(const rtf_forest *f, const uint32_t *u,
+                      const int32_t *dist_id, int64_t count, int32_t mode,
+                      int32_t *idx_out, float *pos_out, void *stream);
+
+/* Bytes of workspace rtf_sample_backward needs. */
+size_t rtf_backward_workspace_size(int64_t num_elems, int32_t num_dists);
+
+/*
+ * Gradient of the in-bin positions with respect to the weights (not in the
+ * paper).  With the bin i of each sample held fixed, the position is the
+ * real-valued x = (xi W - C_i) / w_i, W = sum_k w_k, C_i = sum_{k<i} w_k, so
+ *
+ *   dL/dw_k = sum_i Xi_i / w_i - sum_{i>k} A_i / w_i - X_k / w_k
+ *
+ * with, over the samples s that fell into bin i, A_i = sum g_s,
+ * X_i = sum g_s x_s, Xi_i = sum g_s xi_s (g = dL/dx).  The library scatters
+ * A_i / w_i and X_i / w_i per bin, sums Xi_i / w_i per distribution and runs a
+ * reverse suffix scan per distribution.  In RTF_SAMPLE_2D mode the column
+ * positions differentiate through their row and the row positions through the
+ * marginal, whose weights are the row sums, so a row's marginal term is added
+ * to every weight of that row.
+ *
+ *   w          the weights the forest was built from (same layout as the build).
+ *   u, dist_id, idx, pos   the inputs and outputs of the forward rtf_sample.
+ *   grad_pos   float32[count] (1-D) or [2 count] (2-D): dL/dpos.
+ *   grad_w     float32[offsets[D_w]] output.
+ *   ws         at least rtf_backward_workspace_size(N, D) bytes, 256-byte
+ *              aligned; no state is kept between calls.
+ */
+rtf_status rtf_sample_backward(const rtf_forest *f, const float *w,
+                               const uint32_t *u, const int32_t *dist_id,
+                               const int32_t *idx, const float *pos,
+                               const float *grad_pos, int64_t count,
+                               int32_t mode, float *grad_w, void *ws,
+                               size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+} /* extern "C" */
+#endif
+
+#endif /* RTF_H_ */

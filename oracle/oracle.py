@@ -78,6 +78,7 @@ def _load():
             "orc_build": (ctypes.c_int, [P, i64, i64, i64, P, P, P, P]),
             "orc_build_int": (ctypes.c_int, [P, i64, i64, P, P, P]),
             "orc_grad": (None, [P, i64, P, P, P, i64, P]),
+            "orc_grad64": (None, [P, i64, P, P, P, i64, P]),
             "orc_relaxed_position": (None, [P, i64, P, P, i64, P]),
         }
         for name, (res, args) in sig.items():
@@ -293,6 +294,37 @@ def grad(w, u, idx, gx) -> np.ndarray:
     gx = np.ascontiguousarray(gx, dtype=np.float32)
     out = np.zeros(w.size, np.float64)
     _load().orc_grad(_p(w), w.size, _p(u), _p(idx), _p(gx), u.size, _p(out))
+    return out
+
+
+def grad64(w64, u, idx, gx) -> np.ndarray:
+    """``orc_grad64``: the same gradient for fp64 weights."""
+    w64 = np.ascontiguousarray(w64, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    gx = np.ascontiguousarray(gx, dtype=np.float32)
+    out = np.zeros(w64.size, np.float64)
+    _load().orc_grad64(_p(w64), w64.size, _p(u), _p(idx), _p(gx), u.size, _p(out))
+    return out
+
+
+def grad_env(lum, u1, u2, r, c, g_row, g_col) -> np.ndarray:
+    """Gradient of the 2-D positions (Sec. 5, component-wise) with respect to
+    the map: each row's column positions differentiate through that row's
+    weights; the row positions through the marginal, whose relaxed weights are
+    the real row sums R_r, so dL/dR_r is added to every weight of row r."""
+    lum = np.ascontiguousarray(lum, dtype=np.float32)
+    H, Wd = lum.shape
+    out = np.zeros((H, Wd), np.float64)
+    R = lum.astype(np.float64).sum(axis=1)
+    gR = grad64(R, u1, r, g_row)
+    out += gR[:, None]
+    order = np.argsort(r, kind="stable")
+    rs = r[order]
+    bounds = np.searchsorted(rs, np.arange(H + 1))
+    for row in np.unique(rs):
+        sel = order[bounds[row]:bounds[row + 1]]
+        out[row] += grad(lum[row], u2[sel], c[sel], g_col[sel])
     return out
 
 

@@ -338,6 +338,32 @@ void orc_grad(const float* w, int64_t n, const uint32_t* u,
   }
 }
 
+// Same gradient for fp64 weights (the marginal of a 2-D map, whose relaxed
+// weights are the real row sums R_r = sum_c w(r, c)).
+void orc_grad64(const double* w, int64_t n, const uint32_t* u, const int32_t* idx,
+                const float* gx, int64_t ns, double* grad) {
+  std::vector<double> Creal(n + 1);
+  Creal[0] = 0.0;
+  for (int64_t k = 0; k < n; ++k) Creal[k + 1] = Creal[k] + w[k];
+  double W = Creal[n];
+  double dW = 0.0;
+  std::vector<double> dC(n, 0.0), dwd(n, 0.0);
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t i = idx[s];
+    double xi = std::ldexp((double)u[s], -32);
+    double x = (xi * W - Creal[i]) / w[i];
+    double g = (double)gx[s];
+    dW += g * xi / w[i];
+    dC[i] += -g / w[i];
+    dwd[i] += -g * x / w[i];
+  }
+  double suffix = 0.0;
+  for (int64_t k = n - 1; k >= 0; --k) {
+    grad[k] = dW + suffix + dwd[k];
+    suffix += dC[k];
+  }
+}
+
 // The relaxed fp64 forward of the same function (used by the finite
 // difference check of orc_grad): x for fixed bins.
 void orc_relaxed_position(const double* w, int64_t n, const uint32_t* u,

@@ -1,0 +1,923 @@
+// Build of the radix tree forest (Binder & Keller, Sec. 3.2, Algorithm 1) and
+// of the guide table (Cutpoint method, Sec. 2.5, with the encoding of
+// Sec. 3.2) for one or many distributions at once (Sec. 5).
+//
+// Kernels, in launch order:
+//   init_dists_kernel   per-distribution parameters from the plan; epoch + 1
+//   scale_kernel        validation and max exponent (one read of w)
+//   scan_kernel         exact integer prefix sums of the tiles by a decoupled
+//                       lookback (second read of w); totals T and key
+//                       reciprocals; in marginal mode the last tile to finish
+//                       also scans the row totals
+//   forest_kernel       C_j, keys K_j, distances, Algorithm 1 inside each tile
+//                       in shared memory, the cross-tile merges through an
+//                       epoch-tagged global otherBounds; node records, roots,
+//                       guide entries of non-empty cells (third read of w)
+//   guide_kernel        guide entries of cells that no key falls into: the
+//                       interval of the last key before them (carry-forward
+//                       scan with a decoupled lookback)
+#include <cstdint>
+
+#include "rtf_device.cuh"
+
+namespace rtf {
+
+// ---------------------------------------------------------------------------
+// init
+// ---------------------------------------------------------------------------
+__global__ void init_dists_kernel(rtf_dist* dists, int D, const int64_t* offsets,
+                                  const int32_t* m_arr, const int64_t* goff, int marginal,
+                                  int64_t n_single, int m_single, uint32_t* epoch,
+                                  uint32_t* status) {
+  int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d == 0) *epoch = *epoch + 1u;
+  if (d >= D) return;
+  rtf_dist P;
+  if (offsets == nullptr) {
+    P.elem_off = 0;
+    P.n = n_single;
+    P.guide_off = 0;
+    P.m = m_single;
+  } else {
+    P.elem_off = offsets[d];
+    P.n = offsets[d + 1] - offsets[d];
+    P.guide_off = goff[d];
+    P.m = m_arr[d];
+    bool bad = P.n < 1 || P.m < 0 || P.m > 30 ||
+               goff[d + 1] - goff[d] != (int64_t(1) << (P.m < 0 || P.m > 30 ? 0 : P.m));
+    if (marginal && d == D - 1 && P.n != D - 1) bad = true;
+    if (bad) {
+      raise_status(status, RTF_STATUS_BAD_PLAN);
+      P.m = 0;
+      if (P.n < 1) P.n = 1;
+    }
+  }
+  P.total = 0;
+  P.recip = 0;
+  P.scale = 0;
+  P.shift = 0;
+  P.flags = 0;
+  if (marginal) P.flags = (d == D - 1) ? kDistMarginal : kDistShared;
+  P.reserved = 0;
+  dists[d] = P;
+}
+
+// ---------------------------------------------------------------------------
+// scale: max float bits per distribution (or per shared group) + validation
+// ---------------------------------------------------------------------------
+constexpr int kScaleThreads = 256;
+constexpr int kScalePer = 16;
+constexpr int kScaleTile = kScaleThreads * kScalePer;
+
+template <bool SEG>
+__global__ void __launch_bounds__(kScaleThreads)
+    scale_kernel(const float* __restrict__ w, int64_t Nw, const rtf_dist* __restrict__ dists,
+                 int Dw, uint32_t* dmax, uint32_t* status) {
+  __shared__ uint32_t smax[SEG ? kScaleTile + 1 : 1];
+  __shared__ int dfirst_s;
+  __shared__ uint32_t red[kScaleThreads / 32];
+  const int64_t c0 = (int64_t)blockIdx.x * kScaleTile;
+  const int64_t c1 = min(c0 + (int64_t)kScaleTile, Nw);
+  const int64_t e0 = c0 + (int64_t)threadIdx.x * kScalePer;
+  uint32_t bad = 0;
+  if (!SEG) {
+    uint32_t mx = 0;
+    if (e0 + kScalePer <= c1) {
+      const float4* p = reinterpret_cast<const float4*>(w + e0);
+#pragma unroll
+      for (int k = 0; k < kScalePer / 4; ++k) {
+        float4 v = __ldcs(p + k);
+        uint32_t b0 = weight_bits(v.x), b1 = weight_bits(v.y), b2 = weight_bits(v.z),
+                 b3 = weight_bits(v.w);
+        bad |= weight_bad(b0) | weight_bad(b1) | weight_bad(b2) | weight_bad(b3);
+        mx = max(mx, max(max(b0, b1), max(b2, b3)));
+      }
+    } else {
+      for (int64_t e = e0; e < c1; ++e) {
+        uint32_t b = weight_bits(w[e]);
+        bad |= weight_bad(b);
+        mx = max(mx, b);
+      }
+    }
+    // invalid weights must not win the max
+    if (bad) mx = 0;
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t v = threadIdx.x < kScaleThreads / 32 ? red[threadIdx.x] : 0u;
+      v = __reduce_max_sync(0xffffffffu, v);
+      if (threadIdx.x == 0 && v) atomicMax(dmax, v);
+    }
+    if (bad) raise_status(status, RTF_STATUS_BAD_WEIGHT);
+    return;
+  }
+  // segmented: the block's elements span distributions dfirst..dlast
+  if (threadIdx.x == 0) dfirst_s = find_dist(dists, 0, Dw - 1, c0);
+  for (int k = threadIdx.x; k <= kScaleTile; k += kScaleThreads) smax[k] = 0u;
+  __syncthreads();
+  const int dfirst = dfirst_s;
+  if (e0 < c1) {
+    int hi = min(Dw - 1, dfirst + kScaleTile);
+    int d = find_dist(dists, dfirst, hi, e0);
+    int64_t next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
+    uint32_t run = 0;
+    const int64_t e1 = min(e0 + (int64_t)kScalePer, c1);
+    for (int64_t e = e0; e < e1; ++e) {
+      if (e >= next) {
+        if (run) atomicMax(&smax[d - dfirst], run);
+        run = 0;
+        ++d;
+        next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
+      }
+      uint32_t b = weight_bits(w[e]);
+      if (weight_bad(b)) {
+        bad = 1;
+      } else {
+        run = max(run, b);
+      }
+    }
+    if (run) atomicMax(&smax[d - dfirst], run);
+  }
+  if (bad) raise_status(status, RTF_STATUS_BAD_WEIGHT);
+  __syncthreads();
+  const int dlast = (c1 > c0) ? find_dist(dists, dfirst, min(Dw - 1, dfirst + kScaleTile), c1 - 1)
+                              : dfirst;
+  for (int d = dfirst + (int)threadIdx.x; d <= dlast; d += kScaleThreads) {
+    uint32_t v = smax[d - dfirst];
+    if (v) atomicMax(&dmax[d], v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// scan: tile sums of q with a decoupled lookback
+// ---------------------------------------------------------------------------
+struct DistScale {
+  int S;
+};
+
+__device__ __forceinline__ int dist_scale(const rtf_dist& P, const uint32_t* dmax, int d,
+                                          int64_t n_shared) {
+  if (P.flags & kDistShared) return scale_from_max(dmax[0], n_shared);
+  return scale_from_max(dmax[d], P.n);
+}
+
+// Finish one distribution once its total is known: T, reciprocal, scale.
+__device__ inline void finish_dist(rtf_dist* dists, int d, uint64_t T, int S, uint32_t* status) {
+  if (T == 0) {
+    raise_status(status, RTF_STATUS_ZERO_TOTAL);
+    T = 1;  // keep the key arithmetic defined; the status word says the result is void
+  }
+  int z = __clzll(T);
+  dists[d].total = T;
+  dists[d].shift = z;
+  dists[d].recip = total_recip(T, z);
+  dists[d].scale = S;
+}
+
+// Lookback by warp 0: exclusive prefix of tile `tile` (the sum of the last
+// pieces of the predecessors back to the first one that published a prefix).
+__device__ inline uint64_t lookback_sum(const uint64_t* st, int64_t tile, uint32_t* status) {
+  const int lane = threadIdx.x & 31;
+  uint64_t E = 0;
+  int64_t look = tile - 1;
+  long long spins = 0;
+  while (look >= 0) {
+    int64_t idx = look - lane;
+    uint64_t s = idx >= 0 ? ld_acquire_u64(st + idx) : kFlagPrefix;
+    uint32_t flag = (uint32_t)(s >> 62);
+    unsigned inval = __ballot_sync(0xffffffffu, flag == 0);
+    unsigned pref = __ballot_sync(0xffffffffu, flag == 2);
+    unsigned upto;
+    if (pref) {
+      int p = __ffs(pref) - 1;
+      unsigned below = (p == 31) ? 0xffffffffu : ((2u << p) - 1u);
+      if (inval & below) {
+        if (++spins > kSpinLimit) {
+          raise_status(status, RTF_STATUS_TIMEOUT);
+          return E;
+        }
+        __nanosleep(32);
+        continue;
+      }
+      upto = below;
+    } else {
+      if (inval) {
+        if (++spins > kSpinLimit) {
+          raise_status(status, RTF_STATUS_TIMEOUT);
+          return E;
+        }
+        __nanosleep(32);
+        continue;
+      }
+      upto = 0xffffffffu;
+    }
+    uint64_t v = ((upto >> lane) & 1u) && idx >= 0 ? (s & kValueMask) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    E += v;
+    if (pref) break;
+    look -= 32;
+  }
+  return E;
+}
+
+constexpr int kScanPer = kTile / kScanThreads;  // 8
+
+template <bool SEG>
+__global__ void __launch_bounds__(kScanThreads)
+    scan_kernel(const float* __restrict__ w, int64_t Nw, rtf_dist* dists, int D, int Dw,
+                int marginal, int64_t n_shared, const uint32_t* dmax, uint64_t* scan_status,
+                uint64_t* tile_prefix, Counters* ctr, uint32_t* status) {
+  __shared__ alignas(16) float wsm[kTile];
+  __shared__ uint64_t bar;
+  __shared__ int ok_s;
+  __shared__ uint32_t tile_s;
+  __shared__ int dfirst_s;
+  __shared__ SegPair wtot[kScanThreads / 32];
+  __shared__ SegPair btot;
+  __shared__ uint64_t E_s;
+  __shared__ int last_s;
+
+  if (threadIdx.x == 0) tile_s = atomicAdd(&ctr->scan_ticket, 1u);
+  __syncthreads();
+  const int64_t tile = tile_s;
+  const int64_t ntiles = num_tiles(Nw);
+  const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, Nw);
+  if (threadIdx.x == 0) dfirst_s = SEG ? find_dist(dists, 0, Dw - 1, t0) : 0;
+  bool staged = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
+  const int dfirst = dfirst_s;
+
+  // per-thread run of kScanPer consecutive weights
+  const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
+  uint64_t incl[kScanPer];
+  int dk[kScanPer];
+  uint32_t headmask = 0;
+  SegPair agg{0ull, 0u};
+  {
+    int d = 0;
+    int64_t next = INT64_MAX;
+    int S = 0;
+    if (e0 < t1) {
+      if (SEG) {
+        d = find_dist(dists, dfirst, min(Dw - 1, dfirst + kTile), e0);
+        next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
+      }
+      rtf_dist P = dists[d];
+      S = dist_scale(P, dmax, d, n_shared);
+    }
+    uint64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      int64_t e = e0 + k;
+      uint64_t q = 0;
+      if (e < t1) {
+        if (SEG && e >= next) {
+          ++d;
+          next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
+          rtf_dist P = dists[d];
+          S = dist_scale(P, dmax, d, n_shared);
+        }
+        bool head = SEG ? (dists[d].elem_off == e) : (e == 0);
+        if (head) {
+          headmask |= 1u << k;
+          run = 0;
+        }
+        uint32_t b = weight_bits(wsm[e - t0]);
+        q = weight_bad(b) ? 0ull : quantize_bits(b, S);
+      }
+      run += q;
+      incl[k] = run;
+      dk[k] = d;
+    }
+    agg.s = run;
+    agg.f = headmask ? 1u : 0u;
+  }
+  SegPair ex = block_seg_exclusive(agg, wtot, &btot);
+
+  // tile head / tail facts
+  const bool head0 = SEG ? (dists[dfirst].elem_off == t0) : (t0 == 0);
+  int dlast = dfirst;
+  if (SEG) dlast = find_dist(dists, dfirst, min(Dw - 1, dfirst + kTile), t1 - 1);
+  const bool last_head_in_tile = SEG ? (dists[dlast].elem_off >= t0) : (t0 == 0);
+  const uint64_t A = btot.s;  // sum of the last piece (since the last head)
+
+  if (threadIdx.x == 0) {
+    uint64_t v = (A & kValueMask) | (last_head_in_tile ? kFlagPrefix : kFlagAgg);
+    if (!staged) v = kFlagPrefix;  // keep successors from waiting on a failed tile
+    st_release_u64(scan_status + tile, v);
+  }
+  uint64_t E = 0;
+  if (!head0 && threadIdx.x < 32) {
+    E = lookback_sum(scan_status, tile, status);
+    if (threadIdx.x == 0) {
+      E_s = E;
+      if (!last_head_in_tile) st_release_u64(scan_status + tile, ((E + A) & kValueMask) | kFlagPrefix);
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (head0) E_s = 0;
+    tile_prefix[tile] = E_s;
+  }
+  __syncthreads();
+  E = E_s;
+
+  // distributions whose last element lies in this tile
+  if (e0 < t1) {
+    // inclusive value of each element = (thread exclusive) + local run, with
+    // the tile prefix for the first piece
+    uint64_t base = ex.f ? ex.s : ex.s + E;
+    bool first_piece = !ex.f && !head0;
+    (void)first_piece;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      int64_t e = e0 + k;
+      if (e >= t1) break;
+      bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
+      uint64_t v = seen_head ? incl[k] : base + incl[k];
+      int d = dk[k];
+      int64_t end = SEG ? (d + 1 < Dw ? dists[d + 1].elem_off : Nw) : Nw;
+      if (e + 1 == end) {
+        rtf_dist P = dists[d];
+        finish_dist(dists, d, v, dist_scale(P, dmax, d, n_shared), status);
+      }
+    }
+  }
+
+  if (!marginal) return;
+  // marginal mode: the last tile to finish scans the row totals
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last_s = (atomicAdd(&ctr->scan_done, 1u) == (uint32_t)(ntiles - 1));
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  const int H = D - 1;
+  const int64_t moff = dists[D - 1].elem_off;  // == Nw
+  uint64_t carry = 0;
+  for (int r0 = 0; r0 < H; r0 += kScanThreads) {
+    int r = r0 + threadIdx.x;
+    uint64_t Tr = r < H ? __ldcg(&dists[r].total) : 0ull;
+    SegPair x{Tr, 0u};
+    SegPair px = block_seg_exclusive(x, wtot, &btot);
+    uint64_t excl = carry + px.s;  // sum of T over rows < r
+    if (r < H) {
+      int64_t e = moff + r;
+      if (e % kTile == 0) tile_prefix[e / kTile] = excl;
+    }
+    carry += btot.s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) finish_dist(dists, D - 1, carry, 0, status);
+}
+
+// ---------------------------------------------------------------------------
+// forest: Algorithm 1 per tile in shared memory, cross-tile merges in global
+// ---------------------------------------------------------------------------
+constexpr int kForestPer = kTile / kForestThreads;  // 4
+constexpr int32_t kUnset = 0x7FFFFFFF;
+
+struct ForestShared {
+  alignas(16) float w[kTile];
+  alignas(16) uint64_t C[kTile + 2];  // C_{t0-1} .. C_{t1}
+  alignas(16) uint64_t K[kTile + 2];  // K_{t0-1} .. K_{t1}
+  alignas(16) int32_t child[kTile][2];
+  int32_t other[kTile];
+  int32_t dist[kTile];
+  uint8_t delta[kTile + 4];  // delta_{t0-1} .. delta_{t1-1}
+  SegPair wtot[kForestThreads / 32];
+  SegPair btot;
+  uint64_t bar;
+  int ok;
+  int dfirst;
+  int dprev;
+  int ndefer;
+  int64_t defer_parent[4];
+  int64_t defer_lo[4];
+  int64_t defer_hi[4];
+  int32_t defer_node[4];
+  int32_t defer_child[4];
+};
+
+struct ForestArgs {
+  const float* w;
+  int64_t N, Nw;
+  const rtf_dist* dists;
+  int D, Dw;
+  int64_t n_shared;
+  rtf_node* nodes;
+  int32_t* guide;
+  int32_t* last;
+  const uint64_t* tile_prefix;
+  const uint32_t* dmax;
+  uint8_t* delta;
+  unsigned long long* other;
+  const uint32_t* epoch;
+  uint32_t* status;
+};
+
+// Key of C_j for distribution P.
+__device__ __forceinline__ uint64_t key_for(const rtf_dist& P, uint64_t C) {
+  return key_of(C, P.total, P.recip, P.shift);
+}
+
+// Root of a finished cell [lo, hi] (global element indices) of distribution P:
+// guide entry and last-leaf entry of the cell.  K_lo / K_hi are the keys.
+__device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist& P, int64_t lo,
+                                            int64_t hi, uint64_t Klo, uint64_t Khi) {
+  uint64_t c = cell_of(Klo, P.m);
+  if (c >= (1ull << P.m)) return;  // unreachable trailing cell of zero-width bins
+  int32_t lo_l = (int32_t)(lo - P.elem_off), hi_l = (int32_t)(hi - P.elem_off);
+  uint64_t start = c << (32 - P.m);
+  a.guide[P.guide_off + (int64_t)c] = (Khi == start) ? ~hi_l : lo_l;
+  a.last[P.guide_off + (int64_t)c] = hi_l;
+}
+
+__device__ __forceinline__ unsigned long long pack_other(uint32_t epoch, int64_t bound) {
+  return ((unsigned long long)epoch << 32) | (unsigned long long)(uint32_t)bound;
+}
+
+// Continue Algorithm 1 through global memory from range [lo, hi] with node
+// `node` (local reference) of distribution P.
+__device__ void climb_global(const ForestArgs& a, const rtf_dist& P, int64_t lo, int64_t hi,
+                             int32_t node, uint32_t epoch) {
+  for (int64_t guard = 0; guard <= a.N; ++guard) {  // each pass grows the range
+    uint32_t dl = lo > 0 ? (uint32_t)__ldcg(a.delta + lo - 1) : kDeltaInf;
+    uint32_t dr = (uint32_t)__ldcg(a.delta + hi);
+    if (dl >= kDeltaInf && dr >= kDeltaInf) {
+      rtf_node* root = a.nodes + lo;
+      int32_t lo_l = (int32_t)(lo - P.elem_off);
+      root->child[0] = ~(lo_l > 0 ? lo_l - 1 : 0);
+      root->child[1] = node;
+      uint64_t Clo = __ldcg(&a.nodes[lo].cdf), Chi = __ldcg(&a.nodes[hi].cdf);
+      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, Chi));
+      return;
+    }
+    int child = dl > dr ? 0 : 1;
+    int64_t parent = child ? lo : hi + 1;
+    a.nodes[parent].child[child] = node;
+    __threadfence();
+    unsigned long long v =
+        atomicExch(a.other + parent, pack_other(epoch, child ? hi : lo));
+    if ((uint32_t)(v >> 32) != epoch) return;  // first of the two children
+    __threadfence();
+    int64_t ob = (int64_t)(uint32_t)v;
+    if (child)
+      lo = ob;
+    else
+      hi = ob;
+    node = (int32_t)(parent - P.elem_off);
+  }
+  raise_status(a.status, RTF_STATUS_TIMEOUT);
+}
+
+template <bool SEG>
+__global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ForestShared& s = *reinterpret_cast<ForestShared*>(smem_raw);
+  const int64_t tile = blockIdx.x;
+  const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
+  const int tid = threadIdx.x;
+  const uint32_t epoch = *a.epoch;
+
+  if (tid == 0) {
+    int df = SEG ? find_dist(a.dists, 0, a.D - 1, t0) : 0;
+    s.dfirst = df;
+    s.dprev = (t0 > 0 && SEG) ? (a.dists[df].elem_off == t0 ? df - 1 : df) : df;
+    s.ndefer = 0;
+  }
+  bool staged = true;
+  if (t0 < a.Nw) staged = stage_weights(s.w, a.w, t0, min(t1, a.Nw), &s.bar, &s.ok, a.status);
+  else __syncthreads();
+  (void)staged;
+  const int dfirst = s.dfirst;
+
+  // ---- q, C, keys of the thread's leaves --------------------------------
+  const int64_t e0 = t0 + (int64_t)tid * kForestPer;
+  uint64_t q[kForestPer], incl[kForestPer];
+  uint32_t headmask = 0;
+  int dcur = dfirst;
+  {
+    int64_t next = INT64_MAX;
+    int S = 0;
+    rtf_dist P;
+    if (e0 < t1) {
+      if (SEG) {
+        dcur = find_dist(a.dists, dfirst, min(a.D - 1, dfirst + kTile), e0);
+        next = dcur + 1 < a.D ? a.dists[dcur + 1].elem_off : INT64_MAX;
+      }
+      P = a.dists[dcur];
+      S = (P.flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
+    }
+    uint64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kForestPer; ++k) {
+      int64_t e = e0 + k;
+      uint64_t qq = 0;
+      if (e < t1) {
+        if (SEG && e >= next) {
+          ++dcur;
+          next = dcur + 1 < a.D ? a.dists[dcur + 1].elem_off : INT64_MAX;
+          P = a.dists[dcur];
+          S = (P.flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
+        }
+        if (P.elem_off == e) {
+          headmask |= 1u << k;
+          run = 0;
+        }
+        if (P.flags & kDistMarginal) {
+          qq = __ldcg(&a.dists[e - P.elem_off].total);
+        } else {
+          uint32_t b = weight_bits(s.w[e - t0]);
+          qq = weight_bad(b) ? 0ull : quantize_bits(b, S);
+        }
+        s.dist[e - t0] = dcur;
+      }
+      q[k] = qq;
+      run += qq;
+      incl[k] = run;
+    }
+    SegPair agg{run, headmask ? 1u : 0u};
+    SegPair ex = block_seg_exclusive(agg, s.wtot, &s.btot);
+    const bool head0 = a.dists[dfirst].elem_off == t0;
+    const uint64_t E = head0 ? 0ull : a.tile_prefix[tile];
+    uint64_t base = ex.f ? ex.s : ex.s + E;
+#pragma unroll
+    for (int k = 0; k < kForestPer; ++k) {
+      int64_t e = e0 + k;
+      if (e >= t1) break;
+      bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
+      uint64_t inc = seen_head ? incl[k] : base + incl[k];
+      s.C[e - t0 + 1] = inc - q[k];  // exclusive: C_e
+      if (e == t1 - 1) s.C[t1 - t0 + 1] = inc;  // C_{t1} within the same distribution
+    }
+  }
+  __syncthreads();
+  // C_{t0-1} (only meaningful when t0-1 belongs to the same distribution)
+  if (tid == 0) {
+    s.C[0] = 0;
+    if (t0 > 0 && s.dprev == dfirst) {
+      rtf_dist P = a.dists[dfirst];
+      uint64_t qp;
+      if (P.flags & kDistMarginal) {
+        qp = __ldcg(&a.dists[t0 - 1 - P.elem_off].total);
+      } else {
+        uint32_t b = weight_bits(a.w[t0 - 1]);
+        qp = weight_bad(b) ? 0ull : quantize_bits(b, dist_scale(P, a.dmax, dfirst, a.n_shared));
+      }
+      s.C[0] = s.C[1] - qp;
+    }
+  }
+  __syncthreads();
+  // keys K_j for j in [t0-1, t1]
+  for (int k = tid; k < (int)(t1 - t0) + 2; k += kForestThreads) {
+    int64_t j = t0 - 1 + k;
+    uint64_t K = 0;
+    if (j >= 0 && j <= t1) {
+      int d;
+      if (k == 0) d = s.dprev;
+      else if (j < t1) d = s.dist[j - t0];
+      else d = s.dist[t1 - 1 - t0];  // C_{t1} belongs to the distribution of t1-1
+      rtf_dist P = a.dists[d];
+      K = key_for(P, s.C[k]);
+    }
+    s.K[k] = K;
+  }
+  __syncthreads();
+  // distances delta_j for j in [t0-1, t1-1]
+  for (int k = tid; k < (int)(t1 - t0) + 1; k += kForestThreads) {
+    int64_t j = t0 - 1 + k;
+    uint32_t dlt = kDeltaInf;
+    if (j >= 0) {
+      int d = (k == 0) ? s.dprev : s.dist[j - t0];
+      rtf_dist P = a.dists[d];
+      int64_t end = P.elem_off + P.n;
+      bool same_dist = (j + 1 < end);
+      if (k == 0) same_dist = same_dist && (s.dprev == dfirst);
+      if (same_dist) {
+        uint64_t Ka = s.K[k], Kb = s.K[k + 1];
+        if (cell_of(Ka, P.m) == cell_of(Kb, P.m)) dlt = key_distance(Ka, Kb);
+      }
+      a.delta[j] = (uint8_t)dlt;
+    }
+    s.delta[k] = (uint8_t)dlt;
+  }
+  for (int k = tid; k < (int)(t1 - t0); k += kForestThreads) {
+    s.child[k][0] = kUnset;
+    s.child[k][1] = kUnset;
+    s.other[k] = -1;
+  }
+  __syncthreads();
+
+  // ---- phase A: Algorithm 1 inside the tile --------------------------------
+#pragma unroll 1
+  for (int k = 0; k < kForestPer; ++k) {
+    int64_t j = e0 + k;
+    if (j >= t1) break;
+    const int d = s.dist[j - t0];
+    const int64_t off = a.dists[d].elem_off;
+    int64_t lo = j, hi = j;
+    int32_t node = ~(int32_t)(j - off);
+    while (true) {
+      uint32_t dl = s.delta[lo - t0];
+      uint32_t dr = s.delta[hi - t0 + 1];
+      if (dl >= kDeltaInf && dr >= kDeltaInf) {
+        // full cell inside the tile: its root is the node of the first leaf
+        int32_t lo_l = (int32_t)(lo - off);
+        s.child[lo - t0][0] = ~(lo_l > 0 ? lo_l - 1 : 0);
+        s.child[lo - t0][1] = node;
+        rtf_dist P = a.dists[d];
+        finish_cell(a, P, lo, hi, s.K[lo - t0 + 1], s.K[hi - t0 + 1]);
+        break;
+      }
+      int child = dl > dr ? 0 : 1;
+      if ((child == 1 && lo == t0) || (child == 0 && hi == t1 - 1)) {
+        int slot = atomicAdd(&s.ndefer, 1);
+        if (slot < 4) {
+          s.defer_parent[slot] = child ? lo : hi + 1;
+          s.defer_child[slot] = child;
+          s.defer_node[slot] = node;
+          s.defer_lo[slot] = lo;
+          s.defer_hi[slot] = hi;
+        } else {
+          raise_status(a.status, RTF_STATUS_TIMEOUT);
+        }
+        break;
+      }
+      int64_t parent = child ? lo : hi + 1;
+      s.child[parent - t0][child] = node;
+      int ob = atomicExch(&s.other[parent - t0], (int)((child ? hi : lo) - t0));
+      if (ob < 0) break;
+      s.other[parent - t0] = -2;
+      if (child)
+        lo = t0 + ob;
+      else
+        hi = t0 + ob;
+      node = (int32_t)(parent - off);
+    }
+  }
+  __syncthreads();
+
+  // ---- node records --------------------------------------------------------
+#pragma unroll
+  for (int k = 0; k < kForestPer; ++k) {
+    int64_t j = e0 + k;
+    if (j >= t1) break;
+    int i = (int)(j - t0);
+    int32_t c0 = s.child[i][0], c1 = s.child[i][1];
+    uint64_t C = s.C[i + 1];
+    if (c0 != kUnset && c1 != kUnset) {
+      rtf_node r;
+      r.cdf = C;
+      r.child[0] = c0;
+      r.child[1] = c1;
+      a.nodes[j] = r;
+    } else {
+      a.nodes[j].cdf = C;
+      if (c0 != kUnset) a.nodes[j].child[0] = c0;
+      if (c1 != kUnset) a.nodes[j].child[1] = c1;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+
+  // ---- phase B: merges across tiles ----------------------------------------
+#pragma unroll 1
+  for (int k = 0; k < kForestPer; ++k) {
+    int64_t p = e0 + k;
+    if (p >= t1) break;
+    int ob = s.other[p - t0];
+    if (ob < 0) continue;
+    // a first arrival that no sibling met inside the tile
+    const int d = s.dist[p - t0];
+    rtf_dist P = a.dists[d];
+    int64_t b = t0 + ob;
+    int child = b < p ? 0 : 1;
+    unsigned long long v = atomicExch(a.other + p, pack_other(epoch, b));
+    if ((uint32_t)(v >> 32) != epoch) continue;
+    __threadfence();
+    int64_t o = (int64_t)(uint32_t)v;
+    int64_t lo = child ? o : b, hi = child ? b : o;
+    climb_global(a, P, lo, hi, (int32_t)(p - P.elem_off), epoch);
+  }
+  if (tid < min(s.ndefer, 4)) {
+    int slot = tid;
+    int64_t parent = s.defer_parent[slot];
+    int child = s.defer_child[slot];
+    int64_t lo = s.defer_lo[slot], hi = s.defer_hi[slot];
+    const int d = s.dist[lo - t0 >= 0 && lo - t0 < kTile ? lo - t0 : hi - t0];
+    rtf_dist P = a.dists[d];
+    a.nodes[parent].child[child] = s.defer_node[slot];
+    __threadfence();
+    unsigned long long v = atomicExch(a.other + parent, pack_other(epoch, child ? hi : lo));
+    if ((uint32_t)(v >> 32) == epoch) {
+      __threadfence();
+      int64_t o = (int64_t)(uint32_t)v;
+      if (child)
+        lo = o;
+      else
+        hi = o;
+      climb_global(a, P, lo, hi, (int32_t)(parent - P.elem_off), epoch);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// guide: cells without keys take the interval of the last key before them
+// ---------------------------------------------------------------------------
+constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 16
+
+// Lookback for the carry-forward scan: the value of the nearest predecessor
+// tile that published a prefix.
+__device__ inline int32_t lookback_last(const uint64_t* st, int64_t tile, uint32_t* status) {
+  const int lane = threadIdx.x & 31;
+  int64_t look = tile - 1;
+  long long spins = 0;
+  while (look >= 0) {
+    int64_t idx = look - lane;
+    uint64_t s = idx >= 0 ? ld_acquire_u64(st + idx) : kFlagPrefix;
+    uint32_t flag = (uint32_t)(s >> 62);
+    unsigned inval = __ballot_sync(0xffffffffu, flag == 0);
+    unsigned pref = __ballot_sync(0xffffffffu, flag == 2);
+    if (pref) {
+      int p = __ffs(pref) - 1;
+      unsigned below = (p == 31) ? 0xffffffffu : ((2u << p) - 1u);
+      if (inval & below) {
+        if (++spins > kSpinLimit) {
+          raise_status(status, RTF_STATUS_TIMEOUT);
+          return 0;
+        }
+        __nanosleep(32);
+        continue;
+      }
+      uint64_t sv = __shfl_sync(0xffffffffu, s, p);
+      return (int32_t)(uint32_t)(sv & 0xffffffffull);
+    }
+    if (inval) {
+      if (++spins > kSpinLimit) {
+        raise_status(status, RTF_STATUS_TIMEOUT);
+        return 0;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    look -= 32;
+  }
+  return 0;
+}
+
+__global__ void __launch_bounds__(kGuideThreads)
+    guide_kernel(int64_t G, const int32_t* __restrict__ last, int32_t* guide, uint64_t* gstatus,
+                 Counters* ctr, uint32_t* status) {
+  __shared__ uint32_t tile_s;
+  __shared__ int32_t wlast[kGuideThreads / 32];
+  __shared__ int32_t carry_s;
+  if (threadIdx.x == 0) tile_s = atomicAdd(&ctr->guide_ticket, 1u);
+  __syncthreads();
+  const int64_t tile = tile_s;
+  const int64_t g0 = tile * kGuideTile + (int64_t)threadIdx.x * kGuidePer;
+  const int64_t gend = min(tile * kGuideTile + (int64_t)kGuideTile, G);
+  int32_t v[kGuidePer];
+  int32_t tlast = -1;
+#pragma unroll
+  for (int k = 0; k < kGuidePer; ++k) {
+    int64_t g = g0 + k;
+    v[k] = g < gend ? last[g] : -1;
+    if (v[k] >= 0) tlast = v[k];
+  }
+  // last valid value of all threads before this one (warp, then block)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t inc = tlast;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d && inc < 0) inc = o;
+  }
+  if (lane == 31) wlast[warp] = inc;
+  __syncthreads();
+  int32_t before_warp = -1;
+  for (int w2 = 0; w2 < warp; ++w2)
+    if (wlast[w2] >= 0) before_warp = wlast[w2];
+  int32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) ex = -1;
+  int32_t before = ex >= 0 ? ex : before_warp;
+  int32_t tile_last = -1;
+  for (int w2 = 0; w2 < kGuideThreads / 32; ++w2)
+    if (wlast[w2] >= 0) tile_last = wlast[w2];
+  if (threadIdx.x == 0) {
+    if (tile_last >= 0)
+      st_release_u64(gstatus + tile, kFlagPrefix | (uint32_t)tile_last);
+    else
+      st_release_u64(gstatus + tile, kFlagAgg);
+  }
+  // the incoming carry is needed only when the tile's first cell has no key
+  __shared__ int need_s;
+  if (threadIdx.x == 0) {
+    carry_s = -1;
+    need_s = (g0 < gend && v[0] < 0) ? 1 : 0;
+  }
+  __syncthreads();
+  if (warp == 0 && need_s) {
+    int32_t c = lookback_last(gstatus, tile, status);
+    if (lane == 0) {
+      carry_s = c;
+      if (tile_last < 0) st_release_u64(gstatus + tile, kFlagPrefix | (uint32_t)c);
+    }
+  }
+  __syncthreads();
+  int32_t carry = before >= 0 ? before : carry_s;
+#pragma unroll
+  for (int k = 0; k < kGuidePer; ++k) {
+    int64_t g = g0 + k;
+    if (g >= gend) break;
+    if (v[k] >= 0) {
+      carry = v[k];
+    } else {
+      guide[g] = ~carry;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch sequence (called from the C interface)
+// ---------------------------------------------------------------------------
+cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int marginal,
+                         const int64_t* offsets, const int32_t* m_arr, const int64_t* goff,
+                         int64_t n_single, int m_single, const rtf_forest* f, void* ws,
+                         cudaStream_t st) {
+  const int64_t G = f->num_cells;
+  WsLayout L = ws_layout(N, D, G);
+  char* base = static_cast<char*>(ws);
+  uint32_t* epoch = reinterpret_cast<uint32_t*>(base + L.persist);
+  Counters* ctr = reinterpret_cast<Counters*>(base + L.counters);
+  uint32_t* dmax = reinterpret_cast<uint32_t*>(base + L.dmax);
+  uint64_t* scan_status = reinterpret_cast<uint64_t*>(base + L.scan_status);
+  uint64_t* guide_status = reinterpret_cast<uint64_t*>(base + L.guide_status);
+  int32_t* last = reinterpret_cast<int32_t*>(base + L.last);
+  uint64_t* tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
+  uint8_t* delta = reinterpret_cast<uint8_t*>(base + L.delta);
+  unsigned long long* other = reinterpret_cast<unsigned long long*>(base + L.other);
+  const bool seg = D > 1;
+  const int Dw = marginal ? D - 1 : D;
+  const int64_t n_shared = marginal ? Nw : 0;
+
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(base + L.zero_begin, 0, L.zero_end - L.zero_begin, st))) return e;
+  if ((e = cudaMemsetAsync(last, 0xFF, sizeof(int32_t) * (size_t)G, st))) return e;
+  if ((e = cudaMemsetAsync(f->status, 0, sizeof(uint32_t), st))) return e;
+  init_dists_kernel<<<(D + 255) / 256, 256, 0, st>>>(f->dists, D, offsets, m_arr, goff, marginal,
+                                                      n_single, m_single, epoch, f->status);
+  const int64_t nscale = (Nw + kScaleTile - 1) / kScaleTile;
+  if (marginal || !seg) {
+    // one group: a plain block max into dmax[0]
+    scale_kernel<false><<<(unsigned)nscale, kScaleThreads, 0, st>>>(w, Nw, f->dists, Dw, dmax,
+                                                                    f->status);
+  } else {
+    scale_kernel<true><<<(unsigned)nscale, kScaleThreads, 0, st>>>(w, Nw, f->dists, Dw, dmax,
+                                                                   f->status);
+  }
+  const int64_t tiles_w = num_tiles(Nw);
+  if (seg)
+    scan_kernel<true><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(
+        w, Nw, f->dists, D, Dw, marginal, n_shared, dmax, scan_status, tile_prefix, ctr,
+        f->status);
+  else
+    scan_kernel<false><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(
+        w, Nw, f->dists, D, Dw, marginal, n_shared, dmax, scan_status, tile_prefix, ctr,
+        f->status);
+  ForestArgs fa;
+  fa.w = w;
+  fa.N = N;
+  fa.Nw = Nw;
+  fa.dists = f->dists;
+  fa.D = D;
+  fa.Dw = Dw;
+  fa.n_shared = n_shared;
+  fa.nodes = f->nodes;
+  fa.guide = f->guide;
+  fa.last = last;
+  fa.tile_prefix = tile_prefix;
+  fa.dmax = dmax;
+  fa.delta = delta;
+  fa.other = other;
+  fa.epoch = epoch;
+  fa.status = f->status;
+  const size_t fsmem = sizeof(ForestShared);
+  if (seg) {
+    if ((e = cudaFuncSetAttribute(forest_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fsmem)))
+      return e;
+    forest_kernel<true><<<(unsigned)num_tiles(N), kForestThreads, fsmem, st>>>(fa);
+  } else {
+    if ((e = cudaFuncSetAttribute(forest_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
+      return e;
+    forest_kernel<false><<<(unsigned)num_tiles(N), kForestThreads, fsmem, st>>>(fa);
+  }
+  const int64_t gtiles = (G + kGuideTile - 1) / kGuideTile;
+  guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, f->guide, guide_status, ctr,
+                                                           f->status);
+  return cudaGetLastError();
+}
+
+}  // namespace rtf

@@ -1,0 +1,389 @@
+// Device-side helpers shared by the build, sample and backward kernels.
+//
+// Exact integer arithmetic of the fixed-point reading of the paper's CDF
+// (Sec. 1), the keys of Algorithm 1 (Sec. 3.2) in the 32-bit sample domain,
+// bulk-copy (TMA) staging of weight tiles into shared memory with bounded
+// mbarrier waits, and a few warp/block scan primitives.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rtf.h"
+
+namespace rtf {
+
+// ---------------------------------------------------------------------------
+// tunables (tile shapes); the build and the workspace layout agree on them
+// ---------------------------------------------------------------------------
+constexpr int kTile = 2048;           // weights per scan / forest tile
+constexpr int kScanThreads = 256;     // scan kernel: 8 weights per thread
+constexpr int kForestThreads = 512;   // forest kernel: 4 leaves per thread
+constexpr int kGuideTile = 4096;      // guide cells per guide-fill tile
+constexpr int kGuideThreads = 256;    // 16 cells per thread
+constexpr int kMaxThreads = 512;
+constexpr uint32_t kDeltaInf = 64;    // distance across a cell / distribution boundary
+constexpr long long kSpinLimit = 1ll << 22;   // bounded waits
+
+// status-word flags of the decoupled lookback (top two bits of a u64)
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 62) - 1;
+
+// ---------------------------------------------------------------------------
+// workspace layout (byte offsets, 256-aligned regions)
+// ---------------------------------------------------------------------------
+struct WsLayout {
+  size_t persist;      // u32 epoch (kept across builds)
+  size_t zero_begin;   // start of the region zero-filled by every build
+  size_t counters;     // u32 tickets / done counters
+  size_t dmax;         // u32 [D] max float bits per distribution / group
+  size_t scan_status;  // u64 [num_tiles]
+  size_t guide_status; // u64 [num_guide_tiles]
+  size_t zero_end;
+  size_t last;         // i32 [G] last leaf of each non-empty cell (set to -1)
+  size_t tile_prefix;  // u64 [num_tiles]
+  size_t delta;        // u8  [N]
+  size_t other;        // u64 [N] epoch-tagged otherBounds of Algorithm 1
+  size_t total;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+__host__ __device__ inline int64_t num_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
+
+__host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
+  WsLayout L;
+  size_t o = 0;
+  L.persist = o; o += 256;
+  L.zero_begin = o;
+  L.counters = o; o += 256;
+  L.dmax = o; o = align256(o + sizeof(uint32_t) * (size_t)D);
+  L.scan_status = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
+  L.guide_status = o;
+  o = align256(o + sizeof(uint64_t) * (size_t)((G + kGuideTile - 1) / kGuideTile));
+  L.zero_end = o;
+  L.last = o; o = align256(o + sizeof(int32_t) * (size_t)G);
+  L.tile_prefix = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
+  L.delta = o; o = align256(o + (size_t)N);
+  L.other = o; o = align256(o + sizeof(uint64_t) * (size_t)N);
+  L.total = o;
+  return L;
+}
+
+// counters inside WsLayout::counters
+struct Counters {
+  uint32_t scan_ticket;
+  uint32_t guide_ticket;
+  uint32_t scan_done;
+  uint32_t pad[61];
+};
+
+// internal rtf_dist.flags
+constexpr int32_t kDistMarginal = 1;   // weights are the totals of dists [0, D-1)
+constexpr int32_t kDistShared = 2;     // scale shared with every non-marginal dist
+
+// ---------------------------------------------------------------------------
+// status word
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void raise_status(uint32_t* status, uint32_t bits) {
+  atomicOr(status, bits);
+}
+
+// ---------------------------------------------------------------------------
+// float weights -> fixed point
+// ---------------------------------------------------------------------------
+// Bits of a weight with -0 folded to +0.
+__device__ __forceinline__ uint32_t weight_bits(float x) {
+  uint32_t b = __float_as_uint(x);
+  return b == 0x80000000u ? 0u : b;
+}
+
+__device__ __forceinline__ bool weight_bad(uint32_t b) {
+  return (b >> 31) != 0 || (b & 0x7F800000u) == 0x7F800000u;
+}
+
+// floor(log2 x) for the bits of a positive finite float (subnormals too).
+__device__ __forceinline__ int floor_log2_bits(uint32_t b) {
+  uint32_t E = b >> 23;
+  if (E) return (int)E - 127;
+  return (31 - __clz(b & 0x7FFFFFu)) - 149;
+}
+
+__host__ __device__ inline int ceil_log2_i64(int64_t n) {
+  int c = 0;
+  while ((int64_t(1) << c) < n) ++c;
+  return c;
+}
+
+// S = B - 1 - e_max with B = 62 - ceil(log2 n_group).
+__device__ __forceinline__ int scale_from_max(uint32_t maxbits, int64_t n_group) {
+  int B = 62 - ceil_log2_i64(n_group);
+  return B - 1 - floor_log2_bits(maxbits);
+}
+
+// q = floor(w 2^S) from the bits of w: an exact shift of the integer
+// significand.
+__device__ __forceinline__ uint64_t quantize_bits(uint32_t b, int S) {
+  if (b == 0) return 0;
+  uint32_t E = b >> 23;
+  uint64_t M;
+  int e2;
+  if (E) {
+    M = (b & 0x7FFFFFu) | 0x800000u;
+    e2 = (int)E - 150;
+  } else {
+    M = b & 0x7FFFFFu;
+    e2 = -149;
+  }
+  int sh = e2 + S;
+  if (sh >= 0) return M << sh;
+  sh = -sh;
+  return sh >= 64 ? 0ull : (M >> sh);
+}
+
+// ---------------------------------------------------------------------------
+// sample-domain arithmetic
+// ---------------------------------------------------------------------------
+// t(u) = floor(u T / 2^32) for 0 <= u <= 2^32 (T < 2^62).
+__device__ __forceinline__ uint64_t t_of(uint64_t u, uint64_t T) {
+  return u >= (1ull << 32) ? T : __umul64hi(T, u << 32);
+}
+
+// floor((hi 2^64 + lo) / d) for hi < d (restoring long division; used once per
+// distribution).
+__device__ inline uint64_t div128_64(uint64_t hi, uint64_t lo, uint64_t d) {
+  uint64_t q = 0;
+  for (int i = 0; i < 64; ++i) {
+    uint64_t carry = hi >> 63;
+    hi = (hi << 1) | (lo >> 63);
+    lo <<= 1;
+    q <<= 1;
+    if (carry || hi >= d) {
+      hi -= d;
+      q |= 1;
+    }
+  }
+  return q;
+}
+
+// Reciprocal of the normalised total: floor((2^128 - 1) / (T << z)) - 2^64.
+__device__ inline uint64_t total_recip(uint64_t T, int z) {
+  uint64_t Tn = T << z;
+  return div128_64(~Tn, ~0ull, Tn);
+}
+
+// Key K = ceil(C 2^32 / T): the smallest u with t(u) >= C.  A multiply by the
+// reciprocal gives a value at most two below K; two exact checks finish it.
+__device__ __forceinline__ uint64_t key_of(uint64_t C, uint64_t T, uint64_t R, int z) {
+  if (C >= T) return 1ull << 32;
+  uint64_t X = C << z;
+  uint64_t Q = __umul64hi(X, R) + X;
+  uint64_t v = Q >> 32;
+  if (t_of(v, T) < C) {
+    ++v;
+    if (t_of(v, T) < C) ++v;
+  }
+  return v;
+}
+
+// Cell of a key among 2^m cells; 2^m for K = 2^32.
+__device__ __forceinline__ uint64_t cell_of(uint64_t K, int m) { return K >> (32 - m); }
+
+// Distance of two neighbouring keys of one cell: bit length of their XOR
+// (the XOR of two keys of one cell fits in 32 bits).
+__device__ __forceinline__ uint32_t key_distance(uint64_t a, uint64_t b) {
+  return 32u - (uint32_t)__clz((uint32_t)(a ^ b));
+}
+
+// ---------------------------------------------------------------------------
+// memory ordering helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// bulk copy (TMA, non-tensor) global -> shared with an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+      "[%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Stage w[t0, t1) into shared memory: the 16-byte aligned body by one bulk
+// copy, the (at most 3) trailing weights by plain loads.  Called by all
+// threads; returns false (after raising RTF_STATUS_TIMEOUT and a second
+// bounded wait for the copy in flight) when the copy did not complete.
+// `w + t0` must be 16-byte aligned (t0 is a multiple of the tile size and w is
+// 16-byte aligned).
+__device__ inline bool stage_weights(float* dst, const float* w, int64_t t0, int64_t t1,
+                                     uint64_t* bar, int* flag, uint32_t* status) {
+  int cnt = (int)(t1 - t0);
+  int body = cnt & ~3;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    if (body > 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)body * 4u);
+      bulk_g2s(dst, w + t0, (uint32_t)body * 4u, bar);
+    }
+  }
+  for (int k = body + (int)threadIdx.x; k < cnt; k += blockDim.x) dst[k] = w[t0 + k];
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (body > 0 && !mbar_wait(bar, 0)) {
+      raise_status(status, RTF_STATUS_TIMEOUT);
+      mbar_wait(bar, 0);
+      ok = 0;
+    }
+    *flag = ok;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide scans
+// ---------------------------------------------------------------------------
+// Segmented exclusive scan of (head, value) pairs, one pair per thread:
+// (f1, s1) + (f2, s2) = (f1 | f2, f2 ? s2 : s1 + s2).  Returns the exclusive
+// prefix (sum since the last head before this thread, or 0) and stores the
+// block total in *total_f / *total_s.  `scratch` needs 2 * (blockDim/32)
+// u64 + flags.
+struct SegPair {
+  uint64_t s;
+  uint32_t f;
+};
+
+__device__ __forceinline__ SegPair seg_combine(SegPair a, SegPair b) {
+  SegPair r;
+  r.f = a.f | b.f;
+  r.s = b.f ? b.s : a.s + b.s;
+  return r;
+}
+
+__device__ inline SegPair block_seg_exclusive(SegPair x, SegPair* warp_tot, SegPair* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // inclusive warp scan
+  SegPair inc = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    SegPair o;
+    o.s = __shfl_up_sync(0xffffffffu, inc.s, d);
+    o.f = __shfl_up_sync(0xffffffffu, inc.f, d);
+    if (lane >= d) inc = seg_combine(o, inc);
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    SegPair v = lane < nw ? warp_tot[lane] : SegPair{0ull, 0u};
+    SegPair vi = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      SegPair o;
+      o.s = __shfl_up_sync(0xffffffffu, vi.s, d);
+      o.f = __shfl_up_sync(0xffffffffu, vi.f, d);
+      if (lane >= d) vi = seg_combine(o, vi);
+    }
+    if (lane < nw) warp_tot[lane] = vi;  // inclusive over warps
+    if (lane == nw - 1) *total = vi;
+  }
+  __syncthreads();
+  SegPair excl_warp = warp > 0 ? warp_tot[warp - 1] : SegPair{0ull, 0u};
+  // exclusive within warp
+  SegPair ex;
+  ex.s = __shfl_up_sync(0xffffffffu, inc.s, 1);
+  ex.f = __shfl_up_sync(0xffffffffu, inc.f, 1);
+  if (lane == 0) ex = SegPair{0ull, 0u};
+  SegPair r = seg_combine(excl_warp, ex);
+  __syncthreads();
+  return r;
+}
+
+// Plain (unsegmented) exclusive block scan of u32 values.
+__device__ inline uint32_t block_exclusive_u32(uint32_t x, uint32_t* warp_tot, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += o;
+    }
+    if (lane < nw) warp_tot[lane] = v;
+    if (lane == nw - 1) *total = v;
+  }
+  __syncthreads();
+  uint32_t r = (warp > 0 ? warp_tot[warp - 1] : 0u) + inc - x;
+  __syncthreads();
+  return r;
+}
+
+// Index of the distribution that owns element `e`: the largest d with
+// dists[d].elem_off <= e (binary search over [lo, hi]).
+__device__ inline int find_dist(const rtf_dist* dists, int lo, int hi, int64_t e) {
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (dists[mid].elem_off <= e)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace rtf

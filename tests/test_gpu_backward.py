@@ -1,0 +1,173 @@
+"""Gradient of the in-bin positions on the GPU against the oracle's fp64
+chain-rule gradient (relative error in the 2-norm at most 1e-4) and against
+central differences of the GPU forward itself."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_1901_05423_gb300 import api
+from paper_1901_05423_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _require_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def run_1d(n, n_s, m, seed, sigma=1.0):
+    w = W.lognormal_weights(n, seed=seed, sigma=sigma)
+    u = W.iid_u32(n_s, seed=seed + 1)
+    g = W.normal_f32(n_s, seed=seed + 2)
+    wd = to_dev(w)
+    f = api.rtf_build(wd, m)
+    ud = api.u32_tensor(u, DEV)
+    idx, pos = api.rtf_sample(f, ud)
+    gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, to_dev(g))
+    torch.cuda.synchronize()
+    f.check_status()
+    ref = orc.build(w, 1 << m)
+    ridx, _ = orc.sample(ref.C, u)
+    assert np.array_equal(idx.cpu().numpy(), ridx)
+    gref = orc.grad(w, u, ridx, g)
+    return gw.cpu().numpy(), gref
+
+
+def test_backward_small():
+    gw, gref = run_1d(1000, 100000, 8, seed=0)
+    assert rel_err(gw, gref) <= TOL
+
+
+def test_backward_single_bin_is_zero():
+    w = np.array([3.0], np.float32)
+    u = W.iid_u32(4096, seed=1)
+    g = W.normal_f32(4096, seed=2)
+    wd = to_dev(w)
+    f = api.rtf_build(wd, 2)
+    ud = api.u32_tensor(u, DEV)
+    idx, pos = api.rtf_sample(f, ud)
+    gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, to_dev(g))
+    # xi W - 0 over W: the weight cancels exactly in the relaxed position
+    assert abs(float(gw.item())) <= 1e-5 * float(np.abs(g).sum())
+
+
+def test_backward_config_full():
+    """n = 2^20 lognormal(0, 1), 2^24 uniform samples, dL/dx ~ N(0, 1)."""
+    gw, gref = run_1d(1 << 20, 1 << 24, 18, seed=10)
+    assert rel_err(gw, gref) <= TOL
+
+
+def test_backward_sorted_samples_merge_runs():
+    """Sorted samples put long runs of equal bins inside a warp."""
+    n, n_s, m = 5000, 1 << 20, 10
+    w = W.lognormal_weights(n, seed=20, sigma=1.0)
+    u = W.sorted_radical_inverse_u32(n_s)
+    g = W.normal_f32(n_s, seed=21)
+    wd = to_dev(w)
+    f = api.rtf_build(wd, m)
+    ud = api.u32_tensor(u, DEV)
+    idx, pos = api.rtf_sample(f, ud)
+    gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, to_dev(g))
+    ref = orc.build(w, 1 << m)
+    ridx, _ = orc.sample(ref.C, u)
+    gref = orc.grad(w, u, ridx, g)
+    assert rel_err(gw.cpu().numpy(), gref) <= TOL
+
+
+def test_backward_tagged_batch():
+    sizes = [1, 17, 300, 4096, 2049]
+    ms = [0, 3, 6, 10, 9]
+    w = np.concatenate([W.lognormal_weights(s, seed=30 + i, sigma=1.0) for i, s in enumerate(sizes)])
+    n_s = 1 << 18
+    rng = np.random.default_rng(31)
+    dist = rng.integers(0, len(sizes), n_s).astype(np.int32)
+    u = W.iid_u32(n_s, seed=32)
+    g = W.normal_f32(n_s, seed=33)
+    wd = to_dev(w)
+    f = api.rtf_build_batched(wd, sizes, ms)
+    ud = api.u32_tensor(u, DEV)
+    dd = to_dev(dist)
+    idx, pos = api.rtf_sample(f, ud, dist_id=dd)
+    gw = api.rtf_sample_backward(f, wd, ud, dd, idx, pos, to_dev(g)).cpu().numpy()
+    off = f.offsets
+    gref = np.zeros(w.size)
+    for d in range(len(sizes)):
+        sel = dist == d
+        ref = orc.build(w[off[d]:off[d + 1]], 1 << ms[d])
+        ridx, _ = orc.sample(ref.C, u[sel])
+        gref[off[d]:off[d + 1]] = orc.grad(w[off[d]:off[d + 1]], u[sel], ridx, g[sel])
+    assert rel_err(gw, gref) <= TOL
+
+
+@pytest.mark.parametrize("H,Wd,n_s", [(32, 64, 1 << 16), (512, 1024, 1 << 22)])
+def test_backward_env_map(H, Wd, n_s):
+    lum = W.env_map(H, Wd, seed=40)
+    m_row, m_col = 9, 10
+    sizes = [Wd] * H + [H]
+    ms = [m_col] * H + [m_row]
+    wd = to_dev(lum.reshape(-1))
+    f = api.rtf_build_batched(wd, sizes, ms, marginal=True)
+    rng = np.random.default_rng(41)
+    u = rng.integers(0, 1 << 32, 2 * n_s, dtype=np.uint64).astype(np.uint32)
+    g = W.normal_f32(2 * n_s, seed=42)
+    ud = api.u32_tensor(u, DEV)
+    idx, pos = api.rtf_sample(f, ud, mode=api.SAMPLE_2D)
+    gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, to_dev(g), mode=api.SAMPLE_2D)
+    torch.cuda.synchronize()
+    f.check_status()
+    rows, marg = orc.build_env(lum, 1 << m_row, 1 << m_col)
+    r, c, _, _ = orc.sample_env(rows, marg, u[0::2], u[1::2])
+    ii = idx.cpu().numpy()
+    assert np.array_equal(ii[:, 0], r) and np.array_equal(ii[:, 1], c)
+    gref = orc.grad_env(lum, u[0::2], u[1::2], r, c, g[0::2], g[1::2]).reshape(-1)
+    assert rel_err(gw.cpu().numpy(), gref) <= TOL
+
+
+def test_backward_matches_gpu_forward_differences():
+    """Central differences of the GPU forward (positions in float32) for
+    weights whose integer q is >= 2^30, on samples whose bin does not change."""
+    n, n_s, m = 64, 1 << 16, 6
+    w = W.lognormal_weights(n, seed=50, sigma=0.5)
+    u = W.iid_u32(n_s, seed=51)
+    g = W.normal_f32(n_s, seed=52)
+    wd = to_dev(w)
+    ud = api.u32_tensor(u, DEV)
+    f = api.rtf_build(wd, m)
+    idx, pos = api.rtf_sample(f, ud)
+    gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, to_dev(g)).cpu().numpy()
+    i0 = idx.cpu().numpy()
+    for k in (3, 17, 40):
+        h = np.float32(1e-2) * w[k]
+        wp, wm = w.copy(), w.copy()
+        wp[k] += h
+        wm[k] -= h
+        fp = api.rtf_build(to_dev(wp), m)
+        ip, pp = api.rtf_sample(fp, ud)
+        ip, pp = ip.cpu().numpy(), pp.cpu().numpy().astype(np.float64)
+        fm = api.rtf_build(to_dev(wm), m)
+        im, pm = api.rtf_sample(fm, ud)
+        im, pm = im.cpu().numpy(), pm.cpu().numpy().astype(np.float64)
+        keep = (ip == i0) & (im == i0)
+        hk = float(wp[k]) - float(wm[k])
+        fd = np.dot(g[keep].astype(np.float64), pp[keep] - pm[keep]) / hk
+        # the analytic gradient restricted to the same samples
+        ref = orc.build(w, 1 << m)
+        ridx, _ = orc.sample(ref.C, u[keep])
+        gk = orc.grad(w, u[keep], ridx, g[keep])[k]
+        assert abs(fd - gk) <= 2e-3 * (abs(gk) + np.abs(g[keep]).sum() * 1e-4)
+    assert np.isfinite(gw).all()

@@ -1,0 +1,330 @@
+"""Parity of the CUDA path (through the C interface) with the CPU oracle.
+
+Bit-exact: the integer CDF, the forest's child references, the guide table and
+the sampled bin indices.  Floating point: the in-bin positions within 4 ulp of
+the oracle's fp64 value rounded to float32 (the three roundings of the float32
+quotient bound the error by 3 ulp plus the reference's half ulp).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_1901_05423_gb300 import api
+from paper_1901_05423_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+MAX_ULP = 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _require_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_05423_gb300 import _native
+    _native.load()
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def ulp_dist(pos_gpu, pos_ref64):
+    a = np.ascontiguousarray(pos_gpu, dtype=np.float32).view(np.int32).astype(np.int64)
+    b = np.asarray(pos_ref64, dtype=np.float64).astype(np.float32).view(np.int32).astype(np.int64)
+    return np.abs(a - b)
+
+
+def check_structure(f, ref, elem_off=0, guide_off=0, n=None, cells=None):
+    n = ref.n if n is None else n
+    cells = ref.M if cells is None else cells
+    C = f.cdf()[elem_off:elem_off + n].cpu().numpy().view(np.uint64)
+    ch = f.children()[elem_off:elem_off + n].cpu().numpy()
+    g = f.guide[guide_off:guide_off + cells].cpu().numpy()
+    assert np.array_equal(C, ref.C[:-1]), "CDF"
+    bad = np.nonzero((ch != ref.nodes).any(axis=1))[0]
+    assert bad.size == 0, f"{bad.size} node records differ, first {bad[:5]}"
+    badg = np.nonzero(g != ref.guide)[0]
+    assert badg.size == 0, f"{badg.size} guide cells differ, first {badg[:5]}"
+
+
+def check_samples(idx, pos, ridx, rpos):
+    idx = idx.cpu().numpy() if torch.is_tensor(idx) else idx
+    pos = pos.cpu().numpy() if torch.is_tensor(pos) else pos
+    bad = np.nonzero(idx != ridx)[0]
+    assert bad.size == 0, f"{bad.size} indices differ, first at {bad[:5]}"
+    d = ulp_dist(pos, rpos)
+    assert d.max() <= MAX_ULP, f"position off by {d.max()} ulp"
+    return int(d.max())
+
+
+def build_and_check(w, m):
+    f = api.rtf_build(to_dev(w), m)
+    torch.cuda.synchronize()
+    f.check_status()
+    ref = orc.build(w, 1 << m)
+    check_structure(f, ref)
+    return f, ref
+
+
+# ---------------------------------------------------------------------------
+# single distribution
+# ---------------------------------------------------------------------------
+
+def test_config_small_uniform_radical_inverse():
+    """n = 1024 uniform(0.01, 1) weights, 2^8 cells, 2^20 radical-inverse samples."""
+    w = W.uniform_weights(1024, seed=0)
+    f, ref = build_and_check(w, 8)
+    u = W.radical_inverse_u32(1 << 20)
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
+    ridx, rpos = orc.sample(ref.C, u)
+    check_samples(idx, pos, ridx, rpos)
+
+
+def weight_cases():
+    rng = np.random.default_rng(123)
+    sizes = [1, 2, 3, 4, 5, 31, 32, 33, 1023, 2047, 2048, 2049, 4095, 4096, 4097,
+             3 * 2048 + 17, 20000]
+    kinds = ["uniform", "lognormal2", "equal", "zeros", "spike", "range", "subnormal", "dups"]
+    cases = []
+    for n in sizes:
+        for kind in kinds:
+            if kind == "uniform":
+                w = rng.uniform(0.01, 1, n)
+            elif kind == "lognormal2":
+                w = np.exp(rng.normal(0, 2, n))
+            elif kind == "equal":
+                w = np.full(n, 0.37)
+            elif kind == "zeros":
+                w = rng.uniform(0, 1, n) * (rng.random(n) < 0.3)
+                if not w.any():
+                    w[n // 2] = 1.0
+            elif kind == "spike":
+                w = np.full(n, 1e-3)
+                w[rng.integers(0, n)] = 1e6
+            elif kind == "range":
+                w = np.exp(rng.normal(0, 12, n))
+            elif kind == "subnormal":
+                w = np.full(n, 1e-40)
+                w[::7] = 3e-39
+            else:
+                w = np.repeat(rng.uniform(0.01, 1, (n + 7) // 8), 8)[:n] * (rng.random(n) < 0.8)
+                if not w.any():
+                    w[0] = 1.0
+            cases.append((n, kind, w.astype(np.float32)))
+    return cases
+
+
+@pytest.mark.parametrize("m", [0, 1, 4, 9, 14])
+def test_random_sizes_and_weight_kinds(m):
+    rng = np.random.default_rng(m)
+    for n, kind, w in weight_cases():
+        f = api.rtf_build(to_dev(w), m)
+        u = rng.integers(0, 1 << 32, 4096, dtype=np.uint64).astype(np.uint32)
+        u[:3] = [0, 1, 0xFFFFFFFF]
+        idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
+        torch.cuda.synchronize()
+        f.check_status()
+        ref = orc.build(w, 1 << m)
+        try:
+            check_structure(f, ref)
+            ridx, rpos = orc.sample(ref.C, u)
+            check_samples(idx, pos, ridx, rpos)
+        except AssertionError as e:
+            raise AssertionError(f"n={n} kind={kind} m={m}: {e}")
+
+
+def test_worked_example_fig11_cells_power_of_two():
+    """The weights of the worked forest with 16 cells (the GPU supports 2^m)."""
+    w = np.array([5, 1, 3, 2, 6, 6, 7, 6, 28, 2, 14, 33], np.float32)
+    build_and_check(w, 4)
+
+
+def test_rebuild_reuses_workspace_epochs():
+    """Repeated builds through one workspace (epoch-tagged synchronisation)
+    give identical structures."""
+    w = W.lognormal_weights(50000, seed=3, sigma=2.0)
+    f1, ref = build_and_check(w, 12)
+    snap = f1.nodes.clone()
+    for _ in range(3):
+        f2 = api.rtf_build(to_dev(w), 12)
+        torch.cuda.synchronize()
+        f2.check_status()
+        assert torch.equal(f2.nodes, snap)
+
+
+def test_status_bits_for_bad_weights():
+    for bad, bit in (([1.0, -1.0, 2.0], api.STATUS_BAD_WEIGHT),
+                     ([1.0, np.nan, 2.0], api.STATUS_BAD_WEIGHT),
+                     ([np.inf, 1.0, 1.0], api.STATUS_BAD_WEIGHT),
+                     ([0.0, 0.0, 0.0], api.STATUS_ZERO_TOTAL)):
+        f = api.rtf_build(to_dev(np.array(bad, np.float32)), 2)
+        torch.cuda.synchronize()
+        assert int(f.status.item()) & bit
+    # a good build afterwards is clean again
+    build_and_check(np.array([1.0, 2.0, 3.0], np.float32), 2)
+
+
+def test_monotone_on_sorted_samples():
+    w = W.lognormal_weights(100000, seed=4, sigma=2.0)
+    f = api.rtf_build(to_dev(w), 14)
+    u = W.sorted_radical_inverse_u32(1 << 22)
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
+    idx = idx.cpu().numpy()
+    pos = pos.cpu().numpy()
+    assert np.all(np.diff(idx) >= 0)
+    same = np.diff(idx) == 0
+    assert np.all(np.diff(pos)[same] >= 0)
+
+
+# ---------------------------------------------------------------------------
+# full size: n = 2^24 lognormal(0, 2), 2^20 cells
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def big():
+    w = W.lognormal_weights(1 << 24, seed=0, sigma=2.0)
+    f = api.rtf_build(to_dev(w), 20)
+    torch.cuda.synchronize()
+    f.check_status()
+    ref = orc.build(w, 1 << 20)
+    return w, f, ref
+
+
+def test_full_size_structure_bit_exact(big):
+    w, f, ref = big
+    check_structure(f, ref)
+
+
+def test_full_size_samples(big):
+    """Both sample sets at full size through the same launch configuration as
+    the benchmark; the oracle checks every 64th sample of each."""
+    w, f, ref = big
+    n_s = 1 << 28
+    for name, u in (("iid", W.iid_u32(n_s, seed=1)), ("sorted", W.sorted_radical_inverse_u32(n_s))):
+        ud = api.u32_tensor(u, DEV)
+        idx, pos = api.rtf_sample(f, ud)
+        torch.cuda.synchronize()
+        sel = np.arange(0, n_s, 64)
+        sel = np.concatenate([sel, np.arange(n_s - 4096, n_s)])
+        ridx, rpos = orc.sample(ref.C, u[sel])
+        check_samples(idx[torch.from_numpy(sel).to(DEV)], pos[torch.from_numpy(sel).to(DEV)],
+                      ridx, rpos)
+        del ud, idx, pos
+
+
+# ---------------------------------------------------------------------------
+# batched
+# ---------------------------------------------------------------------------
+
+def batched_check(w, offsets, ms, samples_per=512, seed=0):
+    sizes = np.diff(offsets)
+    f = api.rtf_build_batched(to_dev(w), sizes, ms)
+    torch.cuda.synchronize()
+    f.check_status()
+    goff = f.guide_offsets
+    rng = np.random.default_rng(seed)
+    D = len(sizes)
+    dist = rng.integers(0, D, samples_per * min(D, 64), dtype=np.int64).astype(np.int32)
+    u = rng.integers(0, 1 << 32, dist.size, dtype=np.uint64).astype(np.uint32)
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV), dist_id=to_dev(dist))
+    idx = idx.cpu().numpy()
+    pos = pos.cpu().numpy()
+    check_ds = sorted(set(rng.integers(0, D, 64).tolist()) | {0, D - 1})
+    for d in check_ds:
+        wd = w[offsets[d]:offsets[d + 1]]
+        ref = orc.build(wd, 1 << int(ms[d]))
+        check_structure(f, ref, elem_off=int(offsets[d]), guide_off=int(goff[d]))
+        sel = dist == d
+        if sel.any():
+            ridx, rpos = orc.sample(ref.C, u[sel])
+            check_samples(idx[sel], pos[sel], ridx, rpos)
+    return f
+
+
+def test_batched_small_ragged():
+    rng = np.random.default_rng(5)
+    sizes = np.concatenate([[1, 2, 3, 2048, 2049, 1, 1], rng.integers(1, 5000, 300)])
+    w = np.concatenate([W.lognormal_weights(int(s), seed=int(i), sigma=1.5)
+                        for i, s in enumerate(sizes)])
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    ms = np.clip(np.ceil(np.log2(np.maximum(sizes, 1))).astype(int) - 1, 0, 16)
+    batched_check(w, offsets, ms)
+
+
+def test_batched_ragged_full_config():
+    """16384 distributions, sizes log-uniform in [8, 65536], lognormal(0, 1.5)."""
+    w, offsets = W.ragged_batch(16384, seed=0)
+    sizes = np.diff(offsets)
+    ms = np.clip(np.round(np.log2(sizes)).astype(int), 3, 16)
+    batched_check(w, offsets, ms, samples_per=1024)
+
+
+# ---------------------------------------------------------------------------
+# 2-D environment map (marginal + conditionals in one batched build)
+# ---------------------------------------------------------------------------
+
+def env_check(H, Wd, m_row, m_col, n_s, seed=0):
+    lum = W.env_map(H, Wd, seed=seed)
+    sizes = [Wd] * H + [H]
+    ms = [m_col] * H + [m_row]
+    f = api.rtf_build_batched(to_dev(lum.reshape(-1)), sizes, ms, marginal=True)
+    torch.cuda.synchronize()
+    f.check_status()
+    rows, marg = orc.build_env(lum, 1 << m_row, 1 << m_col)
+    check_structure(f, marg, elem_off=H * Wd, guide_off=H << m_col)
+    rng = np.random.default_rng(seed)
+    for r in sorted(set(rng.integers(0, H, 16).tolist()) | {0, H - 1}):
+        check_structure(f, rows[r], elem_off=r * Wd, guide_off=r << m_col)
+    u = rng.integers(0, 1 << 32, 2 * n_s, dtype=np.uint64).astype(np.uint32)
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV), mode=api.SAMPLE_2D)
+    idx = idx.cpu().numpy()
+    pos = pos.cpu().numpy()
+    k = min(n_s, 1 << 16)
+    r, c, pr, pc = orc.sample_env(rows, marg, u[0:2 * k:2], u[1:2 * k:2])
+    check_samples(idx[:k, 0], pos[:k, 0], r, pr)
+    check_samples(idx[:k, 1], pos[:k, 1], c, pc)
+    return f, lum
+
+
+def test_env_map_small():
+    env_check(64, 128, 6, 7, 1 << 16)
+
+
+def test_env_map_full_config():
+    """4096 x 2048 luminance with hot spots; marginal over 2048 rows and 2048
+    conditionals built in one batched launch sequence; 2^26 sample pairs."""
+    env_check(2048, 4096, 12, 12, 1 << 26)
+
+
+# ---------------------------------------------------------------------------
+# graph capture
+# ---------------------------------------------------------------------------
+
+def test_graph_replay_is_deterministic():
+    w = W.lognormal_weights(300000, seed=7, sigma=2.0)
+    wd = to_dev(w)
+    u = api.u32_tensor(W.iid_u32(1 << 20, seed=8), DEV)
+    f = api.rtf_build(wd, 14)
+    idx, pos = api.rtf_sample(f, u)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            api.rtf_build(wd, 14, forest=f)
+            api.rtf_sample(f, u, idx_out=idx, pos_out=pos)
+    torch.cuda.synchronize()
+    outs = []
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        f.check_status()
+        outs.append((f.nodes.clone(), idx.clone(), pos.clone()))
+    assert all(torch.equal(a, b) for a, b in zip(outs[0], outs[1]))
+    ref = orc.build(w, 1 << 14)
+    check_structure(f, ref)

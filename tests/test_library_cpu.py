@@ -1,0 +1,108 @@
+"""CPU-side checks of the C interface: the library builds for sm_103a, loads,
+exports every function include/rtf.h declares, mirrors its structs, and rejects
+bad arguments before any GPU work.  No compute call is made here."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "rtf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rtf_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1901_05423_gb300 import _native
+    return _native.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rtf_build", "rtf_build_batched", "rtf_sample", "rtf_sample_backward"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1901_05423_gb300 import _native
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _native.EXPORTS, f"binding lacks {name}"
+    assert lib.rtf_version().startswith(b"rtf")
+
+
+def test_struct_layout_matches_header():
+    from paper_1901_05423_gb300 import _native
+    assert ctypes.sizeof(_native.RtfForestC) == 64
+    # rtf_node is 16 bytes (u64 + 2 x i32) and rtf_dist 64 bytes
+    text = open(HEADER).read()
+    assert "uint64_t cdf;" in text and "int32_t child[2];" in text
+
+
+def test_workspace_sizes(lib):
+    a = lib.rtf_build_workspace_size(1 << 24, 1, 1 << 20)
+    b = lib.rtf_build_workspace_size(1 << 10, 1, 1 << 8)
+    assert a > b > 0
+    assert a % 256 == 0
+    # otherBounds (8 B) + distances (1 B) per element dominate
+    assert 9 * (1 << 24) <= a <= 12 * (1 << 24)
+    assert lib.rtf_build_workspace_size(0, 1, 1) == 0
+    assert lib.rtf_backward_workspace_size(1 << 20, 1) >= 16 * (1 << 20)
+
+
+def test_bad_arguments_rejected_without_gpu_work(lib):
+    from paper_1901_05423_gb300 import _native
+    EINVAL = 1
+    f = _native.RtfForestC()
+    assert lib.rtf_build(None, 10, 4, ctypes.byref(f), None, 0, None) == EINVAL
+    f = _native.RtfForestC(num_dists=1, flags=0, num_elems=10, num_cells=16, max_m=4,
+                           nodes=16, guide=16, dists=64, status=4)
+    # misaligned weights / bad m / inconsistent sizes never reach the GPU
+    assert lib.rtf_build(ctypes.c_void_p(4), 10, 4, ctypes.byref(f), ctypes.c_void_p(256),
+                         1 << 20, None) == EINVAL
+    assert lib.rtf_build(ctypes.c_void_p(16), 10, 31, ctypes.byref(f), ctypes.c_void_p(256),
+                         1 << 20, None) == EINVAL
+    assert lib.rtf_build(ctypes.c_void_p(16), 11, 4, ctypes.byref(f), ctypes.c_void_p(256),
+                         1 << 20, None) == EINVAL
+    assert lib.rtf_build(ctypes.c_void_p(16), 10, 4, ctypes.byref(f), ctypes.c_void_p(256),
+                         16, None) == 2  # workspace too small
+    assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, -1, 0, ctypes.c_void_p(16),
+                          ctypes.c_void_p(16), None) == EINVAL
+    assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 5, 1, ctypes.c_void_p(16),
+                          ctypes.c_void_p(16), None) == EINVAL  # 2-D needs a marginal
+    assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 0, 0, None, None,
+                          None) == 0  # nothing to do
+
+
+def test_plan_batched_host_logic():
+    from paper_1901_05423_gb300 import api
+    off, goff, m = api.plan_batched([3, 1, 5], [2, 0, 4])
+    assert off.tolist() == [0, 3, 4, 9]
+    assert goff.tolist() == [0, 4, 5, 21]
+    with pytest.raises(api.RtfError):
+        api.plan_batched([0, 2], [1, 1])
+    with pytest.raises(api.RtfError):
+        api.plan_batched([4, 4, 3], [1, 1, 1], marginal=True)  # marginal needs 2 weights
+    off, goff, m = api.plan_batched([4, 4, 2], [1, 1, 1], marginal=True)
+    assert off[-1] == 10
+
+
+def test_workload_generators_shapes():
+    from paper_1901_05423_gb300 import workloads as W
+    u = W.radical_inverse_u32(1 << 12)
+    assert u.dtype == np.uint32 and len(set(u.tolist())) == 1 << 12
+    assert np.array_equal(np.sort(u), W.sorted_radical_inverse_u32(1 << 12))
+    w, off = W.ragged_batch(64, seed=0)
+    sizes = np.diff(off)
+    assert sizes.min() >= 8 and sizes.max() <= 65536 and w.size == off[-1]
+    lum = W.env_map(32, 64, seed=0)
+    assert lum.shape == (32, 64) and lum.dtype == np.float32 and lum.min() > 0

@@ -539,3 +539,44 @@ def test_gradient_two_bins_closed_form():
     grad = o.grad(w, u, np.array([1], np.int32), np.array([1.0], np.float32))
     assert abs(grad[0] - (xi - 1) / 3.0) < 1e-15
     assert abs(grad[1] - (xi - x) / 3.0) < 1e-15
+
+
+def relaxed_forward_2d(lum64, u1, u2, r, c):
+    """Relaxed 2-D forward (test-side): row position through the row sums,
+    column position through the row's weights."""
+    R = lum64.sum(axis=1)
+    Cm = np.concatenate([[0.0], np.cumsum(R)])
+    xi1 = u1.astype(np.float64) / 2.0 ** 32
+    xi2 = u2.astype(np.float64) / 2.0 ** 32
+    y = (xi1 * Cm[-1] - Cm[r]) / R[r]
+    Crow = np.concatenate([np.zeros((lum64.shape[0], 1)), np.cumsum(lum64, axis=1)], axis=1)
+    x = (xi2 * R[r] - Crow[r, c]) / lum64[r, c]
+    return y, x
+
+
+def test_env_gradient_central_differences():
+    rng = np.random.default_rng(16)
+    H, Wd = 5, 7
+    lum = np.exp(rng.normal(0, 1, (H, Wd))).astype(np.float32)
+    rows, marg = o.build_env(lum, 8, 8)
+    u1 = rng.integers(0, TWO32, 600, dtype=np.uint64).astype(np.uint32)
+    u2 = rng.integers(0, TWO32, 600, dtype=np.uint64).astype(np.uint32)
+    r, c, pr, pc = o.sample_env(rows, marg, u1, u2)
+    keep = (pr > 0.01) & (pr < 0.99) & (pc > 0.01) & (pc < 0.99)
+    u1, u2, r, c = u1[keep], u2[keep], r[keep], c[keep]
+    gy = rng.normal(0, 1, u1.size).astype(np.float32)
+    gx = rng.normal(0, 1, u1.size).astype(np.float32)
+    grad = o.grad_env(lum, u1, u2, r, c, gy, gx)
+    lum64 = lum.astype(np.float64)
+    fd = np.zeros((H, Wd))
+    for k in range(H):
+        for j in range(Wd):
+            h = 1e-3 * lum64[k, j]
+            lp, lm = lum64.copy(), lum64.copy()
+            lp[k, j] += h
+            lm[k, j] -= h
+            yp, xp = relaxed_forward_2d(lp, u1, u2, r, c)
+            ym, xm = relaxed_forward_2d(lm, u1, u2, r, c)
+            fd[k, j] = (np.dot(gy.astype(np.float64), yp - ym) +
+                        np.dot(gx.astype(np.float64), xp - xm)) / (2 * h)
+    assert np.linalg.norm(grad - fd) <= 1e-5 * np.linalg.norm(fd)
