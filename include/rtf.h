@@ -166,6 +166,28 @@ rtf_status rtf_build(const float *w, int64_t n, int32_t m, rtf_forest *f,
                      void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * rtf_build without a caller workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory where
+ * they build (a plugin inside a host application that owns the device memory
+ * budget, a real-time loop that forbids allocation after start-up, a foreign
+ * runtime that hands over raw pointers but cannot reach an allocator).
+ * Arguments, results and device status are those of rtf_build; the caller
+ * still allocates w and the forest buffers.
+ *
+ * The scratch is a fixed 10 MiB array inside the library, held on every GPU
+ * that loads the library until the process exits.  It fits n <= 2^20 weights
+ * and m <= 16 guide bits; larger sizes return RTF_EWORKSPACE without touching
+ * the GPU.  The first call on a device looks up the array's device address
+ * with that device current, so make that first call before capturing a
+ * stream.  Every call shares the one array and leaves its contents behind
+ * (each call clears what must start at zero): calls that overlap on the GPU,
+ * from two streams or two threads, race and corrupt each other's results;
+ * serialise them.  Nothing here calls cudaMalloc or cudaFree.
+ */
+rtf_status rtf_build_static(const float *w, int64_t n, int32_t m, rtf_forest *f,
+                            void *stream);
+
+/*
  * Build many distributions at once (Sec. 5: several tables and trees are
  * built together by treating the index boundary of every distribution like a
  * cell boundary in Algorithm 1).

@@ -21,7 +21,7 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _OUT_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(_OUT_DIR, "librtf.so")
-SOURCES = ["build.cu", "sample.cu", "backward.cu", "api.cu"]
+SOURCES = ["build.cu", "sample.cu", "backward.cu", "api.cu", "static_ws.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -108,6 +108,8 @@ EXPORTS = {
     "rtf_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                  ctypes.POINTER(RtfForestC), ctypes.c_void_p, ctypes.c_size_t,
                                  ctypes.c_void_p]),
+    "rtf_build_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.POINTER(RtfForestC), ctypes.c_void_p]),
     "rtf_build_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.POINTER(RtfForestC),
                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),

@@ -140,6 +140,20 @@ def rtf_build(w: torch.Tensor, m: int, forest: Forest | None = None) -> Forest:
     return forest
 
 
+def rtf_build_static(w: torch.Tensor, m: int, forest: Forest | None = None) -> Forest:
+    """``rtf_build_static``: the build of ``rtf_build`` with the library's own
+    fixed scratch array (n <= 2^20, m <= 16) for callers that cannot allocate
+    a workspace; calls that overlap on the GPU race on that array."""
+    _need(w, torch.float32, "w")
+    n = w.numel()
+    if forest is None:
+        forest = Forest(1, 0, n, 1 << m, m, w.device)
+    cf = forest.c_struct()
+    _check(_native.load().rtf_build_static(_ptr(w), n, m, ctypes.byref(cf),
+                                           _stream_ptr(w.device)), "rtf_build_static")
+    return forest
+
+
 def plan_batched(sizes, m, marginal: bool = False):
     """Host-side plan: element offsets, guide offsets, total sizes."""
     sizes = np.asarray(sizes, dtype=np.int64)
