@@ -135,12 +135,9 @@ const char *rtf_status_string(rtf_status s);
 
 /*
  * Bytes of workspace rtf_build / rtf_build_batched need for N elements, D
- * distributions and G guide cells.
- *
- * The workspace carries state between builds (an epoch counter that replaces
- * a per-build reset of the Algorithm 1 synchronisation array), so it must be
- * zero-filled once before its first use (for example with cudaMemset), and
- * must not serve two builds that run at the same time.
+ * distributions and G guide cells.  The workspace needs no initial contents
+ * (each build writes or clears every part it reads) and keeps nothing between
+ * builds, but it must not serve two builds that run at the same time.
  */
 size_t rtf_build_workspace_size(int64_t num_elems, int32_t num_dists,
                                 int64_t num_cells);
@@ -155,7 +152,7 @@ size_t rtf_build_workspace_size(int64_t num_elems, int32_t num_dists,
  *   f        f->num_dists == 1, f->num_elems == n, f->num_cells == 2^m,
  *            f->max_m == m; nodes[n], guide[2^m], dists[1], status[1] allocated.
  *   ws       device workspace of at least rtf_build_workspace_size(n, 1, 2^m)
- *            bytes, 256-byte aligned, zero-filled before its first use.
+ *            bytes, 256-byte aligned.
  *
  * Steps (all on `stream`, no host synchronisation): validation and scale
  * (max exponent), exact integer CDF by a decoupled-lookback scan, keys

@@ -58,9 +58,7 @@ def _need(t: torch.Tensor, dtype: torch.dtype, name: str):
 
 
 def workspace(nbytes: int, device: torch.device, tag: str) -> torch.Tensor:
-    """A zero-filled device workspace of at least `nbytes`, cached per device
-    and tag (the build workspace must start zero-filled and then keeps its
-    epoch counter)."""
+    """A device workspace of at least `nbytes`, cached per device and tag."""
     key = (str(device), tag)
     ws = _workspaces.get(key)
     if ws is None or ws.numel() < nbytes:

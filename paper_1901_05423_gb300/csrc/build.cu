@@ -3,16 +3,18 @@
 // Sec. 3.2) for one or many distributions at once (Sec. 5).
 //
 // Kernels, in launch order:
-//   init_dists_kernel   per-distribution parameters from the plan; epoch + 1
+//   init_dists_kernel   per-distribution parameters from the plan
 //   scale_kernel        validation and max exponent (one read of w)
 //   scan_kernel         exact integer prefix sums of the tiles by a decoupled
 //                       lookback (second read of w); totals T and key
 //                       reciprocals; in marginal mode the last tile to finish
 //                       also scans the row totals
 //   forest_kernel       C_j, keys K_j, distances, Algorithm 1 inside each tile
-//                       in shared memory, the cross-tile merges through an
-//                       epoch-tagged global otherBounds; node records, roots,
-//                       guide entries of non-empty cells (third read of w)
+//                       in shared memory; node records, roots, guide entries
+//                       of non-empty cells; the tile's slice of the global
+//                       otherBounds (third read of w)
+//   forest_merge_kernel the hand-offs across tile edges: Algorithm 1 continued
+//                       through the global otherBounds
 //   guide_kernel        guide entries of cells that no key falls into: the
 //                       interval of the last key before them (carry-forward
 //                       scan with a decoupled lookback)
@@ -27,10 +29,8 @@ namespace rtf {
 // ---------------------------------------------------------------------------
 __global__ void init_dists_kernel(rtf_dist* dists, int D, const int64_t* offsets,
                                   const int32_t* m_arr, const int64_t* goff, int marginal,
-                                  int64_t n_single, int m_single, uint32_t* epoch,
-                                  uint32_t* status) {
+                                  int64_t n_single, int m_single, uint32_t* status) {
   int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d == 0) *epoch = *epoch + 1u;
   if (d >= D) return;
   rtf_dist P;
   if (offsets == nullptr) {
@@ -175,53 +175,6 @@ __device__ inline void finish_dist(rtf_dist* dists, int d, uint64_t T, int S, ui
   dists[d].scale = S;
 }
 
-// Lookback by warp 0: exclusive prefix of tile `tile` (the sum of the last
-// pieces of the predecessors back to the first one that published a prefix).
-__device__ inline uint64_t lookback_sum(const uint64_t* st, int64_t tile, uint32_t* status) {
-  const int lane = threadIdx.x & 31;
-  uint64_t E = 0;
-  int64_t look = tile - 1;
-  long long spins = 0;
-  while (look >= 0) {
-    int64_t idx = look - lane;
-    uint64_t s = idx >= 0 ? ld_acquire_u64(st + idx) : kFlagPrefix;
-    uint32_t flag = (uint32_t)(s >> 62);
-    unsigned inval = __ballot_sync(0xffffffffu, flag == 0);
-    unsigned pref = __ballot_sync(0xffffffffu, flag == 2);
-    unsigned upto;
-    if (pref) {
-      int p = __ffs(pref) - 1;
-      unsigned below = (p == 31) ? 0xffffffffu : ((2u << p) - 1u);
-      if (inval & below) {
-        if (++spins > kSpinLimit) {
-          raise_status(status, RTF_STATUS_TIMEOUT);
-          return E;
-        }
-        __nanosleep(32);
-        continue;
-      }
-      upto = below;
-    } else {
-      if (inval) {
-        if (++spins > kSpinLimit) {
-          raise_status(status, RTF_STATUS_TIMEOUT);
-          return E;
-        }
-        __nanosleep(32);
-        continue;
-      }
-      upto = 0xffffffffu;
-    }
-    uint64_t v = ((upto >> lane) & 1u) && idx >= 0 ? (s & kValueMask) : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    E += v;
-    if (pref) break;
-    look -= 32;
-  }
-  return E;
-}
-
 constexpr int kScanPer = kTile / kScanThreads;  // 8
 
 template <bool SEG>
@@ -236,7 +189,7 @@ __global__ void __launch_bounds__(kScanThreads)
   __shared__ int dfirst_s;
   __shared__ SegPair wtot[kScanThreads / 32];
   __shared__ SegPair btot;
-  __shared__ uint64_t E_s;
+  __shared__ LookbackShared lb;
   __shared__ int last_s;
 
   if (threadIdx.x == 0) tile_s = atomicAdd(&ctr->scan_ticket, 1u);
@@ -308,19 +261,12 @@ __global__ void __launch_bounds__(kScanThreads)
     st_release_u64(scan_status + tile, v);
   }
   uint64_t E = 0;
-  if (!head0 && threadIdx.x < 32) {
-    E = lookback_sum(scan_status, tile, status);
-    if (threadIdx.x == 0) {
-      E_s = E;
-      if (!last_head_in_tile) st_release_u64(scan_status + tile, ((E + A) & kValueMask) | kFlagPrefix);
-    }
-  }
+  if (!head0) E = block_lookback(scan_status, tile, true, &lb, status);
   if (threadIdx.x == 0) {
-    if (head0) E_s = 0;
-    tile_prefix[tile] = E_s;
+    if (!head0 && !last_head_in_tile)
+      st_release_u64(scan_status + tile, ((E + A) & kValueMask) | kFlagPrefix);
+    tile_prefix[tile] = E;
   }
-  __syncthreads();
-  E = E_s;
 
   // distributions whose last element lies in this tile
   if (e0 < t1) {
@@ -375,6 +321,7 @@ __global__ void __launch_bounds__(kScanThreads)
 // forest: Algorithm 1 per tile in shared memory, cross-tile merges in global
 // ---------------------------------------------------------------------------
 constexpr int kForestPer = kTile / kForestThreads;  // 4
+static_assert(kForestPer == 4, "the otherBounds write-out stores one int4 per thread");
 constexpr int32_t kUnset = 0x7FFFFFFF;
 
 struct ForestShared {
@@ -392,11 +339,11 @@ struct ForestShared {
   int dfirst;
   int dprev;
   int ndefer;
-  int64_t defer_parent[4];
-  int64_t defer_lo[4];
-  int64_t defer_hi[4];
-  int32_t defer_node[4];
-  int32_t defer_child[4];
+  int64_t defer_parent[kDeferCap];
+  int64_t defer_lo[kDeferCap];
+  int64_t defer_hi[kDeferCap];
+  int32_t defer_node[kDeferCap];
+  int32_t defer_child[kDeferCap];
 };
 
 struct ForestArgs {
@@ -411,8 +358,9 @@ struct ForestArgs {
   const uint64_t* tile_prefix;
   const uint32_t* dmax;
   uint8_t* delta;
-  unsigned long long* other;
-  const uint32_t* epoch;
+  int32_t* other;
+  uint4* items;
+  int32_t* item_count;
   uint32_t* status;
 };
 
@@ -433,35 +381,28 @@ __device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist&
   a.last[P.guide_off + (int64_t)c] = hi_l;
 }
 
-__device__ __forceinline__ unsigned long long pack_other(uint32_t epoch, int64_t bound) {
-  return ((unsigned long long)epoch << 32) | (unsigned long long)(uint32_t)bound;
-}
-
 // Continue Algorithm 1 through global memory from range [lo, hi] with node
-// `node` (local reference) of distribution P.
+// `node` (local reference) of distribution P.  This runs in the merge kernel,
+// after every tile has written its records, distances and otherBounds slice,
+// so the hand-offs are plain atomic exchanges.
 __device__ void climb_global(const ForestArgs& a, const rtf_dist& P, int64_t lo, int64_t hi,
-                             int32_t node, uint32_t epoch) {
+                             int32_t node) {
   for (int64_t guard = 0; guard <= a.N; ++guard) {  // each pass grows the range
-    uint32_t dl = lo > 0 ? (uint32_t)__ldcg(a.delta + lo - 1) : kDeltaInf;
-    uint32_t dr = (uint32_t)__ldcg(a.delta + hi);
+    uint32_t dl = lo > 0 ? (uint32_t)a.delta[lo - 1] : kDeltaInf;
+    uint32_t dr = (uint32_t)a.delta[hi];
     if (dl >= kDeltaInf && dr >= kDeltaInf) {
       rtf_node* root = a.nodes + lo;
       int32_t lo_l = (int32_t)(lo - P.elem_off);
       root->child[0] = ~(lo_l > 0 ? lo_l - 1 : 0);
       root->child[1] = node;
-      uint64_t Clo = __ldcg(&a.nodes[lo].cdf), Chi = __ldcg(&a.nodes[hi].cdf);
-      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, Chi));
+      finish_cell(a, P, lo, hi, key_for(P, a.nodes[lo].cdf), key_for(P, a.nodes[hi].cdf));
       return;
     }
     int child = dl > dr ? 0 : 1;
     int64_t parent = child ? lo : hi + 1;
     a.nodes[parent].child[child] = node;
-    __threadfence();
-    unsigned long long v =
-        atomicExch(a.other + parent, pack_other(epoch, child ? hi : lo));
-    if ((uint32_t)(v >> 32) != epoch) return;  // first of the two children
-    __threadfence();
-    int64_t ob = (int64_t)(uint32_t)v;
+    int ob = atomicExch(a.other + parent, (int)(child ? hi : lo));
+    if (ob < 0) return;  // first of the two children
     if (child)
       lo = ob;
     else
@@ -471,6 +412,22 @@ __device__ void climb_global(const ForestArgs& a, const rtf_dist& P, int64_t lo,
   raise_status(a.status, RTF_STATUS_TIMEOUT);
 }
 
+// A hand-off deferred by phase A because the sibling lies in the neighbouring
+// tile, packed as uint4 {parent, bound, node, dist}: the arriver's range is
+// [bound, parent-1] when it is the left child (bound < parent) and
+// [parent, bound] when it is the right child.
+__device__ void run_deferred(const ForestArgs& a, uint4 it) {
+  const int64_t parent = (int32_t)it.x, bound = (int32_t)it.y;
+  const int32_t node = (int32_t)it.z;
+  const int child = bound < parent ? 0 : 1;
+  const rtf_dist P = a.dists[it.w];
+  a.nodes[parent].child[child] = node;
+  const int ob = atomicExch(a.other + parent, (int)bound);
+  if (ob < 0) return;
+  const int64_t lo = child ? ob : bound, hi = child ? bound : ob;
+  climb_global(a, P, lo, hi, (int32_t)(parent - P.elem_off));
+}
+
 template <bool SEG>
 __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -478,7 +435,6 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
   const int64_t tile = blockIdx.x;
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
   const int tid = threadIdx.x;
-  const uint32_t epoch = *a.epoch;
 
   if (tid == 0) {
     int df = SEG ? find_dist(a.dists, 0, a.D - 1, t0) : 0;
@@ -633,14 +589,12 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
       int child = dl > dr ? 0 : 1;
       if ((child == 1 && lo == t0) || (child == 0 && hi == t1 - 1)) {
         int slot = atomicAdd(&s.ndefer, 1);
-        if (slot < 4) {
+        if (slot < kDeferCap) {
           s.defer_parent[slot] = child ? lo : hi + 1;
           s.defer_child[slot] = child;
           s.defer_node[slot] = node;
           s.defer_lo[slot] = lo;
           s.defer_hi[slot] = hi;
-        } else {
-          raise_status(a.status, RTF_STATUS_TIMEOUT);
         }
         break;
       }
@@ -678,48 +632,46 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
       if (c1 != kUnset) a.nodes[j].child[1] = c1;
     }
   }
-  __threadfence();
-  __syncthreads();
+  // this tile's slice of the global otherBounds: the far bound of every first
+  // arrival still waiting for its sibling, -1 everywhere else
+  if (e0 + kForestPer <= t1) {
+    int4 ob;
+    ob.x = s.other[e0 - t0 + 0] >= 0 ? (int)(t0 + s.other[e0 - t0 + 0]) : -1;
+    ob.y = s.other[e0 - t0 + 1] >= 0 ? (int)(t0 + s.other[e0 - t0 + 1]) : -1;
+    ob.z = s.other[e0 - t0 + 2] >= 0 ? (int)(t0 + s.other[e0 - t0 + 2]) : -1;
+    ob.w = s.other[e0 - t0 + 3] >= 0 ? (int)(t0 + s.other[e0 - t0 + 3]) : -1;
+    *reinterpret_cast<int4*>(a.other + e0) = ob;
+  } else {
+    for (int64_t j = e0; j < t1; ++j)
+      a.other[j] = s.other[j - t0] >= 0 ? (int)(t0 + s.other[j - t0]) : -1;
+  }
 
-  // ---- phase B: merges across tiles ----------------------------------------
-#pragma unroll 1
-  for (int k = 0; k < kForestPer; ++k) {
-    int64_t p = e0 + k;
-    if (p >= t1) break;
-    int ob = s.other[p - t0];
-    if (ob < 0) continue;
-    // a first arrival that no sibling met inside the tile
-    const int d = s.dist[p - t0];
-    rtf_dist P = a.dists[d];
-    int64_t b = t0 + ob;
-    int child = b < p ? 0 : 1;
-    unsigned long long v = atomicExch(a.other + p, pack_other(epoch, b));
-    if ((uint32_t)(v >> 32) != epoch) continue;
-    __threadfence();
-    int64_t o = (int64_t)(uint32_t)v;
-    int64_t lo = child ? o : b, hi = child ? b : o;
-    climb_global(a, P, lo, hi, (int32_t)(p - P.elem_off), epoch);
+  // ---- hand-offs across tile edges -------------------------------------------
+  // A first arrival that no sibling met inside the tile stays in this tile's
+  // slice of the global otherBounds (written above); a range that must merge
+  // with a sibling in the neighbouring tile is deferred to the merge kernel.
+  const int nd = s.ndefer;
+  if (tid == 0) {
+    if (nd > kDeferCap) raise_status(a.status, RTF_STATUS_TIMEOUT);
+    a.item_count[tile] = min(nd, kDeferCap);
   }
-  if (tid < min(s.ndefer, 4)) {
-    int slot = tid;
-    int64_t parent = s.defer_parent[slot];
-    int child = s.defer_child[slot];
-    int64_t lo = s.defer_lo[slot], hi = s.defer_hi[slot];
-    const int d = s.dist[lo - t0 >= 0 && lo - t0 < kTile ? lo - t0 : hi - t0];
-    rtf_dist P = a.dists[d];
-    a.nodes[parent].child[child] = s.defer_node[slot];
-    __threadfence();
-    unsigned long long v = atomicExch(a.other + parent, pack_other(epoch, child ? hi : lo));
-    if ((uint32_t)(v >> 32) == epoch) {
-      __threadfence();
-      int64_t o = (int64_t)(uint32_t)v;
-      if (child)
-        lo = o;
-      else
-        hi = o;
-      climb_global(a, P, lo, hi, (int32_t)(parent - P.elem_off), epoch);
-    }
+  if (tid < min(nd, kDeferCap)) {
+    const int child = s.defer_child[tid];
+    const int64_t bound = child ? s.defer_hi[tid] : s.defer_lo[tid];
+    const int d = s.dist[s.defer_lo[tid] - t0];
+    a.items[tile * kDeferCap + tid] = make_uint4((uint32_t)s.defer_parent[tid], (uint32_t)bound,
+                                                 (uint32_t)s.defer_node[tid], (uint32_t)d);
   }
+}
+
+// Hand-offs across tile edges, after every tile finished: one thread per
+// deferred range continues Algorithm 1 through the global otherBounds.
+__global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t ntiles) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tile = i / kDeferCap;
+  const int k = (int)(i % kDeferCap);
+  if (tile >= ntiles || k >= a.item_count[tile]) return;
+  run_deferred(a, a.items[tile * kDeferCap + k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -727,51 +679,13 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 16
 
-// Lookback for the carry-forward scan: the value of the nearest predecessor
-// tile that published a prefix.
-__device__ inline int32_t lookback_last(const uint64_t* st, int64_t tile, uint32_t* status) {
-  const int lane = threadIdx.x & 31;
-  int64_t look = tile - 1;
-  long long spins = 0;
-  while (look >= 0) {
-    int64_t idx = look - lane;
-    uint64_t s = idx >= 0 ? ld_acquire_u64(st + idx) : kFlagPrefix;
-    uint32_t flag = (uint32_t)(s >> 62);
-    unsigned inval = __ballot_sync(0xffffffffu, flag == 0);
-    unsigned pref = __ballot_sync(0xffffffffu, flag == 2);
-    if (pref) {
-      int p = __ffs(pref) - 1;
-      unsigned below = (p == 31) ? 0xffffffffu : ((2u << p) - 1u);
-      if (inval & below) {
-        if (++spins > kSpinLimit) {
-          raise_status(status, RTF_STATUS_TIMEOUT);
-          return 0;
-        }
-        __nanosleep(32);
-        continue;
-      }
-      uint64_t sv = __shfl_sync(0xffffffffu, s, p);
-      return (int32_t)(uint32_t)(sv & 0xffffffffull);
-    }
-    if (inval) {
-      if (++spins > kSpinLimit) {
-        raise_status(status, RTF_STATUS_TIMEOUT);
-        return 0;
-      }
-      __nanosleep(32);
-      continue;
-    }
-    look -= 32;
-  }
-  return 0;
-}
-
 __global__ void __launch_bounds__(kGuideThreads)
     guide_kernel(int64_t G, const int32_t* __restrict__ last, int32_t* guide, uint64_t* gstatus,
                  Counters* ctr, uint32_t* status) {
   __shared__ uint32_t tile_s;
   __shared__ int32_t wlast[kGuideThreads / 32];
   __shared__ int32_t carry_s;
+  __shared__ LookbackShared lb;
   if (threadIdx.x == 0) tile_s = atomicAdd(&ctr->guide_ticket, 1u);
   __syncthreads();
   const int64_t tile = tile_s;
@@ -817,9 +731,10 @@ __global__ void __launch_bounds__(kGuideThreads)
     need_s = (g0 < gend && v[0] < 0) ? 1 : 0;
   }
   __syncthreads();
-  if (warp == 0 && need_s) {
-    int32_t c = lookback_last(gstatus, tile, status);
-    if (lane == 0) {
+  if (need_s) {
+    int32_t c = (int32_t)(uint32_t)(block_lookback(gstatus, tile, false, &lb, status) &
+                                     0xffffffffull);
+    if (threadIdx.x == 0) {
       carry_s = c;
       if (tile_last < 0) st_release_u64(gstatus + tile, kFlagPrefix | (uint32_t)c);
     }
@@ -848,7 +763,6 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   const int64_t G = f->num_cells;
   WsLayout L = ws_layout(N, D, G);
   char* base = static_cast<char*>(ws);
-  uint32_t* epoch = reinterpret_cast<uint32_t*>(base + L.persist);
   Counters* ctr = reinterpret_cast<Counters*>(base + L.counters);
   uint32_t* dmax = reinterpret_cast<uint32_t*>(base + L.dmax);
   uint64_t* scan_status = reinterpret_cast<uint64_t*>(base + L.scan_status);
@@ -856,7 +770,9 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   int32_t* last = reinterpret_cast<int32_t*>(base + L.last);
   uint64_t* tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
   uint8_t* delta = reinterpret_cast<uint8_t*>(base + L.delta);
-  unsigned long long* other = reinterpret_cast<unsigned long long*>(base + L.other);
+  int32_t* other = reinterpret_cast<int32_t*>(base + L.other);
+  uint4* items = reinterpret_cast<uint4*>(base + L.items);
+  int32_t* item_count = reinterpret_cast<int32_t*>(base + L.item_count);
   const bool seg = D > 1;
   const int Dw = marginal ? D - 1 : D;
   const int64_t n_shared = marginal ? Nw : 0;
@@ -866,7 +782,7 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   if ((e = cudaMemsetAsync(last, 0xFF, sizeof(int32_t) * (size_t)G, st))) return e;
   if ((e = cudaMemsetAsync(f->status, 0, sizeof(uint32_t), st))) return e;
   init_dists_kernel<<<(D + 255) / 256, 256, 0, st>>>(f->dists, D, offsets, m_arr, goff, marginal,
-                                                      n_single, m_single, epoch, f->status);
+                                                      n_single, m_single, f->status);
   const int64_t nscale = (Nw + kScaleTile - 1) / kScaleTile;
   if (marginal || !seg) {
     // one group: a plain block max into dmax[0]
@@ -900,7 +816,8 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.dmax = dmax;
   fa.delta = delta;
   fa.other = other;
-  fa.epoch = epoch;
+  fa.items = items;
+  fa.item_count = item_count;
   fa.status = f->status;
   const size_t fsmem = sizeof(ForestShared);
   if (seg) {
@@ -913,6 +830,10 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
       return e;
     forest_kernel<false><<<(unsigned)num_tiles(N), kForestThreads, fsmem, st>>>(fa);
+  }
+  {
+    const int64_t nt = num_tiles(N);
+    forest_merge_kernel<<<(unsigned)((nt * kDeferCap + 127) / 128), 128, 0, st>>>(fa, nt);
   }
   const int64_t gtiles = (G + kGuideTile - 1) / kGuideTile;
   guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, f->guide, guide_status, ctr,

@@ -24,6 +24,7 @@ constexpr int kGuideThreads = 256;    // 16 cells per thread
 constexpr int kMaxThreads = 512;
 constexpr uint32_t kDeltaInf = 64;    // distance across a cell / distribution boundary
 constexpr long long kSpinLimit = 1ll << 22;   // bounded waits
+constexpr int kDeferCap = 4;          // cross-tile hand-offs a forest tile defers (<= 2 occur)
 
 // status-word flags of the decoupled lookback (top two bits of a u64)
 constexpr uint64_t kFlagAgg = 1ull << 62;
@@ -34,7 +35,6 @@ constexpr uint64_t kValueMask = (1ull << 62) - 1;
 // workspace layout (byte offsets, 256-aligned regions)
 // ---------------------------------------------------------------------------
 struct WsLayout {
-  size_t persist;      // u32 epoch (kept across builds)
   size_t zero_begin;   // start of the region zero-filled by every build
   size_t counters;     // u32 tickets / done counters
   size_t dmax;         // u32 [D] max float bits per distribution / group
@@ -44,7 +44,9 @@ struct WsLayout {
   size_t last;         // i32 [G] last leaf of each non-empty cell (set to -1)
   size_t tile_prefix;  // u64 [num_tiles]
   size_t delta;        // u8  [N]
-  size_t other;        // u64 [N] epoch-tagged otherBounds of Algorithm 1
+  size_t other;        // i32 [N] otherBounds of Algorithm 1 (written by every build)
+  size_t items;        // uint4 [num_tiles * kDeferCap] deferred hand-offs per tile
+  size_t item_count;   // i32 [num_tiles]
   size_t total;
 };
 
@@ -55,7 +57,6 @@ __host__ __device__ inline int64_t num_tiles(int64_t n) { return (n + kTile - 1)
 __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   WsLayout L;
   size_t o = 0;
-  L.persist = o; o += 256;
   L.zero_begin = o;
   L.counters = o; o += 256;
   L.dmax = o; o = align256(o + sizeof(uint32_t) * (size_t)D);
@@ -66,7 +67,9 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   L.last = o; o = align256(o + sizeof(int32_t) * (size_t)G);
   L.tile_prefix = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
   L.delta = o; o = align256(o + (size_t)N);
-  L.other = o; o = align256(o + sizeof(uint64_t) * (size_t)N);
+  L.other = o; o = align256(o + sizeof(int32_t) * (size_t)N);
+  L.items = o; o = align256(o + 16 * (size_t)kDeferCap * (size_t)num_tiles(N));
+  L.item_count = o; o = align256(o + sizeof(int32_t) * (size_t)num_tiles(N));
   L.total = o;
   return L;
 }
@@ -196,7 +199,26 @@ __device__ __forceinline__ uint32_t key_distance(uint64_t a, uint64_t b) {
   return 32u - (uint32_t)__clz((uint32_t)(a ^ b));
 }
 
+// Round a 64-bit unsigned integer to the nearest float32 (ties to even) with
+// integer operations only: normalise, keep 24 bits, round on the remaining 40
+// (the top 32 bits with a sticky bit carry everything the rounding needs).
+// GB300 runs 64-bit integer to float conversions on its fp64 pipe, which is
+// slow; this stays on the integer pipes.
+__device__ __forceinline__ float u64_to_f32(uint64_t x) {
+  if (x == 0) return 0.0f;
+  const int lz = __clzll(x);
+  const uint64_t y = x << lz;                        // bit 63 set
+  uint32_t top = (uint32_t)(y >> 32) | ((uint32_t)y != 0u ? 1u : 0u);
+  uint32_t mant = top >> 8;                          // 24 bits, bit 23 set
+  const uint32_t rest = top & 0xFFu;
+  mant += (rest > 0x80u || (rest == 0x80u && (mant & 1u))) ? 1u : 0u;
+  // a carry out of the 24 bits bumps the exponent field by one
+  const uint32_t bits = ((uint32_t)(63 - lz + 127) << 23) + mant - (1u << 23);
+  return __uint_as_float(bits);
+}
+
 // ---------------------------------------------------------------------------
+// memory ordering helpers// ---------------------------------------------------------------------------
 // memory ordering helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
@@ -373,7 +395,75 @@ __device__ inline uint32_t block_exclusive_u32(uint32_t x, uint32_t* warp_tot, u
   return r;
 }
 
-// Index of the distribution that owns element `e`: the largest d with
+// Block-wide decoupled lookback over u64 status words (flag in the top two
+// bits, value below).  Every thread of the block reads one predecessor status
+// per round, so one round covers blockDim tiles.  Returns, to every thread,
+// the sum of the values from tile-1 back to and including the nearest tile
+// that published a prefix (`sum` = true), or that prefix's value alone
+// (`sum` = false: the carry-forward scans, where an aggregate carries no
+// value).  Waits are bounded; on expiry RTF_STATUS_TIMEOUT is raised and the
+// partial result returned.
+struct LookbackShared {
+  int first_prefix;
+  int first_invalid;
+  uint64_t part[32];
+  uint64_t result;
+};
+
+__device__ __forceinline__ uint64_t block_lookback(const uint64_t* st, int64_t tile, bool sum,
+                                          LookbackShared* sh, uint32_t* status) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t E = 0;
+  int64_t look = tile - 1;
+  long long spins = 0;
+  while (look >= 0) {
+    if (tid == 0) {
+      sh->first_prefix = nt;
+      sh->first_invalid = nt;
+    }
+    __syncthreads();
+    const int64_t idx = look - tid;
+    uint64_t s = idx >= 0 ? ld_acquire_u64(st + idx) : kFlagPrefix;
+    const uint32_t flag = (uint32_t)(s >> 62);
+    if (flag == 2) atomicMin(&sh->first_prefix, tid);
+    if (flag == 0) atomicMin(&sh->first_invalid, tid);
+    __syncthreads();
+    const int p = sh->first_prefix, q = sh->first_invalid;
+    if (q < p) {
+      // a predecessor before the nearest prefix has not published yet
+      if (++spins > kSpinLimit) {
+        if (tid == 0) raise_status(status, RTF_STATUS_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+      __syncthreads();
+      continue;
+    }
+    uint64_t v = 0;
+    if (sum) {
+      v = (tid <= p && idx >= 0) ? (s & kValueMask) : 0ull;
+    } else {
+      v = (tid == p && idx >= 0) ? (s & kValueMask) : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh->part[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t t = 0;
+      for (int w = 0; w < (nt >> 5); ++w) t += sh->part[w];
+      sh->result = t;
+    }
+    __syncthreads();
+    E += sh->result;
+    if (p < nt) break;
+    look -= nt;
+  }
+  __syncthreads();
+  return E;
+}
+
+// Index of the distribution that owns element `e`// Index of the distribution that owns element `e`: the largest d with
 // dists[d].elem_off <= e (binary search over [lo, hi]).
 __device__ inline int find_dist(const rtf_dist* dists, int lo, int hi, int64_t e) {
   while (lo < hi) {

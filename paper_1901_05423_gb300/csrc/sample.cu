@@ -32,7 +32,7 @@ __device__ __forceinline__ uint64_t l2_evict_last_policy() {
 __device__ __forceinline__ void load_node(const rtf_node* p, uint64_t pol, uint64_t& cdf,
                                           int32_t& c0, int32_t& c1) {
   uint64_t a, b;
-  asm volatile("ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+  asm("ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
                : "=l"(a), "=l"(b)
                : "l"(p), "l"(pol));
   cdf = a;
@@ -42,23 +42,36 @@ __device__ __forceinline__ void load_node(const rtf_node* p, uint64_t pol, uint6
 
 __device__ __forceinline__ uint64_t load_cdf(const rtf_node* p, uint64_t pol) {
   uint64_t a;
-  asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(a) : "l"(p), "l"(pol));
+  asm("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(a) : "l"(p), "l"(pol));
   return a;
 }
 
-// In-bin position (u T - C_i 2^32) / (q 2^32) from d = t - C_i, the low 32 bits
-// r of u T and q = C_{i+1} - C_i: numerator and denominator are rounded to
-// float32 once each, then divided (three roundings in all).
+// t = floor(u T / 2^32) and r = (u T) mod 2^32 from two 32 x 32 -> 64 products
+// (T < 2^62, so u T_hi + floor(u T_lo / 2^32) cannot overflow).
+__device__ __forceinline__ void scale_sample(uint32_t u, uint64_t T, uint64_t& t, uint32_t& r) {
+  const uint64_t lo = (uint64_t)(uint32_t)T * u;
+  t = (uint64_t)(uint32_t)(T >> 32) * u + (lo >> 32);
+  r = (uint32_t)lo;
+}
+
+// In-bin position (u T - C_i 2^32) / (q 2^32) from d = t - C_i < q, the low 32
+// bits r of u T and q = C_{i+1} - C_i.  Numerator and denominator are rounded
+// to float32 once each (integer arithmetic, no fp64 pipe), and the quotient is
+// a reciprocal refined by one fused residual step: at most about 1.5 ulp from
+// the exact value.  The result is clamped below 1.
 __device__ __forceinline__ float in_bin_position(uint64_t d, uint32_t r, uint64_t q) {
   float num, den;
   if ((d >> 32) == 0) {
-    num = __ull2float_rn((d << 32) | r);
-    den = __ull2float_rn(q) * 4294967296.0f;
+    num = u64_to_f32((d << 32) | r);
+    den = u64_to_f32(q) * 4294967296.0f;
   } else {
-    num = __ull2float_rn(d);
-    den = __ull2float_rn(q);
+    num = u64_to_f32(d);
+    den = u64_to_f32(q);
   }
-  float p = __fdiv_rn(num, den);
+  const float rcp = __frcp_rn(den);
+  float p = num * rcp;
+  const float e = fmaf(-den, p, num);
+  p = fmaf(e, rcp, p);
   return fminf(p, 0x1.fffffep-1f);
 }
 
@@ -82,55 +95,100 @@ __device__ __forceinline__ DistView dist_view(const rtf_dist* dists, int d, cons
   return v;
 }
 
-// Algorithm 2 and the position for one sample of one distribution.  Every
-// index read from the structure is checked against n and the descent is capped
-// at 64 visits (a reachable path visits at most 2 + (32 - m) nodes), so a
-// structure left invalid by a failed build yields idx = -1 instead of an
-// out-of-bounds read.
+// Algorithm 2 and the position for K samples of one distribution at once: the
+// K descents advance in lockstep, so each thread keeps K independent node
+// loads in flight.  Every index read from the structure is checked against n
+// and the descent is capped at 64 visits (a reachable path visits at most
+// 2 + (32 - m) nodes), so a structure left invalid by a failed build yields
+// idx = -1 instead of an out-of-bounds read.
+//
+// After the descent one of C_i, C_{i+1} is the CDF value of the last node
+// visited (its own leaf on a right step, its left neighbour on a left step);
+// the other is loaded.  A guide hit loads both.
+template <int K, bool SMEM>
+__device__ __forceinline__ void sample_group(const DistView& v, const int32_t* gsm,
+                                             const uint32_t (&uu)[K], uint64_t pol,
+                                             int32_t (&idx)[K], float (&pos)[K]) {
+  int32_t j[K];
+  uint64_t t[K], clast[K];
+  uint32_t r[K], dir[K];  // dir: 0 no node visited, 1 last step right, 2 last step left
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t g = v.m ? (uu[k] >> (32 - v.m)) : 0u;
+    j[k] = SMEM ? gsm[g] : __ldg(v.guide + g);
+    scale_sample(uu[k], v.T, t[k], r[k]);
+    dir[k] = 0;
+    clast[k] = 0;
+  }
+  bool live = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) live |= j[k] >= 0;
+#pragma unroll 1
+  for (int step = 0; live && step < 64; ++step) {
+    uint64_t c[K];
+    int32_t c0[K], c1[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (j[k] >= 0) {
+        if ((int64_t)j[k] >= v.n) {
+          dir[k] = 3;   // invalid structure
+          j[k] = -1;
+        } else {
+          load_node(v.nodes + j[k], pol, c[k], c0[k], c1[k]);
+        }
+      }
+    }
+    live = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (j[k] >= 0) {
+        const bool left = t[k] < c[k];
+        j[k] = left ? c0[k] : c1[k];
+        clast[k] = c[k];
+        dir[k] = left ? 2u : 1u;
+        live |= j[k] >= 0;
+      }
+    }
+  }
+  uint64_t clo[K], chi[K];
+  bool ok[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int32_t i = ~j[k];
+    ok[k] = j[k] < 0 && dir[k] != 3 && (int64_t)i < v.n;
+    clo[k] = clast[k];
+    chi[k] = clast[k];
+    if (ok[k]) {
+      if (dir[k] != 1) clo[k] = load_cdf(v.nodes + i, pol);
+      if (dir[k] != 2) chi[k] = (i + 1 < v.n) ? load_cdf(v.nodes + i + 1, pol) : v.T;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (ok[k]) {
+      idx[k] = ~j[k];
+      pos[k] = in_bin_position(t[k] - clo[k], r[k], chi[k] - clo[k]);
+    } else {
+      idx[k] = -1;
+      pos[k] = 0.0f;
+    }
+  }
+}
+
 template <bool SMEM>
 __device__ __forceinline__ void sample_one(const DistView& v, const int32_t* gsm, uint32_t u,
                                            uint64_t pol, int32_t& idx, float& pos) {
-  const uint32_t g = v.m ? (u >> (32 - v.m)) : 0u;
-  int32_t j = SMEM ? gsm[g] : __ldg(v.guide + g);
-  const uint64_t t = __umul64hi(v.T, (uint64_t)u << 32);
-  const uint32_t r = u * (uint32_t)v.T;
-  uint64_t clo = 0, chi = 0;
-  int known = 0;  // 1: clo known, 2: chi known
-  int steps = 0;
-  while (j >= 0) {
-    if ((int64_t)j >= v.n || ++steps > 64) {
-      idx = -1;
-      pos = 0.0f;
-      return;
-    }
-    uint64_t c;
-    int32_t c0, c1;
-    load_node(v.nodes + j, pol, c, c0, c1);
-    if (t < c) {
-      j = c0;
-      chi = c;
-      known = 2;
-    } else {
-      j = c1;
-      clo = c;
-      known = 1;
-    }
-  }
-  const int32_t i = ~j;
-  if ((int64_t)i >= v.n) {
-    idx = -1;
-    pos = 0.0f;
-    return;
-  }
-  if (known != 1) clo = load_cdf(v.nodes + i, pol);
-  if (known != 2) chi = (i + 1 < v.n) ? load_cdf(v.nodes + i + 1, pol) : v.T;
-  idx = i;
-  pos = in_bin_position(t - clo, r, chi - clo);
+  uint32_t uu[1] = {u};
+  int32_t ii[1];
+  float pp[1];
+  sample_group<1, SMEM>(v, gsm, uu, pol, ii, pp);
+  idx = ii[0];
+  pos = pp[0];
 }
 
 // 1-D, one distribution (dist 0); four samples per thread per step.
 template <bool SMEM>
-__global__ void __launch_bounds__(kSampleThreads)
+__global__ void __launch_bounds__(kSampleThreads, 4)
     sample_single_kernel(const rtf_node* __restrict__ nodes, const int32_t* __restrict__ guide,
                          const rtf_dist* __restrict__ dists, const uint32_t* __restrict__ u,
                          int64_t count, int32_t* __restrict__ idx_out,
@@ -154,15 +212,13 @@ __global__ void __launch_bounds__(kSampleThreads)
   float4* p4 = reinterpret_cast<float4*>(pos_out);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nvec;
        q += (int64_t)gridDim.x * blockDim.x) {
-    uint4 uu = __ldcs(u4 + q);
-    int4 ii;
-    float4 pp;
-    sample_one<SMEM>(v, gsm, uu.x, pol, ii.x, pp.x);
-    sample_one<SMEM>(v, gsm, uu.y, pol, ii.y, pp.y);
-    sample_one<SMEM>(v, gsm, uu.z, pol, ii.z, pp.z);
-    sample_one<SMEM>(v, gsm, uu.w, pol, ii.w, pp.w);
-    __stcs(i4 + q, ii);
-    __stcs(p4 + q, pp);
+    const uint4 u4v = __ldcs(u4 + q);
+    uint32_t uu[4] = {u4v.x, u4v.y, u4v.z, u4v.w};
+    int32_t ii[4];
+    float pp[4];
+    sample_group<4, SMEM>(v, gsm, uu, pol, ii, pp);
+    __stcs(i4 + q, make_int4(ii[0], ii[1], ii[2], ii[3]));
+    __stcs(p4 + q, make_float4(pp[0], pp[1], pp[2], pp[3]));
   }
   // tail
   const int64_t rem0 = nvec << 2;

@@ -23,9 +23,8 @@ constexpr int32_t kStaticMaxBits = 16;
 constexpr size_t kStaticBytes = size_t(10) << 20;
 constexpr int kMaxDevices = 64;
 
-// Zero-filled when the module loads, which is the state the build's
-// synchronisation array must start from; the build clears everything else
-// that must start at zero on every call.
+// Every build clears or writes each part of its workspace that it reads, so
+// the array's leftover contents from the previous call do no harm.
 static __device__ __align__(256) unsigned char g_rtf_static_ws[kStaticBytes];
 
 std::mutex g_setup_lock;
