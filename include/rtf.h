@@ -125,6 +125,10 @@ typedef struct rtf_forest {
   int32_t *guide;    /* device [G] */
   rtf_dist *dists;   /* device [D] */
   uint32_t *status;  /* device [1]: RTF_STATUS_* bits, set to 0 by each build */
+  rtf_node *guide_nodes; /* device [G], 16-byte aligned: per cell, a copy of the
+                            record of the cell's root, or {0, ~i, ~i} for a cell
+                            that one interval i covers, so that the sampler takes
+                            the root's decision from the guide entry itself */
 } rtf_forest;
 
 /* Library version string. */
@@ -150,7 +154,8 @@ size_t rtf_build_workspace_size(int64_t num_elems, int32_t num_dists,
  *   n        1 <= n <= 2^31 - 2^16.
  *   m        guide bits, 0 <= m <= 30: 2^m cells (Sec. 2.5, Sec. 3.2).
  *   f        f->num_dists == 1, f->num_elems == n, f->num_cells == 2^m,
- *            f->max_m == m; nodes[n], guide[2^m], dists[1], status[1] allocated.
+ *            f->max_m == m; nodes[n], guide[2^m], guide_nodes[2^m], dists[1],
+ *            status[1] allocated.
  *   ws       device workspace of at least rtf_build_workspace_size(n, 1, 2^m)
  *            bytes, 256-byte aligned.
  *

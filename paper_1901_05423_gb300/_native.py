@@ -85,7 +85,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 class RtfForestC(ctypes.Structure):
-    """Mirror of ``rtf_forest`` in include/rtf.h (64 bytes)."""
+    """Mirror of ``rtf_forest`` in include/rtf.h (72 bytes)."""
     _fields_ = [
         ("num_dists", ctypes.c_int32),
         ("flags", ctypes.c_int32),
@@ -97,6 +97,7 @@ class RtfForestC(ctypes.Structure):
         ("guide", ctypes.c_void_p),
         ("dists", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
+        ("guide_nodes", ctypes.c_void_p),
     ]
 
 

@@ -354,6 +354,7 @@ struct ForestArgs {
   int64_t n_shared;
   rtf_node* nodes;
   int32_t* guide;
+  rtf_node* guide_nodes;
   int32_t* last;
   const uint64_t* tile_prefix;
   const uint32_t* dmax;
@@ -372,13 +373,28 @@ __device__ __forceinline__ uint64_t key_for(const rtf_dist& P, uint64_t C) {
 // Root of a finished cell [lo, hi] (global element indices) of distribution P:
 // guide entry and last-leaf entry of the cell.  K_lo / K_hi are the keys.
 __device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist& P, int64_t lo,
-                                            int64_t hi, uint64_t Klo, uint64_t Khi) {
+                                            int64_t hi, uint64_t Klo, uint64_t Khi, uint64_t Clo,
+                                            int32_t top) {
   uint64_t c = cell_of(Klo, P.m);
   if (c >= (1ull << P.m)) return;  // unreachable trailing cell of zero-width bins
   int32_t lo_l = (int32_t)(lo - P.elem_off), hi_l = (int32_t)(hi - P.elem_off);
   uint64_t start = c << (32 - P.m);
-  a.guide[P.guide_off + (int64_t)c] = (Khi == start) ? ~hi_l : lo_l;
-  a.last[P.guide_off + (int64_t)c] = hi_l;
+  const int64_t gi = P.guide_off + (int64_t)c;
+  rtf_node rec;
+  if (Khi == start) {
+    // one interval covers the whole cell (all its keys equal the cell start)
+    a.guide[gi] = ~hi_l;
+    rec.cdf = 0;
+    rec.child[0] = ~hi_l;
+    rec.child[1] = ~hi_l;
+  } else {
+    a.guide[gi] = lo_l;
+    rec.cdf = Clo;
+    rec.child[0] = ~(lo_l > 0 ? lo_l - 1 : 0);
+    rec.child[1] = top;
+  }
+  a.guide_nodes[gi] = rec;
+  a.last[gi] = hi_l;
 }
 
 // Continue Algorithm 1 through global memory from range [lo, hi] with node
@@ -395,7 +411,8 @@ __device__ void climb_global(const ForestArgs& a, const rtf_dist& P, int64_t lo,
       int32_t lo_l = (int32_t)(lo - P.elem_off);
       root->child[0] = ~(lo_l > 0 ? lo_l - 1 : 0);
       root->child[1] = node;
-      finish_cell(a, P, lo, hi, key_for(P, a.nodes[lo].cdf), key_for(P, a.nodes[hi].cdf));
+      const uint64_t Clo = a.nodes[lo].cdf;
+      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, a.nodes[hi].cdf), Clo, node);
       return;
     }
     int child = dl > dr ? 0 : 1;
@@ -583,7 +600,7 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
         s.child[lo - t0][0] = ~(lo_l > 0 ? lo_l - 1 : 0);
         s.child[lo - t0][1] = node;
         rtf_dist P = a.dists[d];
-        finish_cell(a, P, lo, hi, s.K[lo - t0 + 1], s.K[hi - t0 + 1]);
+        finish_cell(a, P, lo, hi, s.K[lo - t0 + 1], s.K[hi - t0 + 1], s.C[lo - t0 + 1], node);
         break;
       }
       int child = dl > dr ? 0 : 1;
@@ -680,8 +697,8 @@ __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t
 constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 16
 
 __global__ void __launch_bounds__(kGuideThreads)
-    guide_kernel(int64_t G, const int32_t* __restrict__ last, int32_t* guide, uint64_t* gstatus,
-                 Counters* ctr, uint32_t* status) {
+    guide_kernel(int64_t G, const int32_t* __restrict__ last, int32_t* guide,
+                 rtf_node* guide_nodes, uint64_t* gstatus, Counters* ctr, uint32_t* status) {
   __shared__ uint32_t tile_s;
   __shared__ int32_t wlast[kGuideThreads / 32];
   __shared__ int32_t carry_s;
@@ -749,6 +766,11 @@ __global__ void __launch_bounds__(kGuideThreads)
       carry = v[k];
     } else {
       guide[g] = ~carry;
+      rtf_node rec;
+      rec.cdf = 0;
+      rec.child[0] = ~carry;
+      rec.child[1] = ~carry;
+      guide_nodes[g] = rec;
     }
   }
 }
@@ -811,6 +833,7 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.n_shared = n_shared;
   fa.nodes = f->nodes;
   fa.guide = f->guide;
+  fa.guide_nodes = f->guide_nodes;
   fa.last = last;
   fa.tile_prefix = tile_prefix;
   fa.dmax = dmax;
@@ -836,8 +859,8 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
     forest_merge_kernel<<<(unsigned)((nt * kDeferCap + 127) / 128), 128, 0, st>>>(fa, nt);
   }
   const int64_t gtiles = (G + kGuideTile - 1) / kGuideTile;
-  guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, f->guide, guide_status, ctr,
-                                                           f->status);
+  guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, f->guide, f->guide_nodes,
+                                                           guide_status, ctr, f->status);
   return cudaGetLastError();
 }
 

@@ -199,22 +199,18 @@ __device__ __forceinline__ uint32_t key_distance(uint64_t a, uint64_t b) {
   return 32u - (uint32_t)__clz((uint32_t)(a ^ b));
 }
 
-// Round a 64-bit unsigned integer to the nearest float32 (ties to even) with
-// integer operations only: normalise, keep 24 bits, round on the remaining 40
-// (the top 32 bits with a sticky bit carry everything the rounding needs).
-// GB300 runs 64-bit integer to float conversions on its fp64 pipe, which is
-// slow; this stays on the integer pipes.
+// Round a 64-bit unsigned integer to the nearest float32 (ties to even)
+// without the 64-bit conversion instruction (which GB300 runs on its slow fp64
+// pipe): normalise, keep the top 32 bits with every lower bit folded into a
+// sticky bit 0 (enough for a correctly rounded 24-bit result), convert those
+// 32 bits, and scale by an exact power of two.
 __device__ __forceinline__ float u64_to_f32(uint64_t x) {
-  if (x == 0) return 0.0f;
-  const int lz = __clzll(x);
-  const uint64_t y = x << lz;                        // bit 63 set
-  uint32_t top = (uint32_t)(y >> 32) | ((uint32_t)y != 0u ? 1u : 0u);
-  uint32_t mant = top >> 8;                          // 24 bits, bit 23 set
-  const uint32_t rest = top & 0xFFu;
-  mant += (rest > 0x80u || (rest == 0x80u && (mant & 1u))) ? 1u : 0u;
-  // a carry out of the 24 bits bumps the exponent field by one
-  const uint32_t bits = ((uint32_t)(63 - lz + 127) << 23) + mant - (1u << 23);
-  return __uint_as_float(bits);
+  const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
+  if (hi == 0) return __uint2float_rn(lo);
+  const int lz = __clz(hi);                              // 0..31
+  uint32_t top = __funnelshift_l(lo, hi, lz);            // high word of x << lz
+  top |= ((lo << lz) != 0u) ? 1u : 0u;                   // sticky
+  return __uint2float_rn(top) * __uint_as_float((uint32_t)(127 + 32 - lz) << 23);
 }
 
 // ---------------------------------------------------------------------------

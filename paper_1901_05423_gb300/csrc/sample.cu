@@ -21,7 +21,22 @@
 namespace rtf {
 
 constexpr int kSampleThreads = 256;
-constexpr int kSmemGuideMaxBits = 13;  // 32 KB of guide in shared memory
+constexpr int kSmemGuideMaxBits = 11;  // 32 KB of guide records in shared memory
+
+// Tunables of the single-distribution sampler (compile-time): samples per
+// thread descending in lockstep, the minimum resident blocks per SM given to
+// the register allocator (0 = none), and the L2 fetch size requested with each
+// node load (0 = default, 1 = 128 B, 2 = 256 B; a cell's records are
+// contiguous, so a larger fetch brings the rest of its tree along).
+#ifndef RTF_SAMPLE_K
+#define RTF_SAMPLE_K 4
+#endif
+#ifndef RTF_SAMPLE_MINB
+#define RTF_SAMPLE_MINB 0
+#endif
+#ifndef RTF_NODE_PREFETCH
+#define RTF_NODE_PREFETCH 0
+#endif
 
 __device__ __forceinline__ uint64_t l2_evict_last_policy() {
   uint64_t pol;
@@ -32,9 +47,19 @@ __device__ __forceinline__ uint64_t l2_evict_last_policy() {
 __device__ __forceinline__ void load_node(const rtf_node* p, uint64_t pol, uint64_t& cdf,
                                           int32_t& c0, int32_t& c1) {
   uint64_t a, b;
+#if RTF_NODE_PREFETCH == 2
+  asm("ld.global.L2::cache_hint.L2::256B.v2.u64 {%0, %1}, [%2], %3;"
+      : "=l"(a), "=l"(b)
+      : "l"(p), "l"(pol));
+#elif RTF_NODE_PREFETCH == 1
+  asm("ld.global.L2::cache_hint.L2::128B.v2.u64 {%0, %1}, [%2], %3;"
+      : "=l"(a), "=l"(b)
+      : "l"(p), "l"(pol));
+#else
   asm("ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
-               : "=l"(a), "=l"(b)
-               : "l"(p), "l"(pol));
+      : "=l"(a), "=l"(b)
+      : "l"(p), "l"(pol));
+#endif
   cdf = a;
   c0 = (int32_t)(uint32_t)(b & 0xffffffffull);
   c1 = (int32_t)(uint32_t)(b >> 32);
@@ -56,9 +81,9 @@ __device__ __forceinline__ void scale_sample(uint32_t u, uint64_t T, uint64_t& t
 
 // In-bin position (u T - C_i 2^32) / (q 2^32) from d = t - C_i < q, the low 32
 // bits r of u T and q = C_{i+1} - C_i.  Numerator and denominator are rounded
-// to float32 once each (integer arithmetic, no fp64 pipe), and the quotient is
-// a reciprocal refined by one fused residual step: at most about 1.5 ulp from
-// the exact value.  The result is clamped below 1.
+// to float32 once each (no fp64 pipe), the quotient is the hardware
+// reciprocal estimate refined by one fused residual step: within about 1.5 ulp
+// of the exact value.  The result is clamped below 1.
 __device__ __forceinline__ float in_bin_position(uint64_t d, uint32_t r, uint64_t q) {
   float num, den;
   if ((d >> 32) == 0) {
@@ -68,7 +93,8 @@ __device__ __forceinline__ float in_bin_position(uint64_t d, uint32_t r, uint64_
     num = u64_to_f32(d);
     den = u64_to_f32(q);
   }
-  const float rcp = __frcp_rn(den);
+  float rcp;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rcp) : "f"(den));
   float p = num * rcp;
   const float e = fmaf(-den, p, num);
   p = fmaf(e, rcp, p);
@@ -77,14 +103,14 @@ __device__ __forceinline__ float in_bin_position(uint64_t d, uint32_t r, uint64_
 
 struct DistView {
   const rtf_node* nodes;  // records of the distribution
-  const int32_t* guide;   // its guide table
+  const rtf_node* guide;  // its guide records
   uint64_t T;
   int64_t n;
   int m;
 };
 
 __device__ __forceinline__ DistView dist_view(const rtf_dist* dists, int d, const rtf_node* nodes,
-                                              const int32_t* guide) {
+                                              const rtf_node* guide) {
   rtf_dist P = dists[d];
   DistView v;
   v.nodes = nodes + P.elem_off;
@@ -109,20 +135,35 @@ template <int K, bool SMEM>
 __device__ __forceinline__ void sample_group(const DistView& v, const int32_t* gsm,
                                              const uint32_t (&uu)[K], uint64_t pol,
                                              int32_t (&idx)[K], float (&pos)[K]) {
+  // CDF values are below 2^62, so 2^63 marks "no CDF value known yet"
+  constexpr uint64_t kNone = 1ull << 63;
+  const uint32_t n32 = (uint32_t)v.n;
   int32_t j[K];
   uint64_t t[K], clast[K];
-  uint32_t r[K], dir[K];  // dir: 0 no node visited, 1 last step right, 2 last step left
+  uint32_t r[K];
+  // the guide record takes the root's decision (left neighbour interval or the
+  // cell's tree); a cell that one interval covers holds {0, ~i, ~i}
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint32_t g = v.m ? (uu[k] >> (32 - v.m)) : 0u;
-    j[k] = SMEM ? gsm[g] : __ldg(v.guide + g);
     scale_sample(uu[k], v.T, t[k], r[k]);
-    dir[k] = 0;
-    clast[k] = 0;
+    uint64_t c;
+    int32_t c0, c1;
+    if (SMEM) {
+      const uint4 e = reinterpret_cast<const uint4*>(gsm)[g];
+      c = ((uint64_t)e.y << 32) | e.x;
+      c0 = (int32_t)e.z;
+      c1 = (int32_t)e.w;
+    } else {
+      load_node(v.guide + g, pol, c, c0, c1);
+    }
+    j[k] = t[k] < c ? c0 : c1;
+    clast[k] = c0 != c1 ? c : kNone;
   }
   bool live = false;
 #pragma unroll
   for (int k = 0; k < K; ++k) live |= j[k] >= 0;
+  bool bad = false;
 #pragma unroll 1
   for (int step = 0; live && step < 64; ++step) {
     uint64_t c[K];
@@ -130,8 +171,8 @@ __device__ __forceinline__ void sample_group(const DistView& v, const int32_t* g
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (j[k] >= 0) {
-        if ((int64_t)j[k] >= v.n) {
-          dir[k] = 3;   // invalid structure
+        if ((uint32_t)j[k] >= n32) {
+          bad = true;    // invalid structure: stop this descent
           j[k] = -1;
         } else {
           load_node(v.nodes + j[k], pol, c[k], c0[k], c1[k]);
@@ -142,25 +183,27 @@ __device__ __forceinline__ void sample_group(const DistView& v, const int32_t* g
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (j[k] >= 0) {
-        const bool left = t[k] < c[k];
-        j[k] = left ? c0[k] : c1[k];
+        j[k] = t[k] < c[k] ? c0[k] : c1[k];
         clast[k] = c[k];
-        dir[k] = left ? 2u : 1u;
         live |= j[k] >= 0;
       }
     }
   }
+  bad |= live;  // a descent longer than any reachable path
   uint64_t clo[K], chi[K];
   bool ok[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int32_t i = ~j[k];
-    ok[k] = j[k] < 0 && dir[k] != 3 && (int64_t)i < v.n;
+    const uint32_t i = (uint32_t)~j[k];
+    ok[k] = !bad && i < n32;
+    // the last node visited holds C_{i+1} after a left step, C_i after a right one
+    const bool have_hi = clast[k] != kNone && t[k] < clast[k];
+    const bool have_lo = clast[k] != kNone && !have_hi;
     clo[k] = clast[k];
     chi[k] = clast[k];
     if (ok[k]) {
-      if (dir[k] != 1) clo[k] = load_cdf(v.nodes + i, pol);
-      if (dir[k] != 2) chi[k] = (i + 1 < v.n) ? load_cdf(v.nodes + i + 1, pol) : v.T;
+      if (!have_lo) clo[k] = load_cdf(v.nodes + i, pol);
+      if (!have_hi) chi[k] = (i + 1 < n32) ? load_cdf(v.nodes + i + 1, pol) : v.T;
     }
   }
 #pragma unroll
@@ -186,13 +229,17 @@ __device__ __forceinline__ void sample_one(const DistView& v, const int32_t* gsm
   pos = pp[0];
 }
 
-// 1-D, one distribution (dist 0); four samples per thread per step.
+// 1-D, one distribution (dist 0); RTF_SAMPLE_K samples per thread per step
+// (u, idx and pos move as 16-byte vectors, four samples each).
 template <bool SMEM>
-__global__ void __launch_bounds__(kSampleThreads, 4)
-    sample_single_kernel(const rtf_node* __restrict__ nodes, const int32_t* __restrict__ guide,
+__global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
+    sample_single_kernel(const rtf_node* __restrict__ nodes, const rtf_node* __restrict__ guide,
                          const rtf_dist* __restrict__ dists, const uint32_t* __restrict__ u,
                          int64_t count, int32_t* __restrict__ idx_out,
                          float* __restrict__ pos_out, int cap_bits, uint32_t* status) {
+  constexpr int K = RTF_SAMPLE_K;
+  static_assert(K == 1 || K == 2 || K == 4 || K == 8, "samples per thread");
+  constexpr int V = K >= 4 ? K / 4 : 1;   // 16-byte vectors per step
   extern __shared__ int32_t gsm[];
   const DistView v = dist_view(dists, 0, nodes, guide);
   if (SMEM && v.m > cap_bits) {
@@ -201,8 +248,9 @@ __global__ void __launch_bounds__(kSampleThreads, 4)
     return;
   }
   if (SMEM) {
-    const int cells = 1 << v.m;
-    for (int k = threadIdx.x; k < cells; k += blockDim.x) gsm[k] = v.guide[k];
+    const int words = 4 << v.m;
+    const int32_t* src = reinterpret_cast<const int32_t*>(v.guide);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) gsm[k] = src[k];
     __syncthreads();
   }
   const uint64_t pol = l2_evict_last_policy();
@@ -210,19 +258,48 @@ __global__ void __launch_bounds__(kSampleThreads, 4)
   const uint4* u4 = reinterpret_cast<const uint4*>(u);
   int4* i4 = reinterpret_cast<int4*>(idx_out);
   float4* p4 = reinterpret_cast<float4*>(pos_out);
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nvec;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 u4v = __ldcs(u4 + q);
-    uint32_t uu[4] = {u4v.x, u4v.y, u4v.z, u4v.w};
-    int32_t ii[4];
-    float pp[4];
-    sample_group<4, SMEM>(v, gsm, uu, pol, ii, pp);
-    __stcs(i4 + q, make_int4(ii[0], ii[1], ii[2], ii[3]));
-    __stcs(p4 + q, make_float4(pp[0], pp[1], pp[2], pp[3]));
+  if (K >= 4) {
+    const int64_t ngroups = nvec / V;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ngroups;
+         q += (int64_t)gridDim.x * blockDim.x) {
+      uint32_t uu[K];
+      int32_t ii[K];
+      float pp[K];
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const uint4 x = __ldcs(u4 + q * V + t);
+        uu[4 * t] = x.x;
+        uu[4 * t + 1] = x.y;
+        uu[4 * t + 2] = x.z;
+        uu[4 * t + 3] = x.w;
+      }
+      sample_group<K, SMEM>(v, gsm, uu, pol, ii, pp);
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        __stcs(i4 + q * V + t, make_int4(ii[4 * t], ii[4 * t + 1], ii[4 * t + 2], ii[4 * t + 3]));
+        __stcs(p4 + q * V + t, make_float4(pp[4 * t], pp[4 * t + 1], pp[4 * t + 2], pp[4 * t + 3]));
+      }
+    }
+  } else {
+    const int64_t nsub = nvec * (4 / K);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nsub;
+         q += (int64_t)gridDim.x * blockDim.x) {
+      uint32_t uu[K];
+      int32_t ii[K];
+      float pp[K];
+#pragma unroll
+      for (int t = 0; t < K; ++t) uu[t] = __ldcs(u + q * K + t);
+      sample_group<K, SMEM>(v, gsm, uu, pol, ii, pp);
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        __stcs(idx_out + q * K + t, ii[t]);
+        __stcs(pos_out + q * K + t, pp[t]);
+      }
+    }
   }
+  const int64_t done = (K >= 4) ? (nvec / V) * V * 4 : nvec * 4;
   // tail
-  const int64_t rem0 = nvec << 2;
-  for (int64_t s = rem0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < count;
+  for (int64_t s = done + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < count;
        s += (int64_t)gridDim.x * blockDim.x) {
     int32_t ii;
     float pp;
@@ -234,7 +311,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4)
 
 // 1-D with a distribution id per sample.
 __global__ void __launch_bounds__(kSampleThreads)
-    sample_tagged_kernel(const rtf_node* __restrict__ nodes, const int32_t* __restrict__ guide,
+    sample_tagged_kernel(const rtf_node* __restrict__ nodes, const rtf_node* __restrict__ guide,
                          const rtf_dist* __restrict__ dists, int D,
                          const uint32_t* __restrict__ u, const int32_t* __restrict__ dist_id,
                          int64_t count, int32_t* __restrict__ idx_out,
@@ -260,7 +337,7 @@ __global__ void __launch_bounds__(kSampleThreads)
 // 2-D: the row through the marginal (last distribution) with u1, the column
 // through that row's distribution with u2 (Sec. 5).
 __global__ void __launch_bounds__(kSampleThreads)
-    sample_2d_kernel(const rtf_node* __restrict__ nodes, const int32_t* __restrict__ guide,
+    sample_2d_kernel(const rtf_node* __restrict__ nodes, const rtf_node* __restrict__ guide,
                      const rtf_dist* __restrict__ dists, int D, const uint2* __restrict__ u,
                      int64_t count, int2* __restrict__ idx_out, float2* __restrict__ pos_out) {
   const uint64_t pol = l2_evict_last_policy();
@@ -302,27 +379,27 @@ cudaError_t launch_sample(const rtf_forest* f, const uint32_t* u, const int32_t*
   if (mode == RTF_SAMPLE_2D) {
     int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
     sample_2d_kernel<<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
+        f->nodes, f->guide_nodes, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
         reinterpret_cast<int2*>(idx_out), reinterpret_cast<float2*>(pos_out));
     return cudaGetLastError();
   }
   if (dist_id != nullptr) {
     int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
     sample_tagged_kernel<<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
+        f->nodes, f->guide_nodes, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
         f->status);
     return cudaGetLastError();
   }
   const int64_t per_block = (int64_t)kSampleThreads * 4;
   if (f->max_m <= kSmemGuideMaxBits && f->num_dists >= 1) {
-    size_t smem = sizeof(int32_t) << f->max_m;
+    size_t smem = sizeof(rtf_node) << f->max_m;
     int64_t blocks = min((int64_t)sms * 8, (count + per_block - 1) / per_block);
     sample_single_kernel<true><<<(unsigned)blocks, kSampleThreads, smem, st>>>(
-        f->nodes, f->guide, f->dists, u, count, idx_out, pos_out, f->max_m, f->status);
+        f->nodes, f->guide_nodes, f->dists, u, count, idx_out, pos_out, f->max_m, f->status);
   } else {
     int64_t blocks = min((int64_t)sms * 8, (count + per_block - 1) / per_block);
     sample_single_kernel<false><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide, f->dists, u, count, idx_out, pos_out, 31, f->status);
+        f->nodes, f->guide_nodes, f->dists, u, count, idx_out, pos_out, 31, f->status);
   }
   return cudaGetLastError();
 }

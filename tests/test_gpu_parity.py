@@ -49,6 +49,17 @@ def check_structure(f, ref, elem_off=0, guide_off=0, n=None, cells=None):
     assert bad.size == 0, f"{bad.size} node records differ, first {bad[:5]}"
     badg = np.nonzero(g != ref.guide)[0]
     assert badg.size == 0, f"{badg.size} guide cells differ, first {badg[:5]}"
+    # guide records: a copy of each root's record, {0, ~i, ~i} for one interval
+    rec = f.guide_nodes.view(torch.int32).view(f.num_cells, 4)[guide_off:guide_off + cells]
+    rec = rec.cpu().numpy()
+    rec_c = rec[:, 0:2].copy().view(np.uint64).reshape(-1)
+    root = ref.guide >= 0
+    j0 = np.where(root, ref.guide, 0)
+    exp_c = np.where(root, ref.C[j0], np.uint64(0))
+    exp_c0 = np.where(root, ref.nodes[j0, 0], ref.guide)
+    exp_c1 = np.where(root, ref.nodes[j0, 1], ref.guide)
+    assert np.array_equal(rec_c, exp_c), "guide record CDF"
+    assert np.array_equal(rec[:, 2], exp_c0) and np.array_equal(rec[:, 3], exp_c1), "guide record children"
 
 
 def check_samples(idx, pos, ridx, rpos):
@@ -143,9 +154,8 @@ def test_worked_example_fig11_cells_power_of_two():
     build_and_check(w, 4)
 
 
-def test_rebuild_reuses_workspace_epochs():
-    """Repeated builds through one workspace (epoch-tagged synchronisation)
-    give identical structures."""
+def test_rebuild_reuses_workspace():
+    """Repeated builds through one cached workspace give identical structures."""
     w = W.lognormal_weights(50000, seed=3, sigma=2.0)
     f1, ref = build_and_check(w, 12)
     snap = f1.nodes.clone()
@@ -154,6 +164,20 @@ def test_rebuild_reuses_workspace_epochs():
         torch.cuda.synchronize()
         f2.check_status()
         assert torch.equal(f2.nodes, snap)
+
+
+def test_workspace_reused_across_sizes():
+    """A workspace that served a larger batched build (whose regions lie
+    elsewhere) serves smaller and differently shaped builds correctly."""
+    wb, offb = W.ragged_batch(600, seed=9)
+    sizes = np.diff(offb)
+    ms = np.clip(np.round(np.log2(sizes)).astype(int), 3, 16)
+    f = api.rtf_build_batched(to_dev(wb), sizes, ms)
+    torch.cuda.synchronize()
+    f.check_status()
+    for n, m, seed in ((300000, 14, 1), (4097, 5, 2), (1 << 20, 18, 3)):
+        w = W.lognormal_weights(n, seed=seed, sigma=2.0)
+        build_and_check(w, m)
 
 
 def test_status_bits_for_bad_weights():

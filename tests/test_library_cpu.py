@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_struct_layout_matches_header():
     from paper_1901_05423_gb300 import _native
-    assert ctypes.sizeof(_native.RtfForestC) == 64
+    assert ctypes.sizeof(_native.RtfForestC) == 72
     # rtf_node is 16 bytes (u64 + 2 x i32) and rtf_dist 64 bytes
     text = open(HEADER).read()
     assert "uint64_t cdf;" in text and "int32_t child[2];" in text
@@ -66,7 +66,7 @@ def test_bad_arguments_rejected_without_gpu_work(lib):
     f = _native.RtfForestC()
     assert lib.rtf_build(None, 10, 4, ctypes.byref(f), None, 0, None) == EINVAL
     f = _native.RtfForestC(num_dists=1, flags=0, num_elems=10, num_cells=16, max_m=4,
-                           nodes=16, guide=16, dists=64, status=4)
+                           nodes=16, guide=16, dists=64, status=4, guide_nodes=32)
     # misaligned weights / bad m / inconsistent sizes never reach the GPU
     assert lib.rtf_build(ctypes.c_void_p(4), 10, 4, ctypes.byref(f), ctypes.c_void_p(256),
                          1 << 20, None) == EINVAL
