@@ -319,6 +319,9 @@ def gpu_arm(args):
         "gpu_launches": 10 * args.steps,
         "clocks": clk.summary(),
     }
+    if rank == 0 and not args.no_extras:
+        line["extras"] = {"ragged_batch": extra_ragged(dev), "env_map_2d": extra_env_map(dev),
+                          "backward_vs_forward": extra_backward(dev)}
     if rank == 0 and not args.no_cpu_baseline:
         cb = time_oracle(w, u_iid, u_sorted, gx)
         line["cpu_baseline"] = {"value": cb["value"], "unit": "samples/s", "cores": 1,
@@ -331,6 +334,176 @@ def gpu_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# extra workloads (reported beside the main line)
+# ---------------------------------------------------------------------------
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def extra_ragged(dev, reps=3):
+    """16384 distributions (sizes log-uniform in [8, 65536], lognormal(0, 1.5)),
+    guide bits from the autotuner; batched build vs a loop of single builds;
+    build + 2^27 tagged samples replayed as one CUDA graph."""
+    import ctypes
+    import torch
+    from paper_1901_05423_gb300 import _native, api, autotune
+    from paper_1901_05423_gb300 import workloads as W
+    w_h, off = W.ragged_batch(16384, seed=0)
+    sizes = np.diff(off)
+    table = autotune.tune(dev)
+    ms = autotune.guide_bits_for(sizes, table)
+    w = torch.from_numpy(w_h).to(dev)
+    f = api.rtf_build_batched(w, sizes, ms)
+    ns = 1 << 27
+    u = api.u32_tensor(W.iid_u32(ns, seed=1), dev)
+    dist = torch.from_numpy(W.dist_ids(ns, len(sizes), seed=2)).to(dev)
+    idx = torch.empty(ns, dtype=torch.int32, device=dev)
+    pos = torch.empty(ns, dtype=torch.float32, device=dev)
+    api.rtf_sample(f, u, dist_id=dist, idx_out=idx, pos_out=pos)
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for _ in range(reps):
+        api.rtf_build_batched(w, sizes, ms, forest=f, plan_dev=f._plan_dev)
+    b.record()
+    torch.cuda.synchronize()
+    f.check_status()
+    batched_ms = a.elapsed_time(b) / reps
+    # the same builds one distribution at a time through rtf_build
+    lib = _native.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    goff = f.guide_offsets
+    nmax = int(sizes.max())
+    ws = api.workspace(lib.rtf_build_workspace_size(nmax, 1, 1 << int(ms.max())), dev, "build")
+    structs = []
+    for d in range(len(sizes)):
+        cf = _native.RtfForestC(
+            num_dists=1, flags=0, num_elems=int(sizes[d]), num_cells=1 << int(ms[d]),
+            max_m=int(ms[d]), nodes=f.nodes.data_ptr() + 16 * int(off[d]),
+            guide=f.guide.data_ptr() + 4 * int(goff[d]),
+            dists=f.dists.data_ptr() + 64 * d, status=f.status.data_ptr(),
+            guide_nodes=f.guide_nodes.data_ptr() + 16 * int(goff[d]))
+        structs.append((ctypes.c_void_p(w.data_ptr() + 4 * int(off[d])), int(sizes[d]),
+                        int(ms[d]), cf))
+    wsp, wsn = ctypes.c_void_p(ws.data_ptr()), ws.numel()
+    for wp, n, m, cf in structs[:64]:
+        lib.rtf_build(wp, n, m, ctypes.byref(cf), wsp, wsn, stream)
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for wp, n, m, cf in structs:
+        rc = lib.rtf_build(wp, n, m, ctypes.byref(cf), wsp, wsn, stream)
+        if rc:
+            raise RuntimeError(f"rtf_build failed ({rc})")
+    b.record()
+    torch.cuda.synchronize()
+    looped_ms = a.elapsed_time(b)
+    # build + tagged sampling captured once, replayed
+    f = api.rtf_build_batched(w, sizes, ms, forest=f, plan_dev=f._plan_dev)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream(dev)
+    st.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            api.rtf_build_batched(w, sizes, ms, forest=f, plan_dev=f._plan_dev)
+            api.rtf_sample(f, u, dist_id=dist, idx_out=idx, pos_out=pos)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for _ in range(reps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    f.check_status()
+    graph_ms = a.elapsed_time(b) / reps
+    N = int(off[-1])
+    return {
+        "workload": "16384 ragged distributions, n_d log-uniform in [8,65536] (sum %d), "
+                    "lognormal(0,1.5), autotuned guide bits, 2^27 tagged iid samples" % N,
+        "batched_build_ms": batched_ms, "looped_build_ms": looped_ms,
+        "batched_over_looped": looped_ms / batched_ms,
+        "build_elem_per_s": N / (batched_ms * 1e-3),
+        "build_hbm_frac": (28 * N + 4 * int(goff[-1])) / (batched_ms * 1e-3) / 1e9 / measured_peaks()[0],
+        "graph_build_plus_sample_ms": graph_ms,
+        "samples_per_s_in_graph": ns / (graph_ms * 1e-3),
+        "guide_bits_table": {str(k): int(v) for k, v in table.items()},
+    }
+
+
+def extra_env_map(dev, reps=3):
+    """4096 x 2048 map: marginal + 2048 conditionals in one batched build;
+    2^26 (u1, u2) pairs."""
+    import torch
+    from paper_1901_05423_gb300 import api
+    from paper_1901_05423_gb300 import workloads as W
+    H, Wd, m = 2048, 4096, 12
+    lum = torch.from_numpy(W.env_map(H, Wd, seed=0).reshape(-1)).to(dev)
+    sizes = [Wd] * H + [H]
+    ms = [m] * (H + 1)
+    f = api.rtf_build_batched(lum, sizes, ms, marginal=True)
+    ns = 1 << 26
+    u = api.u32_tensor(W.iid_u32(2 * ns, seed=3), dev)
+    idx = torch.empty((ns, 2), dtype=torch.int32, device=dev)
+    pos = torch.empty((ns, 2), dtype=torch.float32, device=dev)
+    api.rtf_sample(f, u, mode=api.SAMPLE_2D, idx_out=idx, pos_out=pos)
+    torch.cuda.synchronize()
+    a, b = _events()
+    c = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        api.rtf_build_batched(lum, sizes, ms, forest=f, plan_dev=f._plan_dev)
+    b.record()
+    for _ in range(reps):
+        api.rtf_sample(f, u, mode=api.SAMPLE_2D, idx_out=idx, pos_out=pos)
+    c.record()
+    torch.cuda.synchronize()
+    f.check_status()
+    bms = a.elapsed_time(b) / reps
+    sms = b.elapsed_time(c) / reps
+    return {"workload": "env map 4096x2048 + marginal, 2^12 guide cells per row and for the "
+                        "marginal, 2^26 iid (u1,u2) pairs",
+            "build_ms": bms, "build_elem_per_s": (H * Wd + H) / (bms * 1e-3),
+            "sample_ms": sms, "samples_2d_per_s": ns / (sms * 1e-3)}
+
+
+def extra_backward(dev, reps=5):
+    """n = 2^20 lognormal(0,1), 2^24 iid samples: forward (build + sample) vs
+    backward (dL/dw from dL/dx ~ N(0,1))."""
+    import torch
+    from paper_1901_05423_gb300 import api
+    from paper_1901_05423_gb300 import workloads as W
+    n, m, ns = 1 << 20, 18, 1 << 24
+    w = torch.from_numpy(W.lognormal_weights(n, seed=10, sigma=1.0)).to(dev)
+    u = api.u32_tensor(W.iid_u32(ns, seed=11), dev)
+    g = torch.from_numpy(W.normal_f32(ns, seed=12)).to(dev)
+    f = api.rtf_build(w, m)
+    idx, pos = api.rtf_sample(f, u)
+    gw = api.rtf_sample_backward(f, w, u, None, idx, pos, g)
+    torch.cuda.synchronize()
+    a, b = _events()
+    c = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        api.rtf_build(w, m, forest=f)
+        api.rtf_sample(f, u, idx_out=idx, pos_out=pos)
+    b.record()
+    for _ in range(reps):
+        api.rtf_sample_backward(f, w, u, None, idx, pos, g, grad_w=gw)
+    c.record()
+    torch.cuda.synchronize()
+    f.check_status()
+    fwd = a.elapsed_time(b) / reps
+    bwd = b.elapsed_time(c) / reps
+    return {"workload": "n=2^20 lognormal(0,1), 2^18 guide cells, 2^24 iid samples",
+            "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,6 +511,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rtf", choices=["rtf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ragged-batch, 2-D map and backward measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

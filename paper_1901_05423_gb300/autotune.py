@@ -1,0 +1,90 @@
+"""Autotuner of the guide size for ragged batches.
+
+The paper leaves the guide table size to the application: as large as memory
+allows, or proportional to the size of the distribution (Sec. 3).  For a
+batch of many distributions of different sizes the choice per size class is
+measured here on the GPU: for every power-of-two size bucket a batch of
+synthetic lognormal distributions of that size is built and sampled (one
+tagged sample per weight, the ratio of the ragged workload) for each candidate
+number of guide bits m around log2(n), and the m with the smallest build +
+sampling time wins.  Results are cached per GPU model in a JSON file
+(``$RTF_CACHE_DIR`` or ``~/.cache/rtf``).
+"""
+
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import api
+from . import workloads as W
+
+DEFAULT_OFFSETS = (-2, -1, 0, 1, 2)
+
+
+def _cache_path(device: torch.device) -> str:
+    root = os.environ.get("RTF_CACHE_DIR") or os.path.join(os.path.expanduser("~"), ".cache", "rtf")
+    name = torch.cuda.get_device_name(device).replace(" ", "_")
+    return os.path.join(root, f"guide_bits_{name}.json")
+
+
+def _time_bucket(n: int, m: int, device, total: int, reps: int, seed: int) -> float:
+    D = max(1, total // n)
+    sizes = [n] * D
+    w = torch.from_numpy(W.lognormal_weights(n * D, seed=seed, sigma=1.5)).to(device)
+    ns = n * D
+    u = api.u32_tensor(W.iid_u32(ns, seed=seed + 1), device)
+    dist = torch.from_numpy(W.dist_ids(ns, D, seed=seed + 2)).to(device)
+    idx = torch.empty(ns, dtype=torch.int32, device=device)
+    pos = torch.empty(ns, dtype=torch.float32, device=device)
+    f = api.rtf_build_batched(w, sizes, [m] * D)
+    api.rtf_sample(f, u, dist_id=dist, idx_out=idx, pos_out=pos)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        api.rtf_build_batched(w, sizes, [m] * D, forest=f, plan_dev=f._plan_dev)
+        api.rtf_sample(f, u, dist_id=dist, idx_out=idx, pos_out=pos)
+    e1.record()
+    torch.cuda.synchronize(device)
+    f.check_status()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune(device=None, buckets=range(3, 17), offsets=DEFAULT_OFFSETS, total: int = 1 << 22,
+         reps: int = 3, use_cache: bool = True) -> dict:
+    """Guide bits per size bucket: {bucket: m} with bucket = round(log2 n)."""
+    device = torch.device(device or "cuda:0")
+    path = _cache_path(device)
+    if use_cache and os.path.exists(path):
+        with open(path) as fh:
+            table = {int(k): int(v) for k, v in json.load(fh).items()}
+        if all(b in table for b in buckets):
+            return table
+    table = {}
+    for b in buckets:
+        n = 1 << b
+        best = None
+        for off in offsets:
+            m = min(max(b + off, 0), 24)
+            t = _time_bucket(n, m, device, total, reps, seed=b)
+            if best is None or t < best[0]:
+                best = (t, m)
+        table[b] = best[1]
+    if use_cache:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as fh:
+            json.dump({str(k): v for k, v in table.items()}, fh)
+    return table
+
+
+def guide_bits_for(sizes, table: dict) -> np.ndarray:
+    """m per distribution from a tuned table (nearest bucket, clamped)."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    b = np.clip(np.round(np.log2(np.maximum(sizes, 1))).astype(int), min(table), max(table))
+    lut = np.array([table.get(int(k), int(k)) for k in range(0, max(table) + 1)])
+    return lut[b].astype(np.int32)

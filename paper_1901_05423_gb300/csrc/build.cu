@@ -465,115 +465,152 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
   (void)staged;
   const int dfirst = s.dfirst;
 
-  // ---- q, C, keys of the thread's leaves --------------------------------
+  // ---- q, C, keys and distances of the thread's leaves ----------------------
+  // Each thread owns kForestPer consecutive leaves; the parameters of the
+  // distribution it is in stay in registers (reloaded only at a boundary).
   const int64_t e0 = t0 + (int64_t)tid * kForestPer;
   uint64_t q[kForestPer], incl[kForestPer];
+  int dk[kForestPer];
   uint32_t headmask = 0;
-  int dcur = dfirst;
   {
+    int dcur = dfirst;
     int64_t next = INT64_MAX;
     int S = 0;
-    rtf_dist P;
+    int32_t flags = 0;
+    int64_t off = 0;
     if (e0 < t1) {
       if (SEG) {
         dcur = find_dist(a.dists, dfirst, min(a.D - 1, dfirst + kTile), e0);
         next = dcur + 1 < a.D ? a.dists[dcur + 1].elem_off : INT64_MAX;
       }
-      P = a.dists[dcur];
-      S = (P.flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
+      const rtf_dist P = a.dists[dcur];
+      flags = P.flags;
+      off = P.elem_off;
+      S = (flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
     }
     uint64_t run = 0;
 #pragma unroll
     for (int k = 0; k < kForestPer; ++k) {
-      int64_t e = e0 + k;
+      const int64_t e = e0 + k;
       uint64_t qq = 0;
       if (e < t1) {
         if (SEG && e >= next) {
           ++dcur;
           next = dcur + 1 < a.D ? a.dists[dcur + 1].elem_off : INT64_MAX;
-          P = a.dists[dcur];
-          S = (P.flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
+          const rtf_dist P = a.dists[dcur];
+          flags = P.flags;
+          off = P.elem_off;
+          S = (flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
         }
-        if (P.elem_off == e) {
+        if (off == e) {
           headmask |= 1u << k;
           run = 0;
         }
-        if (P.flags & kDistMarginal) {
-          qq = __ldcg(&a.dists[e - P.elem_off].total);
+        if (flags & kDistMarginal) {
+          qq = __ldcg(&a.dists[e - off].total);
         } else {
-          uint32_t b = weight_bits(s.w[e - t0]);
+          const uint32_t b = weight_bits(s.w[e - t0]);
           qq = weight_bad(b) ? 0ull : quantize_bits(b, S);
         }
-        s.dist[e - t0] = dcur;
+        if (SEG) s.dist[e - t0] = dcur;
       }
+      dk[k] = dcur;
       q[k] = qq;
       run += qq;
       incl[k] = run;
     }
     SegPair agg{run, headmask ? 1u : 0u};
     SegPair ex = block_seg_exclusive(agg, s.wtot, &s.btot);
-    const bool head0 = a.dists[dfirst].elem_off == t0;
+    const bool head0 = SEG ? (a.dists[dfirst].elem_off == t0) : (t0 == 0);
     const uint64_t E = head0 ? 0ull : a.tile_prefix[tile];
-    uint64_t base = ex.f ? ex.s : ex.s + E;
+    const uint64_t base = ex.f ? ex.s : ex.s + E;
+    // keys of the thread's leaves (and of C_{t1} for the tile's last leaf)
+    int dP = -1;
+    uint64_t T = 0, R = 0;
+    int z = 0;
 #pragma unroll
     for (int k = 0; k < kForestPer; ++k) {
-      int64_t e = e0 + k;
+      const int64_t e = e0 + k;
       if (e >= t1) break;
-      bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
-      uint64_t inc = seen_head ? incl[k] : base + incl[k];
-      s.C[e - t0 + 1] = inc - q[k];  // exclusive: C_e
-      if (e == t1 - 1) s.C[t1 - t0 + 1] = inc;  // C_{t1} within the same distribution
+      if (dk[k] != dP) {
+        dP = dk[k];
+        const rtf_dist P = a.dists[dP];
+        T = P.total;
+        R = P.recip;
+        z = P.shift;
+      }
+      const bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
+      const uint64_t inc = seen_head ? incl[k] : base + incl[k];
+      const uint64_t C = inc - q[k];
+      s.C[e - t0 + 1] = C;
+      s.K[e - t0 + 1] = key_of(C, T, R, z);
+      if (e == t1 - 1) {
+        s.C[t1 - t0 + 1] = inc;  // C_{t1} within the distribution of t1-1
+        s.K[t1 - t0 + 1] = key_of(inc, T, R, z);
+      }
     }
   }
-  __syncthreads();
-  // C_{t0-1} (only meaningful when t0-1 belongs to the same distribution)
+  // C_{t0-1} and its key (only meaningful when t0-1 belongs to the same distribution)
   if (tid == 0) {
     s.C[0] = 0;
+    s.K[0] = 0;
     if (t0 > 0 && s.dprev == dfirst) {
-      rtf_dist P = a.dists[dfirst];
+      const rtf_dist P = a.dists[dfirst];
       uint64_t qp;
       if (P.flags & kDistMarginal) {
         qp = __ldcg(&a.dists[t0 - 1 - P.elem_off].total);
       } else {
-        uint32_t b = weight_bits(a.w[t0 - 1]);
+        const uint32_t b = weight_bits(a.w[t0 - 1]);
         qp = weight_bad(b) ? 0ull : quantize_bits(b, dist_scale(P, a.dmax, dfirst, a.n_shared));
       }
-      s.C[0] = s.C[1] - qp;
+      // C_{t0} is the tile prefix: this thread's first leaf when t0 is not a head
+      const uint64_t Ct0 = a.tile_prefix[tile];
+      s.C[0] = Ct0 - qp;
+      s.K[0] = key_for(P, Ct0 - qp);
     }
   }
   __syncthreads();
-  // keys K_j for j in [t0-1, t1]
-  for (int k = tid; k < (int)(t1 - t0) + 2; k += kForestThreads) {
-    int64_t j = t0 - 1 + k;
-    uint64_t K = 0;
-    if (j >= 0 && j <= t1) {
-      int d;
-      if (k == 0) d = s.dprev;
-      else if (j < t1) d = s.dist[j - t0];
-      else d = s.dist[t1 - 1 - t0];  // C_{t1} belongs to the distribution of t1-1
-      rtf_dist P = a.dists[d];
-      K = key_for(P, s.C[k]);
-    }
-    s.K[k] = K;
-  }
-  __syncthreads();
-  // distances delta_j for j in [t0-1, t1-1]
-  for (int k = tid; k < (int)(t1 - t0) + 1; k += kForestThreads) {
-    int64_t j = t0 - 1 + k;
-    uint32_t dlt = kDeltaInf;
-    if (j >= 0) {
-      int d = (k == 0) ? s.dprev : s.dist[j - t0];
-      rtf_dist P = a.dists[d];
-      int64_t end = P.elem_off + P.n;
-      bool same_dist = (j + 1 < end);
-      if (k == 0) same_dist = same_dist && (s.dprev == dfirst);
-      if (same_dist) {
-        uint64_t Ka = s.K[k], Kb = s.K[k + 1];
-        if (cell_of(Ka, P.m) == cell_of(Kb, P.m)) dlt = key_distance(Ka, Kb);
+  // distances: delta_j for the thread's leaves j, and delta_{t0-1} by thread 0
+  {
+    int dP = -1;
+    int m = 0;
+    int64_t end = 0;
+    uint32_t packed = 0;
+#pragma unroll
+    for (int k = 0; k < kForestPer; ++k) {
+      const int64_t j = e0 + k;
+      uint32_t dlt = kDeltaInf;
+      if (j < t1) {
+        if (dk[k] != dP) {
+          dP = dk[k];
+          const rtf_dist P = a.dists[dP];
+          m = P.m;
+          end = P.elem_off + P.n;
+        }
+        if (j + 1 < end) {
+          const uint64_t Ka = s.K[j - t0 + 1], Kb = s.K[j - t0 + 2];
+          if (cell_of(Ka, m) == cell_of(Kb, m)) dlt = key_distance(Ka, Kb);
+        }
+        s.delta[j - t0 + 1] = (uint8_t)dlt;
       }
-      a.delta[j] = (uint8_t)dlt;
+      packed |= dlt << (8 * k);
     }
-    s.delta[k] = (uint8_t)dlt;
+    if (e0 + kForestPer <= t1) {
+      *reinterpret_cast<uint32_t*>(a.delta + e0) = packed;
+    } else {
+      for (int k = 0; k < kForestPer && e0 + k < t1; ++k)
+        a.delta[e0 + k] = (uint8_t)(packed >> (8 * k));
+    }
+    if (tid == 0) {
+      uint32_t d0 = kDeltaInf;
+      if (t0 > 0 && s.dprev == dfirst) {
+        const int mm = a.dists[dfirst].m;
+        const uint64_t Ka = s.K[0], Kb = s.K[1];
+        if (cell_of(Ka, mm) == cell_of(Kb, mm)) d0 = key_distance(Ka, Kb);
+      }
+      s.delta[0] = (uint8_t)d0;
+      if (t0 > 0) a.delta[t0 - 1] = (uint8_t)d0;
+    }
   }
   for (int k = tid; k < (int)(t1 - t0); k += kForestThreads) {
     s.child[k][0] = kUnset;
@@ -587,7 +624,7 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
   for (int k = 0; k < kForestPer; ++k) {
     int64_t j = e0 + k;
     if (j >= t1) break;
-    const int d = s.dist[j - t0];
+    const int d = SEG ? s.dist[j - t0] : 0;
     const int64_t off = a.dists[d].elem_off;
     int64_t lo = j, hi = j;
     int32_t node = ~(int32_t)(j - off);
@@ -675,7 +712,7 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
   if (tid < min(nd, kDeferCap)) {
     const int child = s.defer_child[tid];
     const int64_t bound = child ? s.defer_hi[tid] : s.defer_lo[tid];
-    const int d = s.dist[s.defer_lo[tid] - t0];
+    const int d = SEG ? s.dist[s.defer_lo[tid] - t0] : 0;
     a.items[tile * kDeferCap + tid] = make_uint4((uint32_t)s.defer_parent[tid], (uint32_t)bound,
                                                  (uint32_t)s.defer_node[tid], (uint32_t)d);
   }

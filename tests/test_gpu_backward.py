@@ -171,3 +171,36 @@ def test_backward_matches_gpu_forward_differences():
         gk = orc.grad(w, u[keep], ridx, g[keep])[k]
         assert abs(fd - gk) <= 2e-3 * (abs(gk) + np.abs(g[keep]).sum() * 1e-4)
     assert np.isfinite(gw).all()
+
+
+def test_autograd_function_matches_oracle():
+    from paper_1901_05423_gb300.autograd import sample_positions
+    n, n_s, m = 3000, 1 << 16, 11
+    w_h = W.lognormal_weights(n, seed=60, sigma=1.0)
+    u_h = W.iid_u32(n_s, seed=61)
+    c_h = W.normal_f32(n_s, seed=62)
+    w = to_dev(w_h).requires_grad_(True)
+    pos, idx = sample_positions(w, api.u32_tensor(u_h, DEV), m)
+    loss = (pos * to_dev(c_h)).sum()
+    loss.backward()
+    ref = orc.build(w_h, 1 << m)
+    ridx, _ = orc.sample(ref.C, u_h)
+    assert np.array_equal(idx.cpu().numpy(), ridx)
+    gref = orc.grad(w_h, u_h, ridx, c_h)
+    assert rel_err(w.grad.cpu().numpy(), gref) <= TOL
+
+
+def test_autograd_function_2d_matches_oracle():
+    from paper_1901_05423_gb300.autograd import sample_positions_2d
+    H, Wd, n_s = 24, 40, 1 << 15
+    lum_h = W.env_map(H, Wd, seed=63)
+    rng = np.random.default_rng(64)
+    u_h = rng.integers(0, 1 << 32, 2 * n_s, dtype=np.uint64).astype(np.uint32)
+    c_h = W.normal_f32(2 * n_s, seed=65).reshape(n_s, 2)
+    lum = to_dev(lum_h).requires_grad_(True)
+    pos, idx = sample_positions_2d(lum, api.u32_tensor(u_h, DEV), 6, 7)
+    (pos * to_dev(c_h)).sum().backward()
+    rows, marg = orc.build_env(lum_h, 1 << 6, 1 << 7)
+    r, c, _, _ = orc.sample_env(rows, marg, u_h[0::2], u_h[1::2])
+    gref = orc.grad_env(lum_h, u_h[0::2], u_h[1::2], r, c, c_h[:, 0].copy(), c_h[:, 1].copy())
+    assert rel_err(lum.grad.cpu().numpy(), gref) <= TOL

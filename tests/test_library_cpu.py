@@ -107,3 +107,10 @@ def test_workload_generators_shapes():
     assert sizes.min() >= 8 and sizes.max() <= 65536 and w.size == off[-1]
     lum = W.env_map(32, 64, seed=0)
     assert lum.shape == (32, 64) and lum.dtype == np.float32 and lum.min() > 0
+
+
+def test_guide_bits_lookup_without_gpu():
+    from paper_1901_05423_gb300 import autotune
+    table = {3: 2, 4: 4, 5: 5, 6: 7}
+    ms = autotune.guide_bits_for([1, 8, 11, 16, 40, 64, 10 ** 6], table)
+    assert ms.tolist() == [2, 2, 2, 4, 5, 7, 7]
