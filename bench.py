@@ -457,7 +457,7 @@ def extra_env_map(dev, reps=3):
     c = torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(reps):
-        api.rtf_build_batched(lum, sizes, ms, forest=f, plan_dev=f._plan_dev)
+        api.rtf_build_batched(lum, sizes, ms, marginal=True, forest=f, plan_dev=f._plan_dev)
     b.record()
     for _ in range(reps):
         api.rtf_sample(f, u, mode=api.SAMPLE_2D, idx_out=idx, pos_out=pos)

@@ -149,7 +149,7 @@ size_t rtf_build_workspace_size(int64_t num_elems, int32_t num_dists,
 /*
  * Build the structure of one distribution.
  *
- *   w        device float32[n], 16-byte aligned: the weights (Sec. 1: p up to
+ *   w        device float32[n], 4-byte aligned: the weights (Sec. 1: p up to
  *            normalisation), w_i >= 0, finite, at least one positive.
  *   n        1 <= n <= 2^31 - 2^16.
  *   m        guide bits, 0 <= m <= 30: 2^m cells (Sec. 2.5, Sec. 3.2).
@@ -194,7 +194,7 @@ rtf_status rtf_build_static(const float *w, int64_t n, int32_t m, rtf_forest *f,
  * built together by treating the index boundary of every distribution like a
  * cell boundary in Algorithm 1).
  *
- *   w              device float32[offsets[D_w]], 16-byte aligned, where
+ *   w              device float32[offsets[D_w]], 4-byte aligned, where
  *                  D_w = D (independent distributions) or D - 1 (marginal mode).
  *   offsets        device int64[D + 1]: distribution d owns elements
  *                  [offsets[d], offsets[d+1]); offsets[0] = 0, n_d >= 1.

@@ -69,7 +69,7 @@ rtf_status rtf_build(const float* w, int64_t n, int32_t m, rtf_forest* f, void* 
   if (f->num_dists != 1 || f->num_elems != n || f->num_cells != (int64_t(1) << m) ||
       f->max_m != m || f->flags != 0)
     return RTF_EINVAL;
-  if (!aligned(w, 16) || !aligned(ws, 256)) return RTF_EINVAL;
+  if (!aligned(w, 4) || !aligned(ws, 256)) return RTF_EINVAL;
   if (ws_bytes < rtf_build_workspace_size(n, 1, int64_t(1) << m)) return RTF_EWORKSPACE;
   return cuda_status(rtf::launch_build(w, n, n, 1, 0, nullptr, nullptr, nullptr, n, m, f, ws,
                                        static_cast<cudaStream_t>(stream)));
@@ -83,7 +83,7 @@ rtf_status rtf_build_batched(const float* w, const int64_t* offsets, const int32
   const int marginal = (f->flags & RTF_FOREST_MARGINAL) ? 1 : 0;
   if (f->flags & ~RTF_FOREST_MARGINAL) return RTF_EINVAL;
   if (marginal && D < 2) return RTF_EINVAL;
-  if (!aligned(w, 16) || !aligned(ws, 256) || !aligned(offsets, 8) || !aligned(guide_offsets, 8))
+  if (!aligned(w, 4) || !aligned(ws, 256) || !aligned(offsets, 8) || !aligned(guide_offsets, 8))
     return RTF_EINVAL;
   const int64_t N = f->num_elems;
   const int64_t Nw = marginal ? N - (D - 1) : N;

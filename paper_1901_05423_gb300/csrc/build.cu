@@ -5,10 +5,13 @@
 // Kernels, in launch order:
 //   init_dists_kernel   per-distribution parameters from the plan
 //   scale_kernel        validation and max exponent (one read of w)
-//   scan_kernel         exact integer prefix sums of the tiles by a decoupled
-//                       lookback (second read of w); totals T and key
-//                       reciprocals; in marginal mode the last tile to finish
-//                       also scans the row totals
+//   tile_sum_kernel     segmented sums of the integer weights per tile (second
+//                       read of w, staged by a bulk copy); totals of the
+//                       distributions that lie inside one tile
+//   tile_scan_kernel    decoupled-lookback segmented scan of the tile sums:
+//                       the prefix of every tile, the totals T (and key
+//                       reciprocals) of the distributions that cross tiles; in
+//                       marginal mode the last block also scans the row totals
 //   forest_kernel       C_j, keys K_j, distances, Algorithm 1 inside each tile
 //                       in shared memory; node records, roots, guide entries
 //                       of non-empty cells; the tile's slice of the global
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(kScaleThreads)
   uint32_t bad = 0;
   if (!SEG) {
     uint32_t mx = 0;
-    if (e0 + kScalePer <= c1) {
+    if (e0 + kScalePer <= c1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
       const float4* p = reinterpret_cast<const float4*>(w + e0);
 #pragma unroll
       for (int k = 0; k < kScalePer / 4; ++k) {
@@ -177,28 +180,38 @@ __device__ inline void finish_dist(rtf_dist* dists, int d, uint64_t T, int S, ui
 
 constexpr int kScanPer = kTile / kScanThreads;  // 8
 
+// Per-tile results of tile_sum_kernel, consumed by tile_scan_kernel.
+struct TileSums {
+  uint64_t* sum;     // sum of q since the tile's last head (the whole tile without one)
+  uint64_t* first;   // partial sum of the tile's first piece when its distribution ends here
+  uint32_t* meta;    // bit0: a head lies in the tile, bit1: t0 is a head,
+                     // bit2: the distribution of t0 ends inside the tile
+  int32_t* dist0;    // distribution of t0
+};
+
+// Tile sums of q (second read of w, staged by a bulk copy).  Distributions that
+// begin and end inside the tile are finished here; the tile's first piece,
+// whose distribution began in an earlier tile, waits for the scan of the tile
+// sums.
 template <bool SEG>
 __global__ void __launch_bounds__(kScanThreads)
-    scan_kernel(const float* __restrict__ w, int64_t Nw, rtf_dist* dists, int D, int Dw,
-                int marginal, int64_t n_shared, const uint32_t* dmax, uint64_t* scan_status,
-                uint64_t* tile_prefix, Counters* ctr, uint32_t* status) {
-  __shared__ alignas(16) float wsm[kTile];
+    tile_sum_kernel(const float* __restrict__ w, int64_t Nw, rtf_dist* dists, int Dw,
+                    int64_t n_shared, const uint32_t* dmax, TileSums ts, uint32_t* status) {
+  __shared__ alignas(16) float wsm[kTile + 4];
   __shared__ uint64_t bar;
   __shared__ int ok_s;
-  __shared__ uint32_t tile_s;
   __shared__ int dfirst_s;
   __shared__ SegPair wtot[kScanThreads / 32];
   __shared__ SegPair btot;
-  __shared__ LookbackShared lb;
-  __shared__ int last_s;
+  __shared__ uint32_t meta_s;
 
-  if (threadIdx.x == 0) tile_s = atomicAdd(&ctr->scan_ticket, 1u);
-  __syncthreads();
-  const int64_t tile = tile_s;
-  const int64_t ntiles = num_tiles(Nw);
+  const int64_t tile = blockIdx.x;
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, Nw);
-  if (threadIdx.x == 0) dfirst_s = SEG ? find_dist(dists, 0, Dw - 1, t0) : 0;
-  bool staged = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
+  if (threadIdx.x == 0) {
+    dfirst_s = SEG ? find_dist(dists, 0, Dw - 1, t0) : 0;
+    meta_s = 0;
+  }
+  const int wo = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
   const int dfirst = dfirst_s;
 
   // per-thread run of kScanPer consecutive weights
@@ -208,35 +221,37 @@ __global__ void __launch_bounds__(kScanThreads)
   uint32_t headmask = 0;
   SegPair agg{0ull, 0u};
   {
-    int d = 0;
+    int d = dfirst;
     int64_t next = INT64_MAX;
+    int64_t off = 0;
     int S = 0;
     if (e0 < t1) {
       if (SEG) {
         d = find_dist(dists, dfirst, min(Dw - 1, dfirst + kTile), e0);
         next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
       }
-      rtf_dist P = dists[d];
+      const rtf_dist P = dists[d];
+      off = P.elem_off;
       S = dist_scale(P, dmax, d, n_shared);
     }
     uint64_t run = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      int64_t e = e0 + k;
+      const int64_t e = e0 + k;
       uint64_t q = 0;
       if (e < t1) {
         if (SEG && e >= next) {
           ++d;
           next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
-          rtf_dist P = dists[d];
+          const rtf_dist P = dists[d];
+          off = P.elem_off;
           S = dist_scale(P, dmax, d, n_shared);
         }
-        bool head = SEG ? (dists[d].elem_off == e) : (e == 0);
-        if (head) {
+        if (off == e) {
           headmask |= 1u << k;
           run = 0;
         }
-        uint32_t b = weight_bits(wsm[e - t0]);
+        const uint32_t b = weight_bits(wsm[wo + (e - t0)]);
         q = weight_bad(b) ? 0ull : quantize_bits(b, S);
       }
       run += q;
@@ -246,55 +261,113 @@ __global__ void __launch_bounds__(kScanThreads)
     agg.s = run;
     agg.f = headmask ? 1u : 0u;
   }
-  SegPair ex = block_seg_exclusive(agg, wtot, &btot);
-
-  // tile head / tail facts
+  const SegPair ex = block_seg_exclusive(agg, wtot, &btot);
   const bool head0 = SEG ? (dists[dfirst].elem_off == t0) : (t0 == 0);
-  int dlast = dfirst;
-  if (SEG) dlast = find_dist(dists, dfirst, min(Dw - 1, dfirst + kTile), t1 - 1);
-  const bool last_head_in_tile = SEG ? (dists[dlast].elem_off >= t0) : (t0 == 0);
-  const uint64_t A = btot.s;  // sum of the last piece (since the last head)
-
-  if (threadIdx.x == 0) {
-    uint64_t v = (A & kValueMask) | (last_head_in_tile ? kFlagPrefix : kFlagAgg);
-    if (!staged) v = kFlagPrefix;  // keep successors from waiting on a failed tile
-    st_release_u64(scan_status + tile, v);
-  }
-  uint64_t E = 0;
-  if (!head0) E = block_lookback(scan_status, tile, true, &lb, status);
-  if (threadIdx.x == 0) {
-    if (!head0 && !last_head_in_tile)
-      st_release_u64(scan_status + tile, ((E + A) & kValueMask) | kFlagPrefix);
-    tile_prefix[tile] = E;
-  }
 
   // distributions whose last element lies in this tile
   if (e0 < t1) {
-    // inclusive value of each element = (thread exclusive) + local run, with
-    // the tile prefix for the first piece
-    uint64_t base = ex.f ? ex.s : ex.s + E;
-    bool first_piece = !ex.f && !head0;
-    (void)first_piece;
+    const uint64_t base = ex.s;  // the tile's own partial sums (no incoming prefix)
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      int64_t e = e0 + k;
+      const int64_t e = e0 + k;
       if (e >= t1) break;
-      bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
-      uint64_t v = seen_head ? incl[k] : base + incl[k];
-      int d = dk[k];
-      int64_t end = SEG ? (d + 1 < Dw ? dists[d + 1].elem_off : Nw) : Nw;
+      const bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
+      const uint64_t v = seen_head ? incl[k] : base + incl[k];
+      const int d = dk[k];
+      const int64_t end = SEG ? (d + 1 < Dw ? dists[d + 1].elem_off : Nw) : Nw;
       if (e + 1 == end) {
-        rtf_dist P = dists[d];
-        finish_dist(dists, d, v, dist_scale(P, dmax, d, n_shared), status);
+        if (seen_head || ex.f) {
+          const rtf_dist P = dists[d];  // began inside the tile: complete
+          finish_dist(dists, d, v, dist_scale(P, dmax, d, n_shared), status);
+        } else {
+          ts.first[tile] = v;  // the tile's first piece: completed by the tile scan
+          atomicOr(&meta_s, 4u);
+        }
       }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ts.sum[tile] = btot.s;
+    ts.meta[tile] = meta_s | (btot.f ? 1u : 0u) | (head0 ? 2u : 0u);
+    ts.dist0[tile] = dfirst;
+  }
+}
+
+constexpr int kTileScanPer = 8;
+constexpr int kTileScanChunk = kScanThreads * kTileScanPer;  // tiles per scan block
+
+// Decoupled-lookback segmented scan of the tile sums (a distribution's head
+// restarts the sum): the prefix of every tile's first piece, and the totals of
+// the distributions that cross tiles.  In marginal mode the last block to
+// finish also scans the row totals, the marginal's integer weights.
+__global__ void __launch_bounds__(kScanThreads)
+    tile_scan_kernel(TileSums ts, int64_t ntiles, rtf_dist* dists, int D, int Dw, int marginal,
+                     int64_t n_shared, const uint32_t* dmax, uint64_t* chunk_status,
+                     uint64_t* tile_prefix, Counters* ctr, uint32_t* status) {
+  __shared__ uint32_t chunk_s;
+  __shared__ SegPair wtot[kScanThreads / 32];
+  __shared__ SegPair btot;
+  __shared__ LookbackShared lb;
+  __shared__ int last_s;
+  if (threadIdx.x == 0) chunk_s = atomicAdd(&ctr->scan_ticket, 1u);
+  __syncthreads();
+  const int64_t chunk = chunk_s;
+  const int64_t nchunks = (ntiles + kTileScanChunk - 1) / kTileScanChunk;
+  const int64_t c0 = chunk * kTileScanChunk + (int64_t)threadIdx.x * kTileScanPer;
+
+  uint64_t incl[kTileScanPer];
+  uint32_t headmask = 0;
+  uint64_t run = 0;
+#pragma unroll
+  for (int k = 0; k < kTileScanPer; ++k) {
+    const int64_t t = c0 + k;
+    incl[k] = run;  // exclusive value of tile t (since the last head before it)
+    if (t < ntiles) {
+      const uint64_t a = ts.sum[t];
+      if (ts.meta[t] & 1u) {
+        headmask |= 1u << k;  // the value passed on restarts at the tile's last head
+        run = a;
+      } else {
+        run += a;
+      }
+    }
+  }
+  const SegPair agg{run, headmask ? 1u : 0u};
+  const SegPair ex = block_seg_exclusive(agg, wtot, &btot);
+  if (threadIdx.x == 0) {
+    const uint64_t v = (btot.s & kValueMask) | (btot.f ? kFlagPrefix : kFlagAgg);
+    st_release_u64(chunk_status + chunk, v);
+  }
+  // chunk 0 starts with the head at element 0, so its first tile needs no prefix
+  uint64_t E = 0;
+  if (chunk > 0) E = block_lookback(chunk_status, chunk, true, &lb, status);
+  if (threadIdx.x == 0 && !btot.f)
+    st_release_u64(chunk_status + chunk, ((E + btot.s) & kValueMask) | kFlagPrefix);
+  const uint64_t base = ex.f ? ex.s : ex.s + E;
+#pragma unroll
+  for (int k = 0; k < kTileScanPer; ++k) {
+    const int64_t t = c0 + k;
+    if (t >= ntiles) break;
+    // sum of the first piece's distribution before t0: the segmented
+    // exclusive value of tile t (a head in tile t itself does not count)
+    const bool seen_head = (headmask & ((1u << k) - 1u)) != 0;
+    const uint64_t Et = seen_head ? incl[k] : base + incl[k];
+    const uint32_t meta = ts.meta[t];
+    const bool head0 = (meta & 2u) != 0;
+    tile_prefix[t] = head0 ? 0ull : Et;
+    if ((meta & 4u) && !head0) {
+      const int d = ts.dist0[t];
+      const rtf_dist P = dists[d];
+      finish_dist(dists, d, Et + ts.first[t], dist_scale(P, dmax, d, n_shared), status);
     }
   }
 
   if (!marginal) return;
-  // marginal mode: the last tile to finish scans the row totals
+  // marginal mode: the last block to finish scans the row totals
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last_s = (atomicAdd(&ctr->scan_done, 1u) == (uint32_t)(ntiles - 1));
+  if (threadIdx.x == 0) last_s = (atomicAdd(&ctr->scan_done, 1u) == (uint32_t)(nchunks - 1));
   __syncthreads();
   if (!last_s) return;
   __threadfence();
@@ -302,19 +375,20 @@ __global__ void __launch_bounds__(kScanThreads)
   const int64_t moff = dists[D - 1].elem_off;  // == Nw
   uint64_t carry = 0;
   for (int r0 = 0; r0 < H; r0 += kScanThreads) {
-    int r = r0 + threadIdx.x;
-    uint64_t Tr = r < H ? __ldcg(&dists[r].total) : 0ull;
-    SegPair x{Tr, 0u};
-    SegPair px = block_seg_exclusive(x, wtot, &btot);
-    uint64_t excl = carry + px.s;  // sum of T over rows < r
+    const int r = r0 + threadIdx.x;
+    const uint64_t Tr = r < H ? __ldcg(&dists[r].total) : 0ull;
+    const SegPair x{Tr, 0u};
+    const SegPair px = block_seg_exclusive(x, wtot, &btot);
+    const uint64_t excl = carry + px.s;  // sum of T over rows < r
     if (r < H) {
-      int64_t e = moff + r;
+      const int64_t e = moff + r;
       if (e % kTile == 0) tile_prefix[e / kTile] = excl;
     }
     carry += btot.s;
     __syncthreads();
   }
-  if (threadIdx.x == 0) finish_dist(dists, D - 1, carry, 0, status);
+  // the marginal's integers are in the units of the shared scale
+  if (threadIdx.x == 0) finish_dist(dists, D - 1, carry, scale_from_max(dmax[0], n_shared), status);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,7 +399,7 @@ static_assert(kForestPer == 4, "the otherBounds write-out stores one int4 per th
 constexpr int32_t kUnset = 0x7FFFFFFF;
 
 struct ForestShared {
-  alignas(16) float w[kTile];
+  alignas(16) float w[kTile + 4];
   alignas(16) uint64_t C[kTile + 2];  // C_{t0-1} .. C_{t1}
   alignas(16) uint64_t K[kTile + 2];  // K_{t0-1} .. K_{t1}
   alignas(16) int32_t child[kTile][2];
@@ -459,10 +533,9 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
     s.dprev = (t0 > 0 && SEG) ? (a.dists[df].elem_off == t0 ? df - 1 : df) : df;
     s.ndefer = 0;
   }
-  bool staged = true;
-  if (t0 < a.Nw) staged = stage_weights(s.w, a.w, t0, min(t1, a.Nw), &s.bar, &s.ok, a.status);
+  int wo = 0;
+  if (t0 < a.Nw) wo = stage_weights(s.w, a.w, t0, min(t1, a.Nw), &s.bar, &s.ok, a.status);
   else __syncthreads();
-  (void)staged;
   const int dfirst = s.dfirst;
 
   // ---- q, C, keys and distances of the thread's leaves ----------------------
@@ -509,7 +582,7 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
         if (flags & kDistMarginal) {
           qq = __ldcg(&a.dists[e - off].total);
         } else {
-          const uint32_t b = weight_bits(s.w[e - t0]);
+          const uint32_t b = weight_bits(s.w[wo + (e - t0)]);
           qq = weight_bad(b) ? 0ull : quantize_bits(b, S);
         }
         if (SEG) s.dist[e - t0] = dcur;
@@ -852,14 +925,21 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
                                                                    f->status);
   }
   const int64_t tiles_w = num_tiles(Nw);
+  TileSums ts;
+  ts.sum = reinterpret_cast<uint64_t*>(base + L.tile_sum);
+  ts.first = reinterpret_cast<uint64_t*>(base + L.tile_first);
+  ts.meta = reinterpret_cast<uint32_t*>(base + L.tile_meta);
+  ts.dist0 = reinterpret_cast<int32_t*>(base + L.tile_dist0);
   if (seg)
-    scan_kernel<true><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(
-        w, Nw, f->dists, D, Dw, marginal, n_shared, dmax, scan_status, tile_prefix, ctr,
-        f->status);
+    tile_sum_kernel<true><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(w, Nw, f->dists, Dw,
+                                                                     n_shared, dmax, ts, f->status);
   else
-    scan_kernel<false><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(
-        w, Nw, f->dists, D, Dw, marginal, n_shared, dmax, scan_status, tile_prefix, ctr,
-        f->status);
+    tile_sum_kernel<false><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(w, Nw, f->dists, Dw,
+                                                                      n_shared, dmax, ts, f->status);
+  const int64_t chunks = (tiles_w + kTileScanChunk - 1) / kTileScanChunk;
+  tile_scan_kernel<<<(unsigned)chunks, kScanThreads, 0, st>>>(ts, tiles_w, f->dists, D, Dw, marginal,
+                                                             n_shared, dmax, scan_status,
+                                                             tile_prefix, ctr, f->status);
   ForestArgs fa;
   fa.w = w;
   fa.N = N;

@@ -38,11 +38,15 @@ struct WsLayout {
   size_t zero_begin;   // start of the region zero-filled by every build
   size_t counters;     // u32 tickets / done counters
   size_t dmax;         // u32 [D] max float bits per distribution / group
-  size_t scan_status;  // u64 [num_tiles]
+  size_t scan_status;  // u64 [num_tiles / 2048 + 1] status of the tile-sum scan blocks
   size_t guide_status; // u64 [num_guide_tiles]
   size_t zero_end;
   size_t last;         // i32 [G] last leaf of each non-empty cell (set to -1)
   size_t tile_prefix;  // u64 [num_tiles]
+  size_t tile_sum;     // u64 [num_tiles]
+  size_t tile_first;   // u64 [num_tiles]
+  size_t tile_meta;    // u32 [num_tiles]
+  size_t tile_dist0;   // i32 [num_tiles]
   size_t delta;        // u8  [N]
   size_t other;        // i32 [N] otherBounds of Algorithm 1 (written by every build)
   size_t items;        // uint4 [num_tiles * kDeferCap] deferred hand-offs per tile
@@ -60,12 +64,16 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   L.zero_begin = o;
   L.counters = o; o += 256;
   L.dmax = o; o = align256(o + sizeof(uint32_t) * (size_t)D);
-  L.scan_status = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
+  L.scan_status = o; o = align256(o + sizeof(uint64_t) * (size_t)(num_tiles(N) / 2048 + 1));
   L.guide_status = o;
   o = align256(o + sizeof(uint64_t) * (size_t)((G + kGuideTile - 1) / kGuideTile));
   L.zero_end = o;
   L.last = o; o = align256(o + sizeof(int32_t) * (size_t)G);
   L.tile_prefix = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
+  L.tile_sum = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
+  L.tile_first = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
+  L.tile_meta = o; o = align256(o + sizeof(uint32_t) * (size_t)num_tiles(N));
+  L.tile_dist0 = o; o = align256(o + sizeof(int32_t) * (size_t)num_tiles(N));
   L.delta = o; o = align256(o + (size_t)N);
   L.other = o; o = align256(o + sizeof(int32_t) * (size_t)N);
   L.items = o; o = align256(o + 16 * (size_t)kDeferCap * (size_t)num_tiles(N));
@@ -275,24 +283,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// Stage w[t0, t1) into shared memory: the 16-byte aligned body by one bulk
-// copy, the (at most 3) trailing weights by plain loads.  Called by all
-// threads; returns false (after raising RTF_STATUS_TIMEOUT and a second
-// bounded wait for the copy in flight) when the copy did not complete.
-// `w + t0` must be 16-byte aligned (t0 is a multiple of the tile size and w is
-// 16-byte aligned).
-__device__ inline bool stage_weights(float* dst, const float* w, int64_t t0, int64_t t1,
-                                     uint64_t* bar, int* flag, uint32_t* status) {
-  int cnt = (int)(t1 - t0);
-  int body = cnt & ~3;
+// Stage w[t0, t1) into shared memory `dst` (kTile + 4 floats): the 16-byte
+// aligned middle by one bulk copy, the (at most 3 + 3) weights before and
+// after it by plain loads.  Weight t0 + j lands at dst[o + j] for the returned
+// offset o in 0..3, which puts the bulk copy on a 16-byte boundary in shared
+// memory as well.  Called by all threads.  If the copy does not complete
+// within the bounded wait, RTF_STATUS_TIMEOUT is raised (after a second
+// bounded wait for the copy in flight) and *flag is 0.
+__device__ inline int stage_weights(float* dst, const float* w, int64_t t0, int64_t t1,
+                                    uint64_t* bar, int* flag, uint32_t* status) {
+  const float* src = w + t0;
+  const int cnt = (int)(t1 - t0);
+  const int mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+  const int head = min((4 - mis) & 3, cnt);
+  const int body = (cnt - head) & ~3;
+  const int o = mis;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     if (body > 0) {
       mbar_arrive_expect_tx(bar, (uint32_t)body * 4u);
-      bulk_g2s(dst, w + t0, (uint32_t)body * 4u, bar);
+      bulk_g2s(dst + o + head, src + head, (uint32_t)body * 4u, bar);
     }
   }
-  for (int k = body + (int)threadIdx.x; k < cnt; k += blockDim.x) dst[k] = w[t0 + k];
+  for (int k = (int)threadIdx.x; k < head; k += blockDim.x) dst[o + k] = src[k];
+  for (int k = head + body + (int)threadIdx.x; k < cnt; k += blockDim.x) dst[o + k] = src[k];
   if (threadIdx.x == 0) {
     int ok = 1;
     if (body > 0 && !mbar_wait(bar, 0)) {
@@ -303,7 +317,7 @@ __device__ inline bool stage_weights(float* dst, const float* w, int64_t t0, int
     *flag = ok;
   }
   __syncthreads();
-  return *flag != 0;
+  return o;
 }
 
 // ---------------------------------------------------------------------------

@@ -352,3 +352,26 @@ def test_graph_replay_is_deterministic():
     assert all(torch.equal(a, b) for a, b in zip(outs[0], outs[1]))
     ref = orc.build(w, 1 << 14)
     check_structure(f, ref)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_misaligned_weights(shift):
+    """Weights that start 4, 8 or 12 bytes past a 16-byte boundary (the bulk
+    copy covers the aligned middle of each tile, plain loads the edges)."""
+    n = 3 * 2048 + 77
+    w = W.lognormal_weights(n + 8, seed=40 + shift, sigma=2.0)
+    full = to_dev(w)
+    view = full[shift:shift + n]
+    assert view.data_ptr() % 16 == 4 * shift
+    f = api.rtf_build(view, 9)
+    torch.cuda.synchronize()
+    f.check_status()
+    check_structure(f, orc.build(w[shift:shift + n], 1 << 9))
+    sizes = [5, 2048, 700, n - 2753]
+    fb = api.rtf_build_batched(view, sizes, [2, 8, 7, 9])
+    torch.cuda.synchronize()
+    fb.check_status()
+    off = fb.offsets
+    for d in range(len(sizes)):
+        ref = orc.build(w[shift + off[d]:shift + off[d + 1]], 1 << [2, 8, 7, 9][d])
+        check_structure(fb, ref, elem_off=int(off[d]), guide_off=int(fb.guide_offsets[d]))
