@@ -135,7 +135,7 @@ def time_oracle(w, u_iid, u_sorted, gx, sample_count=1 << 21):
         "build_elem_per_s": N_W / t_build,
         "sample": (f"oracle build of n=2^24 (timed once), index+position on {sample_count} "
                    f"i.i.d. + {sample_count} sorted samples and the gradient on {sample_count} "
-                   f"samples, scaled linearly to 2^28 samples per set"),
+                   f"samples, scaled linearly to 2^{N_S.bit_length() - 1} samples per set"),
     }
 
 
@@ -157,8 +157,9 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "n=2^24 lognormal(0,2) weights, 2^20 guide cells, 2^28 iid + "
-                               "2^28 sorted radical-inverse samples, backward on the iid set",
+        "config": {"workload": f"n=2^24 lognormal(0,2) weights, 2^20 guide cells, "
+                               f"2^{lg} iid + 2^{lg} sorted radical-inverse samples, "
+                               f"backward on the iid set",
                    "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
                          "sample": res["sample"].replace(str(1 << 21), str(1 << 19))},
@@ -298,13 +299,15 @@ def gpu_arm(args):
     dom = max(avg, key=avg.get)
     achieved = alg[dom] / (avg[dom] * 1e-3) / 1e9
     value = world * 2 * N_S / (ms * 1e-3)
+    lg = N_S.bit_length() - 1
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": "n=2^24 lognormal(0,2) weights, 2^20 guide cells, 2^28 iid + "
-                               "2^28 sorted radical-inverse samples, backward on the iid set",
+        "config": {"workload": f"n=2^24 lognormal(0,2) weights, 2^20 guide cells, "
+                               f"2^{lg} iid + 2^{lg} sorted radical-inverse samples, "
+                               f"backward on the iid set",
                    "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
         "breakdown_ms": avg,
         "build_elem_per_s": N_W / (avg["build"] * 1e-3),
@@ -385,7 +388,7 @@ def extra_ragged(dev, reps=3):
             max_m=int(ms[d]), nodes=f.nodes.data_ptr() + 16 * int(off[d]),
             guide=f.guide.data_ptr() + 4 * int(goff[d]),
             dists=f.dists.data_ptr() + 64 * d, status=f.status.data_ptr(),
-            guide_nodes=f.guide_nodes.data_ptr() + 16 * int(goff[d]))
+            guide_recs=f.guide_recs.data_ptr() + 32 * int(goff[d]))
         structs.append((ctypes.c_void_p(w.data_ptr() + 4 * int(off[d])), int(sizes[d]),
                         int(ms[d]), cf))
     wsp, wsn = ctypes.c_void_p(ws.data_ptr()), ws.numel()
@@ -513,7 +516,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged-batch, 2-D map and backward measurements")
+    ap.add_argument("--samples-log2", type=int, default=28,
+                    help="2^k samples per set; the benchmarked workload is k = 28, smaller k "
+                         "gives the same structure with fewer samples (profiler captures)")
     args = ap.parse_args()
+    global N_S
+    N_S = 1 << args.samples_log2
     if args.impl == "reference":
         return reference_arm(args)
     return gpu_arm(args)

@@ -94,6 +94,32 @@ typedef struct rtf_node {
 } rtf_node;
 
 /*
+ * Guide record of one cell, 32 bytes (Sec. 3.2: the guide table points to the
+ * root of the cell's tree; here the entry carries the root's decision itself).
+ *
+ *   cdf, child  a copy of the record of the cell's root, or {C_i, ~i, ~i} for
+ *               a cell that one interval i covers.
+ *   lo          lower CDF bound of the interval reached through child[0] of
+ *               the root: C_{j0-1} (0 for j0 = 0); C_i for a covered cell.
+ *   hi          upper CDF bound of the cell's last interval j1: C_{j1+1}, or T
+ *               when j1 = n - 1; C_{i+1} for a covered cell.
+ *
+ * The two neighbours of a leaf in the in-order sequence of a binary tree are
+ * its nearest ancestors entered from the right and from the left, so while
+ * descending, the lower bound of the final interval is the CDF value of the
+ * last node left through child[1] and its upper bound that of the last node
+ * left through child[0]; lo and hi stand in where such an ancestor lies
+ * outside the cell's tree.  The in-bin position (Sec. 5) thus needs no load
+ * after the descent.
+ */
+typedef struct rtf_guide_rec {
+  uint64_t cdf;
+  int32_t child[2];
+  uint64_t lo;
+  uint64_t hi;
+} rtf_guide_rec;
+
+/*
  * Per-distribution parameters, 64 bytes, in device memory.  The build writes
  * every field; the caller only allocates the array.
  */
@@ -118,17 +144,14 @@ typedef struct rtf_forest {
   int32_t num_dists; /* D >= 1 */
   int32_t flags;     /* RTF_FOREST_* */
   int64_t num_elems; /* N = sum of n_d: length of `nodes` */
-  int64_t num_cells; /* G = sum of 2^m_d: length of `guide` */
+  int64_t num_cells; /* G = sum of 2^m_d < 2^31: length of `guide` */
   int32_t max_m;     /* largest m_d (host copy; chooses the shared-memory guide path) */
   int32_t reserved;
   rtf_node *nodes;   /* device [N], 16-byte aligned */
   int32_t *guide;    /* device [G] */
   rtf_dist *dists;   /* device [D] */
   uint32_t *status;  /* device [1]: RTF_STATUS_* bits, set to 0 by each build */
-  rtf_node *guide_nodes; /* device [G], 16-byte aligned: per cell, a copy of the
-                            record of the cell's root, or {0, ~i, ~i} for a cell
-                            that one interval i covers, so that the sampler takes
-                            the root's decision from the guide entry itself */
+  rtf_guide_rec *guide_recs; /* device [G], 32-byte aligned: guide records */
 } rtf_forest;
 
 /* Library version string. */
@@ -154,7 +177,7 @@ size_t rtf_build_workspace_size(int64_t num_elems, int32_t num_dists,
  *   n        1 <= n <= 2^31 - 2^16.
  *   m        guide bits, 0 <= m <= 30: 2^m cells (Sec. 2.5, Sec. 3.2).
  *   f        f->num_dists == 1, f->num_elems == n, f->num_cells == 2^m,
- *            f->max_m == m; nodes[n], guide[2^m], guide_nodes[2^m], dists[1],
+ *            f->max_m == m; nodes[n], guide[2^m], guide_recs[2^m], dists[1],
  *            status[1] allocated.
  *   ws       device workspace of at least rtf_build_workspace_size(n, 1, 2^m)
  *            bytes, 256-byte aligned.

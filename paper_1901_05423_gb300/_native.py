@@ -97,7 +97,7 @@ class RtfForestC(ctypes.Structure):
         ("guide", ctypes.c_void_p),
         ("dists", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
-        ("guide_nodes", ctypes.c_void_p),
+        ("guide_recs", ctypes.c_void_p),
     ]
 
 

@@ -25,6 +25,7 @@ FOREST_MARGINAL = 0x1
 SAMPLE_1D = 0
 SAMPLE_2D = 1
 NODE_BYTES = 16
+GUIDE_REC_BYTES = 32
 DIST_BYTES = 64
 
 _workspaces: dict = {}
@@ -78,7 +79,7 @@ class Forest:
     device: torch.device
     nodes: torch.Tensor = field(init=False)   # uint8 [N * 16]
     guide: torch.Tensor = field(init=False)   # int32 [G]
-    guide_nodes: torch.Tensor = field(init=False)  # uint8 [G * 16]
+    guide_recs: torch.Tensor = field(init=False)   # uint8 [G * 32]
     dists: torch.Tensor = field(init=False)   # uint8 [D * 64]
     status: torch.Tensor = field(init=False)  # int32 [1]
     offsets: np.ndarray | None = None         # host copy of the element offsets
@@ -89,7 +90,8 @@ class Forest:
         dev = self.device
         self.nodes = torch.empty(self.num_elems * NODE_BYTES, dtype=torch.uint8, device=dev)
         self.guide = torch.empty(self.num_cells, dtype=torch.int32, device=dev)
-        self.guide_nodes = torch.empty(self.num_cells * NODE_BYTES, dtype=torch.uint8, device=dev)
+        self.guide_recs = torch.empty(self.num_cells * GUIDE_REC_BYTES, dtype=torch.uint8,
+                                      device=dev)
         self.dists = torch.empty(self.num_dists * DIST_BYTES, dtype=torch.uint8, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
 
@@ -99,7 +101,7 @@ class Forest:
             num_cells=self.num_cells, max_m=self.max_m, reserved=0,
             nodes=self.nodes.data_ptr(), guide=self.guide.data_ptr(),
             dists=self.dists.data_ptr(), status=self.status.data_ptr(),
-            guide_nodes=self.guide_nodes.data_ptr())
+            guide_recs=self.guide_recs.data_ptr())
 
     # views of the device structure (for tests and inspection)
     def cdf(self) -> torch.Tensor:
@@ -107,8 +109,8 @@ class Forest:
         return self.nodes.view(torch.int64).view(self.num_elems, 2)[:, 0]
 
     def guide_records(self) -> torch.Tensor:
-        """guide_nodes as int64 [G, 2] (cdf, packed children)."""
-        return self.guide_nodes.view(torch.int64).view(self.num_cells, 2)
+        """guide records as int64 [G, 4]: cdf, packed children, lo, hi."""
+        return self.guide_recs.view(torch.int64).view(self.num_cells, 4)
 
     def children(self) -> torch.Tensor:
         """child[0], child[1] of every record, int32 [N, 2]."""

@@ -29,9 +29,10 @@ constexpr int64_t kMaxElems = (int64_t(1) << 31) - (int64_t(1) << 16);
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 bool forest_ok(const rtf_forest* f) {
-  return f && f->nodes && f->guide && f->dists && f->status && f->guide_nodes &&
-         aligned(f->guide_nodes, 16) && f->num_dists >= 1 &&
+  return f && f->nodes && f->guide && f->dists && f->status && f->guide_recs &&
+         aligned(f->guide_recs, 32) && f->num_dists >= 1 &&
          f->num_elems >= 1 && f->num_elems <= kMaxElems && f->num_cells >= 1 &&
+         f->num_cells < (int64_t(1) << 31) &&
          f->max_m >= 0 && f->max_m <= 30 && aligned(f->nodes, 16) && aligned(f->status, 4);
 }
 
@@ -41,7 +42,7 @@ rtf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RTF_OK : RTF_E
 
 extern "C" {
 
-const char* rtf_version(void) { return "rtf 0.1.0 (sm_103a)"; }
+const char* rtf_version(void) { return "rtf 0.2.0 (sm_103a)"; }
 
 const char* rtf_status_string(rtf_status s) {
   switch (s) {

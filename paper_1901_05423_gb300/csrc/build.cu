@@ -398,13 +398,17 @@ constexpr int kForestPer = kTile / kForestThreads;  // 4
 static_assert(kForestPer == 4, "the otherBounds write-out stores one int4 per thread");
 constexpr int32_t kUnset = 0x7FFFFFFF;
 
+template <bool SEG>
 struct ForestShared {
-  alignas(16) float w[kTile + 4];
   alignas(16) uint64_t C[kTile + 2];  // C_{t0-1} .. C_{t1}
   alignas(16) uint64_t K[kTile + 2];  // K_{t0-1} .. K_{t1}
   alignas(16) int32_t child[kTile][2];
-  int32_t other[kTile];
-  int32_t dist[kTile];
+  // the staged weights are dead once q is known; the tile's otherBounds reuse them
+  union alignas(16) WO {
+    float w[kTile + 4];
+    int32_t other[kTile + 4];
+  } wo;
+  int32_t dist[SEG ? kTile : 1];
   uint8_t delta[kTile + 4];  // delta_{t0-1} .. delta_{t1-1}
   SegPair wtot[kForestThreads / 32];
   SegPair btot;
@@ -413,11 +417,13 @@ struct ForestShared {
   int dfirst;
   int dprev;
   int ndefer;
-  int64_t defer_parent[kDeferCap];
-  int64_t defer_lo[kDeferCap];
-  int64_t defer_hi[kDeferCap];
+  float wprev;
+  uint64_t prefix;
+  rtf_dist P0;  // parameters of the tile's first distribution
+  int32_t defer_parent[kDeferCap];
+  int32_t defer_bound[kDeferCap];
   int32_t defer_node[kDeferCap];
-  int32_t defer_child[kDeferCap];
+  int32_t defer_dist[kDeferCap];
 };
 
 struct ForestArgs {
@@ -428,8 +434,9 @@ struct ForestArgs {
   int64_t n_shared;
   rtf_node* nodes;
   int32_t* guide;
-  rtf_node* guide_nodes;
+  rtf_guide_rec* guide_recs;
   int32_t* last;
+  uint64_t* last_lo;
   const uint64_t* tile_prefix;
   const uint32_t* dmax;
   uint8_t* delta;
@@ -445,30 +452,38 @@ __device__ __forceinline__ uint64_t key_for(const rtf_dist& P, uint64_t C) {
 }
 
 // Root of a finished cell [lo, hi] (global element indices) of distribution P:
-// guide entry and last-leaf entry of the cell.  K_lo / K_hi are the keys.
+// guide entry, guide record and last-leaf entries of the cell.  K_lo / K_hi
+// are the keys of leaves lo and hi; C_{lo-1} (0 when lo is the first leaf of
+// the distribution), C_lo, C_hi and C_{hi+1} (T after the last leaf) their
+// CDF bounds.
 __device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist& P, int64_t lo,
-                                            int64_t hi, uint64_t Klo, uint64_t Khi, uint64_t Clo,
-                                            int32_t top) {
+                                            int64_t hi, uint64_t Klo, uint64_t Khi,
+                                            uint64_t Clm1, uint64_t Clo, uint64_t Chi,
+                                            uint64_t Chp1, int32_t top) {
   uint64_t c = cell_of(Klo, P.m);
   if (c >= (1ull << P.m)) return;  // unreachable trailing cell of zero-width bins
   int32_t lo_l = (int32_t)(lo - P.elem_off), hi_l = (int32_t)(hi - P.elem_off);
   uint64_t start = c << (32 - P.m);
   const int64_t gi = P.guide_off + (int64_t)c;
-  rtf_node rec;
+  rtf_guide_rec rec;
+  rec.hi = Chp1;
   if (Khi == start) {
     // one interval covers the whole cell (all its keys equal the cell start)
     a.guide[gi] = ~hi_l;
-    rec.cdf = 0;
+    rec.cdf = Chi;
     rec.child[0] = ~hi_l;
     rec.child[1] = ~hi_l;
+    rec.lo = Chi;
   } else {
     a.guide[gi] = lo_l;
     rec.cdf = Clo;
     rec.child[0] = ~(lo_l > 0 ? lo_l - 1 : 0);
     rec.child[1] = top;
+    rec.lo = Clm1;
   }
-  a.guide_nodes[gi] = rec;
+  a.guide_recs[gi] = rec;
   a.last[gi] = hi_l;
+  a.last_lo[gi] = Chi;
 }
 
 // Continue Algorithm 1 through global memory from range [lo, hi] with node
@@ -485,8 +500,10 @@ __device__ void climb_global(const ForestArgs& a, const rtf_dist& P, int64_t lo,
       int32_t lo_l = (int32_t)(lo - P.elem_off);
       root->child[0] = ~(lo_l > 0 ? lo_l - 1 : 0);
       root->child[1] = node;
-      const uint64_t Clo = a.nodes[lo].cdf;
-      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, a.nodes[hi].cdf), Clo, node);
+      const uint64_t Clo = a.nodes[lo].cdf, Chi = a.nodes[hi].cdf;
+      const uint64_t Clm1 = lo_l > 0 ? a.nodes[lo - 1].cdf : 0ull;
+      const uint64_t Chp1 = hi + 1 < P.elem_off + P.n ? a.nodes[hi + 1].cdf : P.total;
+      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, Chi), Clm1, Clo, Chi, Chp1, node);
       return;
     }
     int child = dl > dr ? 0 : 1;
@@ -519,29 +536,40 @@ __device__ void run_deferred(const ForestArgs& a, uint4 it) {
   climb_global(a, P, lo, hi, (int32_t)(parent - P.elem_off));
 }
 
+// Minimum resident forest blocks per SM given to the register allocator.
+#ifndef RTF_FOREST_MINB
+#define RTF_FOREST_MINB 1
+#endif
+
 template <bool SEG>
-__global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
+__global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel(ForestArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ForestShared& s = *reinterpret_cast<ForestShared*>(smem_raw);
+  ForestShared<SEG>& s = *reinterpret_cast<ForestShared<SEG>*>(smem_raw);
   const int64_t tile = blockIdx.x;
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
+  const int tn = (int)(t1 - t0);
   const int tid = threadIdx.x;
 
   if (tid == 0) {
-    int df = SEG ? find_dist(a.dists, 0, a.D - 1, t0) : 0;
+    const int df = SEG ? find_dist(a.dists, 0, a.D - 1, t0) : 0;
     s.dfirst = df;
     s.dprev = (t0 > 0 && SEG) ? (a.dists[df].elem_off == t0 ? df - 1 : df) : df;
     s.ndefer = 0;
+    // loads needed later, issued while the tile is staged
+    s.P0 = a.dists[df];
+    s.prefix = t0 > 0 ? a.tile_prefix[tile] : 0ull;
+    s.wprev = (t0 > 0 && t0 - 1 < a.Nw) ? a.w[t0 - 1] : 0.0f;
   }
   int wo = 0;
-  if (t0 < a.Nw) wo = stage_weights(s.w, a.w, t0, min(t1, a.Nw), &s.bar, &s.ok, a.status);
+  if (t0 < a.Nw) wo = stage_weights(s.wo.w, a.w, t0, min(t1, a.Nw), &s.bar, &s.ok, a.status);
   else __syncthreads();
   const int dfirst = s.dfirst;
 
-  // ---- q, C, keys and distances of the thread's leaves ----------------------
+  // ---- q, C and keys of the thread's leaves ---------------------------------
   // Each thread owns kForestPer consecutive leaves; the parameters of the
   // distribution it is in stay in registers (reloaded only at a boundary).
-  const int64_t e0 = t0 + (int64_t)tid * kForestPer;
+  const int l0 = tid * kForestPer;  // tile-local index of the first leaf
+  const int64_t e0 = t0 + l0;
   uint64_t q[kForestPer], incl[kForestPer];
   int dk[kForestPer];
   uint32_t headmask = 0;
@@ -551,41 +579,45 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
     int S = 0;
     int32_t flags = 0;
     int64_t off = 0;
-    if (e0 < t1) {
+    if (l0 < tn) {
       if (SEG) {
         dcur = find_dist(a.dists, dfirst, min(a.D - 1, dfirst + kTile), e0);
         next = dcur + 1 < a.D ? a.dists[dcur + 1].elem_off : INT64_MAX;
+        const rtf_dist P = a.dists[dcur];
+        flags = P.flags;
+        off = P.elem_off;
+        S = P.scale;
+      } else {
+        flags = s.P0.flags;
+        off = s.P0.elem_off;
+        S = s.P0.scale;
       }
-      const rtf_dist P = a.dists[dcur];
-      flags = P.flags;
-      off = P.elem_off;
-      S = (flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
     }
     uint64_t run = 0;
 #pragma unroll
     for (int k = 0; k < kForestPer; ++k) {
       const int64_t e = e0 + k;
       uint64_t qq = 0;
-      if (e < t1) {
+      if (l0 + k < tn) {
         if (SEG && e >= next) {
           ++dcur;
           next = dcur + 1 < a.D ? a.dists[dcur + 1].elem_off : INT64_MAX;
           const rtf_dist P = a.dists[dcur];
           flags = P.flags;
           off = P.elem_off;
-          S = (flags & kDistMarginal) ? 0 : dist_scale(P, a.dmax, dcur, a.n_shared);
+          S = P.scale;
         }
         if (off == e) {
           headmask |= 1u << k;
           run = 0;
         }
-        if (flags & kDistMarginal) {
+        if (SEG && (flags & kDistMarginal)) {
           qq = __ldcg(&a.dists[e - off].total);
         } else {
-          const uint32_t b = weight_bits(s.w[wo + (e - t0)]);
+          const uint32_t b = weight_bits(s.wo.w[wo + l0 + k]);
           qq = weight_bad(b) ? 0ull : quantize_bits(b, S);
         }
-        if (SEG) s.dist[e - t0] = dcur;
+        if (SEG) s.dist[l0 + k] = dcur;
       }
       dk[k] = dcur;
       q[k] = qq;
@@ -593,21 +625,20 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
       incl[k] = run;
     }
     SegPair agg{run, headmask ? 1u : 0u};
-    SegPair ex = block_seg_exclusive(agg, s.wtot, &s.btot);
+    SegPair ex = block_seg_exclusive(agg, s.wtot, &s.btot);  // also retires s.wo.w
     const bool head0 = SEG ? (a.dists[dfirst].elem_off == t0) : (t0 == 0);
-    const uint64_t E = head0 ? 0ull : a.tile_prefix[tile];
+    const uint64_t E = head0 ? 0ull : s.prefix;
     const uint64_t base = ex.f ? ex.s : ex.s + E;
-    // keys of the thread's leaves (and of C_{t1} for the tile's last leaf)
     int dP = -1;
     uint64_t T = 0, R = 0;
     int z = 0;
 #pragma unroll
     for (int k = 0; k < kForestPer; ++k) {
-      const int64_t e = e0 + k;
-      if (e >= t1) break;
+      const int l = l0 + k;
+      if (l >= tn) break;
       if (dk[k] != dP) {
         dP = dk[k];
-        const rtf_dist P = a.dists[dP];
+        const rtf_dist& P = SEG ? a.dists[dP] : s.P0;
         T = P.total;
         R = P.recip;
         z = P.shift;
@@ -615,12 +646,15 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
       const bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
       const uint64_t inc = seen_head ? incl[k] : base + incl[k];
       const uint64_t C = inc - q[k];
-      s.C[e - t0 + 1] = C;
-      s.K[e - t0 + 1] = key_of(C, T, R, z);
-      if (e == t1 - 1) {
-        s.C[t1 - t0 + 1] = inc;  // C_{t1} within the distribution of t1-1
-        s.K[t1 - t0 + 1] = key_of(inc, T, R, z);
+      s.C[l + 1] = C;
+      s.K[l + 1] = key_of(C, T, R, z);
+      if (l == tn - 1) {
+        s.C[tn + 1] = inc;  // C_{t1} within the distribution of t1-1
+        s.K[tn + 1] = key_of(inc, T, R, z);
       }
+      s.wo.other[l] = -1;
+      s.child[l][0] = kUnset;
+      s.child[l][1] = kUnset;
     }
   }
   // C_{t0-1} and its key (only meaningful when t0-1 belongs to the same distribution)
@@ -628,18 +662,17 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
     s.C[0] = 0;
     s.K[0] = 0;
     if (t0 > 0 && s.dprev == dfirst) {
-      const rtf_dist P = a.dists[dfirst];
+      const rtf_dist& P = s.P0;
       uint64_t qp;
-      if (P.flags & kDistMarginal) {
+      if (SEG && (P.flags & kDistMarginal)) {
         qp = __ldcg(&a.dists[t0 - 1 - P.elem_off].total);
       } else {
-        const uint32_t b = weight_bits(a.w[t0 - 1]);
-        qp = weight_bad(b) ? 0ull : quantize_bits(b, dist_scale(P, a.dmax, dfirst, a.n_shared));
+        const uint32_t b = weight_bits(s.wprev);
+        qp = weight_bad(b) ? 0ull : quantize_bits(b, P.scale);
       }
-      // C_{t0} is the tile prefix: this thread's first leaf when t0 is not a head
-      const uint64_t Ct0 = a.tile_prefix[tile];
-      s.C[0] = Ct0 - qp;
-      s.K[0] = key_for(P, Ct0 - qp);
+      const uint64_t Cp = s.prefix - qp;  // C_{t0} is the tile prefix
+      s.C[0] = Cp;
+      s.K[0] = key_for(P, Cp);
     }
   }
   __syncthreads();
@@ -651,33 +684,33 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
     uint32_t packed = 0;
 #pragma unroll
     for (int k = 0; k < kForestPer; ++k) {
-      const int64_t j = e0 + k;
+      const int l = l0 + k;
       uint32_t dlt = kDeltaInf;
-      if (j < t1) {
+      if (l < tn) {
         if (dk[k] != dP) {
           dP = dk[k];
-          const rtf_dist P = a.dists[dP];
+          const rtf_dist& P = SEG ? a.dists[dP] : s.P0;
           m = P.m;
           end = P.elem_off + P.n;
         }
-        if (j + 1 < end) {
-          const uint64_t Ka = s.K[j - t0 + 1], Kb = s.K[j - t0 + 2];
+        if (t0 + l + 1 < end) {
+          const uint64_t Ka = s.K[l + 1], Kb = s.K[l + 2];
           if (cell_of(Ka, m) == cell_of(Kb, m)) dlt = key_distance(Ka, Kb);
         }
-        s.delta[j - t0 + 1] = (uint8_t)dlt;
+        s.delta[l + 1] = (uint8_t)dlt;
       }
       packed |= dlt << (8 * k);
     }
-    if (e0 + kForestPer <= t1) {
+    if (l0 + kForestPer <= tn) {
       *reinterpret_cast<uint32_t*>(a.delta + e0) = packed;
     } else {
-      for (int k = 0; k < kForestPer && e0 + k < t1; ++k)
+      for (int k = 0; k < kForestPer && l0 + k < tn; ++k)
         a.delta[e0 + k] = (uint8_t)(packed >> (8 * k));
     }
     if (tid == 0) {
       uint32_t d0 = kDeltaInf;
       if (t0 > 0 && s.dprev == dfirst) {
-        const int mm = a.dists[dfirst].m;
+        const int mm = s.P0.m;
         const uint64_t Ka = s.K[0], Kb = s.K[1];
         if (cell_of(Ka, mm) == cell_of(Kb, mm)) d0 = key_distance(Ka, Kb);
       }
@@ -685,92 +718,89 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
       if (t0 > 0) a.delta[t0 - 1] = (uint8_t)d0;
     }
   }
-  for (int k = tid; k < (int)(t1 - t0); k += kForestThreads) {
-    s.child[k][0] = kUnset;
-    s.child[k][1] = kUnset;
-    s.other[k] = -1;
-  }
   __syncthreads();
 
-  // ---- phase A: Algorithm 1 inside the tile --------------------------------
+  // ---- phase A: Algorithm 1 inside the tile (tile-local indices) -----------
+  // delta[l] is the distance left of leaf l, delta[l + 1] the one right of it.
 #pragma unroll 1
   for (int k = 0; k < kForestPer; ++k) {
-    int64_t j = e0 + k;
-    if (j >= t1) break;
-    const int d = SEG ? s.dist[j - t0] : 0;
-    const int64_t off = a.dists[d].elem_off;
-    int64_t lo = j, hi = j;
-    int32_t node = ~(int32_t)(j - off);
+    const int l = l0 + k;
+    if (l >= tn) break;
+    const int d = SEG ? s.dist[l] : 0;
+    const int32_t base_id = (int32_t)(t0 - (SEG ? a.dists[d].elem_off : s.P0.elem_off));
+    int lo = l, hi = l;
+    int32_t node = ~(base_id + l);
     while (true) {
-      uint32_t dl = s.delta[lo - t0];
-      uint32_t dr = s.delta[hi - t0 + 1];
+      const uint32_t dl = s.delta[lo];
+      const uint32_t dr = s.delta[hi + 1];
       if (dl >= kDeltaInf && dr >= kDeltaInf) {
         // full cell inside the tile: its root is the node of the first leaf
-        int32_t lo_l = (int32_t)(lo - off);
-        s.child[lo - t0][0] = ~(lo_l > 0 ? lo_l - 1 : 0);
-        s.child[lo - t0][1] = node;
-        rtf_dist P = a.dists[d];
-        finish_cell(a, P, lo, hi, s.K[lo - t0 + 1], s.K[hi - t0 + 1], s.C[lo - t0 + 1], node);
+        const int32_t lo_id = base_id + lo;
+        s.child[lo][0] = ~(lo_id > 0 ? lo_id - 1 : 0);
+        s.child[lo][1] = node;
+        const rtf_dist& P = SEG ? a.dists[d] : s.P0;
+        // s.C[l + 1] is C of tile leaf l; s.C[0] that of t0 - 1 (same distribution)
+        const uint64_t Clm1 = lo_id > 0 ? s.C[lo] : 0ull;
+        const uint64_t Chp1 = t0 + hi + 1 == P.elem_off + P.n ? P.total : s.C[hi + 2];
+        finish_cell(a, P, t0 + lo, t0 + hi, s.K[lo + 1], s.K[hi + 1], Clm1, s.C[lo + 1],
+                    s.C[hi + 1], Chp1, node);
         break;
       }
-      int child = dl > dr ? 0 : 1;
-      if ((child == 1 && lo == t0) || (child == 0 && hi == t1 - 1)) {
-        int slot = atomicAdd(&s.ndefer, 1);
+      const int child = dl > dr ? 0 : 1;
+      if ((child == 1 && lo == 0) || (child == 0 && hi == tn - 1)) {
+        // the sibling lies in the neighbouring tile
+        const int slot = atomicAdd(&s.ndefer, 1);
         if (slot < kDeferCap) {
-          s.defer_parent[slot] = child ? lo : hi + 1;
-          s.defer_child[slot] = child;
+          s.defer_parent[slot] = (int32_t)(t0 + (child ? lo : hi + 1));
+          s.defer_bound[slot] = (int32_t)(t0 + (child ? hi : lo));
           s.defer_node[slot] = node;
-          s.defer_lo[slot] = lo;
-          s.defer_hi[slot] = hi;
+          s.defer_dist[slot] = d;
         }
         break;
       }
-      int64_t parent = child ? lo : hi + 1;
-      s.child[parent - t0][child] = node;
-      int ob = atomicExch(&s.other[parent - t0], (int)((child ? hi : lo) - t0));
+      const int parent = child ? lo : hi + 1;
+      s.child[parent][child] = node;
+      const int ob = atomicExch(&s.wo.other[parent], child ? hi : lo);
       if (ob < 0) break;
-      s.other[parent - t0] = -2;
+      s.wo.other[parent] = -2;
       if (child)
-        lo = t0 + ob;
+        lo = ob;
       else
-        hi = t0 + ob;
-      node = (int32_t)(parent - off);
+        hi = ob;
+      node = base_id + parent;
     }
   }
   __syncthreads();
 
-  // ---- node records --------------------------------------------------------
+  // ---- node records and the tile's otherBounds slice -------------------------
+  // otherBounds: the far bound of every first arrival still waiting for its
+  // sibling, -1 everywhere else
+  int ob4[kForestPer];
 #pragma unroll
   for (int k = 0; k < kForestPer; ++k) {
-    int64_t j = e0 + k;
-    if (j >= t1) break;
-    int i = (int)(j - t0);
-    int32_t c0 = s.child[i][0], c1 = s.child[i][1];
-    uint64_t C = s.C[i + 1];
+    const int l = l0 + k;
+    if (l >= tn) break;
+    const int32_t c0 = s.child[l][0], c1 = s.child[l][1];
+    const uint64_t C = s.C[l + 1];
+    rtf_node* rec = a.nodes + t0 + l;
     if (c0 != kUnset && c1 != kUnset) {
       rtf_node r;
       r.cdf = C;
       r.child[0] = c0;
       r.child[1] = c1;
-      a.nodes[j] = r;
+      *rec = r;
     } else {
-      a.nodes[j].cdf = C;
-      if (c0 != kUnset) a.nodes[j].child[0] = c0;
-      if (c1 != kUnset) a.nodes[j].child[1] = c1;
+      rec->cdf = C;
+      if (c0 != kUnset) rec->child[0] = c0;
+      if (c1 != kUnset) rec->child[1] = c1;
     }
+    const int o = s.wo.other[l];
+    ob4[k] = o >= 0 ? (int)(t0 + o) : -1;
   }
-  // this tile's slice of the global otherBounds: the far bound of every first
-  // arrival still waiting for its sibling, -1 everywhere else
-  if (e0 + kForestPer <= t1) {
-    int4 ob;
-    ob.x = s.other[e0 - t0 + 0] >= 0 ? (int)(t0 + s.other[e0 - t0 + 0]) : -1;
-    ob.y = s.other[e0 - t0 + 1] >= 0 ? (int)(t0 + s.other[e0 - t0 + 1]) : -1;
-    ob.z = s.other[e0 - t0 + 2] >= 0 ? (int)(t0 + s.other[e0 - t0 + 2]) : -1;
-    ob.w = s.other[e0 - t0 + 3] >= 0 ? (int)(t0 + s.other[e0 - t0 + 3]) : -1;
-    *reinterpret_cast<int4*>(a.other + e0) = ob;
+  if (l0 + kForestPer <= tn) {
+    *reinterpret_cast<int4*>(a.other + e0) = make_int4(ob4[0], ob4[1], ob4[2], ob4[3]);
   } else {
-    for (int64_t j = e0; j < t1; ++j)
-      a.other[j] = s.other[j - t0] >= 0 ? (int)(t0 + s.other[j - t0]) : -1;
+    for (int k = 0; k < kForestPer && l0 + k < tn; ++k) a.other[e0 + k] = ob4[k];
   }
 
   // ---- hand-offs across tile edges -------------------------------------------
@@ -783,11 +813,9 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(ForestArgs a) {
     a.item_count[tile] = min(nd, kDeferCap);
   }
   if (tid < min(nd, kDeferCap)) {
-    const int child = s.defer_child[tid];
-    const int64_t bound = child ? s.defer_hi[tid] : s.defer_lo[tid];
-    const int d = SEG ? s.dist[s.defer_lo[tid] - t0] : 0;
-    a.items[tile * kDeferCap + tid] = make_uint4((uint32_t)s.defer_parent[tid], (uint32_t)bound,
-                                                 (uint32_t)s.defer_node[tid], (uint32_t)d);
+    a.items[tile * kDeferCap + tid] =
+        make_uint4((uint32_t)s.defer_parent[tid], (uint32_t)s.defer_bound[tid],
+                   (uint32_t)s.defer_node[tid], (uint32_t)s.defer_dist[tid]);
   }
 }
 
@@ -807,8 +835,9 @@ __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t
 constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 16
 
 __global__ void __launch_bounds__(kGuideThreads)
-    guide_kernel(int64_t G, const int32_t* __restrict__ last, int32_t* guide,
-                 rtf_node* guide_nodes, uint64_t* gstatus, Counters* ctr, uint32_t* status) {
+    guide_kernel(int64_t G, const int32_t* __restrict__ last, const uint64_t* __restrict__ last_lo,
+                 int32_t* guide, rtf_guide_rec* guide_recs, uint64_t* gstatus, Counters* ctr,
+                 uint32_t* status) {
   __shared__ uint32_t tile_s;
   __shared__ int32_t wlast[kGuideThreads / 32];
   __shared__ int32_t carry_s;
@@ -818,15 +847,16 @@ __global__ void __launch_bounds__(kGuideThreads)
   const int64_t tile = tile_s;
   const int64_t g0 = tile * kGuideTile + (int64_t)threadIdx.x * kGuidePer;
   const int64_t gend = min(tile * kGuideTile + (int64_t)kGuideTile, G);
-  int32_t v[kGuidePer];
+  // the carried value is the index of the last non-empty cell (G < 2^31)
+  bool full[kGuidePer];
   int32_t tlast = -1;
 #pragma unroll
   for (int k = 0; k < kGuidePer; ++k) {
     int64_t g = g0 + k;
-    v[k] = g < gend ? last[g] : -1;
-    if (v[k] >= 0) tlast = v[k];
+    full[k] = g < gend && last[g] >= 0;
+    if (full[k]) tlast = (int32_t)g;
   }
-  // last valid value of all threads before this one (warp, then block)
+  // last non-empty cell of all threads before this one (warp, then block)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t inc = tlast;
 #pragma unroll
@@ -851,11 +881,11 @@ __global__ void __launch_bounds__(kGuideThreads)
     else
       st_release_u64(gstatus + tile, kFlagAgg);
   }
-  // the incoming carry is needed only when the tile's first cell has no key
+  // the incoming carry is needed only when the tile's first cell is empty
   __shared__ int need_s;
   if (threadIdx.x == 0) {
     carry_s = -1;
-    need_s = (g0 < gend && v[0] < 0) ? 1 : 0;
+    need_s = (g0 < gend && !full[0]) ? 1 : 0;
   }
   __syncthreads();
   if (need_s) {
@@ -867,20 +897,34 @@ __global__ void __launch_bounds__(kGuideThreads)
     }
   }
   __syncthreads();
-  int32_t carry = before >= 0 ? before : carry_s;
+  int32_t src = before >= 0 ? before : carry_s;
+  rtf_guide_rec rec;
+  int32_t rec_src = -1;
 #pragma unroll
   for (int k = 0; k < kGuidePer; ++k) {
     int64_t g = g0 + k;
     if (g >= gend) break;
-    if (v[k] >= 0) {
-      carry = v[k];
+    if (full[k]) {
+      src = (int32_t)g;
     } else {
-      guide[g] = ~carry;
-      rtf_node rec;
-      rec.cdf = 0;
-      rec.child[0] = ~carry;
-      rec.child[1] = ~carry;
-      guide_nodes[g] = rec;
+      if (src < 0) {
+        // cell 0 of a distribution always holds key 0, so this is unreachable;
+        // the record refers to no interval (the sampler returns -1 through it)
+        raise_status(status, RTF_STATUS_BAD_PLAN);
+        rec = rtf_guide_rec{0ull, {INT32_MIN, INT32_MIN}, 0ull, 0ull};
+        rec_src = -1;
+      } else if (src != rec_src) {
+        // the last interval of cell src covers this cell
+        rec_src = src;
+        const int32_t i = last[src];
+        rec.lo = last_lo[src];
+        rec.cdf = rec.lo;
+        rec.child[0] = ~i;
+        rec.child[1] = ~i;
+        rec.hi = guide_recs[src].hi;
+      }
+      guide[g] = rec.child[0];
+      guide_recs[g] = rec;
     }
   }
 }
@@ -950,8 +994,9 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.n_shared = n_shared;
   fa.nodes = f->nodes;
   fa.guide = f->guide;
-  fa.guide_nodes = f->guide_nodes;
+  fa.guide_recs = f->guide_recs;
   fa.last = last;
+  fa.last_lo = reinterpret_cast<uint64_t*>(base + L.last_lo);
   fa.tile_prefix = tile_prefix;
   fa.dmax = dmax;
   fa.delta = delta;
@@ -959,13 +1004,14 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.items = items;
   fa.item_count = item_count;
   fa.status = f->status;
-  const size_t fsmem = sizeof(ForestShared);
   if (seg) {
+    const size_t fsmem = sizeof(ForestShared<true>);
     if ((e = cudaFuncSetAttribute(forest_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)fsmem)))
       return e;
     forest_kernel<true><<<(unsigned)num_tiles(N), kForestThreads, fsmem, st>>>(fa);
   } else {
+    const size_t fsmem = sizeof(ForestShared<false>);
     if ((e = cudaFuncSetAttribute(forest_kernel<false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
       return e;
@@ -976,7 +1022,8 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
     forest_merge_kernel<<<(unsigned)((nt * kDeferCap + 127) / 128), 128, 0, st>>>(fa, nt);
   }
   const int64_t gtiles = (G + kGuideTile - 1) / kGuideTile;
-  guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, f->guide, f->guide_nodes,
+  guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, fa.last_lo, f->guide,
+                                                            f->guide_recs,
                                                            guide_status, ctr, f->status);
   return cudaGetLastError();
 }

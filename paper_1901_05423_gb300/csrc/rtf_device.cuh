@@ -42,6 +42,7 @@ struct WsLayout {
   size_t guide_status; // u64 [num_guide_tiles]
   size_t zero_end;
   size_t last;         // i32 [G] last leaf of each non-empty cell (set to -1)
+  size_t last_lo;      // u64 [G] lower CDF bound of that leaf
   size_t tile_prefix;  // u64 [num_tiles]
   size_t tile_sum;     // u64 [num_tiles]
   size_t tile_first;   // u64 [num_tiles]
@@ -69,6 +70,7 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   o = align256(o + sizeof(uint64_t) * (size_t)((G + kGuideTile - 1) / kGuideTile));
   L.zero_end = o;
   L.last = o; o = align256(o + sizeof(int32_t) * (size_t)G);
+  L.last_lo = o; o = align256(o + sizeof(uint64_t) * (size_t)G);
   L.tile_prefix = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
   L.tile_sum = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
   L.tile_first = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
@@ -184,13 +186,18 @@ __device__ inline uint64_t total_recip(uint64_t T, int z) {
   return div128_64(~Tn, ~0ull, Tn);
 }
 
-// Key K = ceil(C 2^32 / T): the smallest u with t(u) >= C.  A multiply by the
-// reciprocal gives a value at most two below K; two exact checks finish it.
+// Key K = ceil(C 2^32 / T): the smallest u with t(u) >= C.  With X = C << z
+// and Tn = T << z, one multiply by the reciprocal gives Q' = floor(X 2^64 / Tn)
+// or one less, so X 2^64 / Tn lies in [Q', Q' + 2).  Unless the low word of Q'
+// is 0 or 2^32 - 1 that interval sits strictly between two multiples of 2^32
+// and K = (Q' >> 32) + 1; next to a multiple, two exact checks decide.
 __device__ __forceinline__ uint64_t key_of(uint64_t C, uint64_t T, uint64_t R, int z) {
   if (C >= T) return 1ull << 32;
-  uint64_t X = C << z;
-  uint64_t Q = __umul64hi(X, R) + X;
+  const uint64_t X = C << z;
+  const uint64_t Q = __umul64hi(X, R) + X;
+  const uint32_t lo = (uint32_t)Q;
   uint64_t v = Q >> 32;
+  if (lo != 0u && lo != 0xFFFFFFFFu) return v + 1;
   if (t_of(v, T) < C) {
     ++v;
     if (t_of(v, T) < C) ++v;

@@ -3,17 +3,21 @@
 //
 // Per sample u (xi = u / 2^32):
 //   g = u >> (32 - m)                       guide cell (Algorithm 2, first line)
-//   j = guide[g]                            ~i, or the root of the cell's tree
 //   t = floor(u T / 2^32)                   the sample in the integer CDF domain
-//   while j >= 0: j = t < C_j ? child0 : child1     (xi < data[j], Algorithm 2)
+//   {c, j0, j1, lo, hi} = guide record g    the decision of the cell's root
+//   j = t < c ? j0 : j1, then while j >= 0: j = t < C_j ? child0 : child1
 //   i = ~j;  pos = (u T - C_i 2^32) / (q_i 2^32)     (Sec. 5)
 //
 // The node records interleave C_j with the children (16 bytes), so one load
-// per visited node serves both the comparison and the next index.  Node loads
-// carry an L2 evict-last policy (the structure stays resident while the
-// sample stream passes through with evict-first loads and streaming stores).
-// When the guide table of a single distribution is small it is staged in
-// shared memory once per block.
+// per visited node serves both the comparison and the next index.  C_i and
+// C_{i+1} are tracked on the way down: every step to child[1] passes the lower
+// bound of the final interval, every step to child[0] its upper bound, and the
+// guide record holds the two bounds that lie outside the cell's tree; so the
+// position needs no load after the descent.  Node loads carry an L2
+// evict-last policy (the structure stays resident while the sample stream
+// passes through with evict-first loads and streaming stores).  When the guide
+// table of a single distribution is small it is staged in shared memory once
+// per block.
 #include <cstdint>
 
 #include "rtf_device.cuh"
@@ -21,7 +25,7 @@
 namespace rtf {
 
 constexpr int kSampleThreads = 256;
-constexpr int kSmemGuideMaxBits = 11;  // 32 KB of guide records in shared memory
+constexpr int kSmemGuideMaxBits = 10;  // 32 KB of guide records in shared memory
 
 // Tunables of the single-distribution sampler (compile-time): samples per
 // thread descending in lockstep, the minimum resident blocks per SM given to
@@ -65,10 +69,15 @@ __device__ __forceinline__ void load_node(const rtf_node* p, uint64_t pol, uint6
   c1 = (int32_t)(uint32_t)(b >> 32);
 }
 
-__device__ __forceinline__ uint64_t load_cdf(const rtf_node* p, uint64_t pol) {
-  uint64_t a;
-  asm("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(a) : "l"(p), "l"(pol));
-  return a;
+__device__ __forceinline__ void load_guide(const rtf_guide_rec* p, uint64_t pol, uint64_t& cdf,
+                                           int32_t& c0, int32_t& c1, uint64_t& lo,
+                                           uint64_t& hi) {
+  uint64_t b;
+  asm("ld.global.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], %5;"
+      : "=l"(cdf), "=l"(b), "=l"(lo), "=l"(hi)
+      : "l"(p), "l"(pol));
+  c0 = (int32_t)(uint32_t)(b & 0xffffffffull);
+  c1 = (int32_t)(uint32_t)(b >> 32);
 }
 
 // t = floor(u T / 2^32) and r = (u T) mod 2^32 from two 32 x 32 -> 64 products
@@ -102,15 +111,15 @@ __device__ __forceinline__ float in_bin_position(uint64_t d, uint32_t r, uint64_
 }
 
 struct DistView {
-  const rtf_node* nodes;  // records of the distribution
-  const rtf_node* guide;  // its guide records
+  const rtf_node* nodes;        // records of the distribution
+  const rtf_guide_rec* guide;  // its guide records
   uint64_t T;
   int64_t n;
   int m;
 };
 
 __device__ __forceinline__ DistView dist_view(const rtf_dist* dists, int d, const rtf_node* nodes,
-                                              const rtf_node* guide) {
+                                              const rtf_guide_rec* guide) {
   rtf_dist P = dists[d];
   DistView v;
   v.nodes = nodes + P.elem_off;
@@ -127,38 +136,37 @@ __device__ __forceinline__ DistView dist_view(const rtf_dist* dists, int d, cons
 // and the descent is capped at 64 visits (a reachable path visits at most
 // 2 + (32 - m) nodes), so a structure left invalid by a failed build yields
 // idx = -1 instead of an out-of-bounds read.
-//
-// After the descent one of C_i, C_{i+1} is the CDF value of the last node
-// visited (its own leaf on a right step, its left neighbour on a left step);
-// the other is loaded.  A guide hit loads both.
 template <int K, bool SMEM>
-__device__ __forceinline__ void sample_group(const DistView& v, const int32_t* gsm,
+__device__ __forceinline__ void sample_group(const DistView& v, const rtf_guide_rec* gsm,
                                              const uint32_t (&uu)[K], uint64_t pol,
                                              int32_t (&idx)[K], float (&pos)[K]) {
-  // CDF values are below 2^62, so 2^63 marks "no CDF value known yet"
-  constexpr uint64_t kNone = 1ull << 63;
   const uint32_t n32 = (uint32_t)v.n;
   int32_t j[K];
-  uint64_t t[K], clast[K];
+  uint64_t t[K], lo[K], hi[K];
   uint32_t r[K];
   // the guide record takes the root's decision (left neighbour interval or the
-  // cell's tree); a cell that one interval covers holds {0, ~i, ~i}
+  // cell's tree); a cell that one interval i covers holds {C_i, ~i, ~i}
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint32_t g = v.m ? (uu[k] >> (32 - v.m)) : 0u;
     scale_sample(uu[k], v.T, t[k], r[k]);
-    uint64_t c;
+    uint64_t c, glo, ghi;
     int32_t c0, c1;
     if (SMEM) {
-      const uint4 e = reinterpret_cast<const uint4*>(gsm)[g];
-      c = ((uint64_t)e.y << 32) | e.x;
-      c0 = (int32_t)e.z;
-      c1 = (int32_t)e.w;
+      const uint4* e = reinterpret_cast<const uint4*>(gsm + g);
+      const uint4 a = e[0], b = e[1];
+      c = ((uint64_t)a.y << 32) | a.x;
+      c0 = (int32_t)a.z;
+      c1 = (int32_t)a.w;
+      glo = ((uint64_t)b.y << 32) | b.x;
+      ghi = ((uint64_t)b.w << 32) | b.z;
     } else {
-      load_node(v.guide + g, pol, c, c0, c1);
+      load_guide(v.guide + g, pol, c, c0, c1, glo, ghi);
     }
-    j[k] = t[k] < c ? c0 : c1;
-    clast[k] = c0 != c1 ? c : kNone;
+    const bool left = t[k] < c;
+    j[k] = left ? c0 : c1;
+    lo[k] = left ? glo : c;
+    hi[k] = left ? c : ghi;
   }
   bool live = false;
 #pragma unroll
@@ -183,34 +191,23 @@ __device__ __forceinline__ void sample_group(const DistView& v, const int32_t* g
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (j[k] >= 0) {
-        j[k] = t[k] < c[k] ? c0[k] : c1[k];
-        clast[k] = c[k];
+        const bool left = t[k] < c[k];
+        j[k] = left ? c0[k] : c1[k];
+        if (left)
+          hi[k] = c[k];
+        else
+          lo[k] = c[k];
         live |= j[k] >= 0;
       }
     }
   }
   bad |= live;  // a descent longer than any reachable path
-  uint64_t clo[K], chi[K];
-  bool ok[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint32_t i = (uint32_t)~j[k];
-    ok[k] = !bad && i < n32;
-    // the last node visited holds C_{i+1} after a left step, C_i after a right one
-    const bool have_hi = clast[k] != kNone && t[k] < clast[k];
-    const bool have_lo = clast[k] != kNone && !have_hi;
-    clo[k] = clast[k];
-    chi[k] = clast[k];
-    if (ok[k]) {
-      if (!have_lo) clo[k] = load_cdf(v.nodes + i, pol);
-      if (!have_hi) chi[k] = (i + 1 < n32) ? load_cdf(v.nodes + i + 1, pol) : v.T;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (ok[k]) {
-      idx[k] = ~j[k];
-      pos[k] = in_bin_position(t[k] - clo[k], r[k], chi[k] - clo[k]);
+    if (!bad && i < n32 && lo[k] <= t[k] && t[k] < hi[k]) {
+      idx[k] = (int32_t)i;
+      pos[k] = in_bin_position(t[k] - lo[k], r[k], hi[k] - lo[k]);
     } else {
       idx[k] = -1;
       pos[k] = 0.0f;
@@ -219,7 +216,7 @@ __device__ __forceinline__ void sample_group(const DistView& v, const int32_t* g
 }
 
 template <bool SMEM>
-__device__ __forceinline__ void sample_one(const DistView& v, const int32_t* gsm, uint32_t u,
+__device__ __forceinline__ void sample_one(const DistView& v, const rtf_guide_rec* gsm, uint32_t u,
                                            uint64_t pol, int32_t& idx, float& pos) {
   uint32_t uu[1] = {u};
   int32_t ii[1];
@@ -233,14 +230,15 @@ __device__ __forceinline__ void sample_one(const DistView& v, const int32_t* gsm
 // (u, idx and pos move as 16-byte vectors, four samples each).
 template <bool SMEM>
 __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
-    sample_single_kernel(const rtf_node* __restrict__ nodes, const rtf_node* __restrict__ guide,
+    sample_single_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                          const rtf_dist* __restrict__ dists, const uint32_t* __restrict__ u,
                          int64_t count, int32_t* __restrict__ idx_out,
                          float* __restrict__ pos_out, int cap_bits, uint32_t* status) {
   constexpr int K = RTF_SAMPLE_K;
   static_assert(K == 1 || K == 2 || K == 4 || K == 8, "samples per thread");
   constexpr int V = K >= 4 ? K / 4 : 1;   // 16-byte vectors per step
-  extern __shared__ int32_t gsm[];
+  extern __shared__ __align__(16) int32_t gsm_words[];
+  const rtf_guide_rec* gsm = reinterpret_cast<const rtf_guide_rec*>(gsm_words);
   const DistView v = dist_view(dists, 0, nodes, guide);
   if (SMEM && v.m > cap_bits) {
     // the host's max_m understated the guide size: refuse rather than overrun
@@ -248,9 +246,10 @@ __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
     return;
   }
   if (SMEM) {
-    const int words = 4 << v.m;
-    const int32_t* src = reinterpret_cast<const int32_t*>(v.guide);
-    for (int k = threadIdx.x; k < words; k += blockDim.x) gsm[k] = src[k];
+    const int vecs = 2 << v.m;
+    const uint4* src = reinterpret_cast<const uint4*>(v.guide);
+    uint4* dst = reinterpret_cast<uint4*>(gsm_words);
+    for (int k = threadIdx.x; k < vecs; k += blockDim.x) dst[k] = src[k];
     __syncthreads();
   }
   const uint64_t pol = l2_evict_last_policy();
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
 
 // 1-D with a distribution id per sample.
 __global__ void __launch_bounds__(kSampleThreads)
-    sample_tagged_kernel(const rtf_node* __restrict__ nodes, const rtf_node* __restrict__ guide,
+    sample_tagged_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                          const rtf_dist* __restrict__ dists, int D,
                          const uint32_t* __restrict__ u, const int32_t* __restrict__ dist_id,
                          int64_t count, int32_t* __restrict__ idx_out,
@@ -337,7 +336,7 @@ __global__ void __launch_bounds__(kSampleThreads)
 // 2-D: the row through the marginal (last distribution) with u1, the column
 // through that row's distribution with u2 (Sec. 5).
 __global__ void __launch_bounds__(kSampleThreads)
-    sample_2d_kernel(const rtf_node* __restrict__ nodes, const rtf_node* __restrict__ guide,
+    sample_2d_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                      const rtf_dist* __restrict__ dists, int D, const uint2* __restrict__ u,
                      int64_t count, int2* __restrict__ idx_out, float2* __restrict__ pos_out) {
   const uint64_t pol = l2_evict_last_policy();
@@ -379,27 +378,27 @@ cudaError_t launch_sample(const rtf_forest* f, const uint32_t* u, const int32_t*
   if (mode == RTF_SAMPLE_2D) {
     int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
     sample_2d_kernel<<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide_nodes, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
+        f->nodes, f->guide_recs, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
         reinterpret_cast<int2*>(idx_out), reinterpret_cast<float2*>(pos_out));
     return cudaGetLastError();
   }
   if (dist_id != nullptr) {
     int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
     sample_tagged_kernel<<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide_nodes, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
+        f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
         f->status);
     return cudaGetLastError();
   }
   const int64_t per_block = (int64_t)kSampleThreads * 4;
   if (f->max_m <= kSmemGuideMaxBits && f->num_dists >= 1) {
-    size_t smem = sizeof(rtf_node) << f->max_m;
+    size_t smem = sizeof(rtf_guide_rec) << f->max_m;
     int64_t blocks = min((int64_t)sms * 8, (count + per_block - 1) / per_block);
     sample_single_kernel<true><<<(unsigned)blocks, kSampleThreads, smem, st>>>(
-        f->nodes, f->guide_nodes, f->dists, u, count, idx_out, pos_out, f->max_m, f->status);
+        f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out, f->max_m, f->status);
   } else {
     int64_t blocks = min((int64_t)sms * 8, (count + per_block - 1) / per_block);
     sample_single_kernel<false><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide_nodes, f->dists, u, count, idx_out, pos_out, 31, f->status);
+        f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out, 31, f->status);
   }
   return cudaGetLastError();
 }

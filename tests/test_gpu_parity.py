@@ -49,17 +49,30 @@ def check_structure(f, ref, elem_off=0, guide_off=0, n=None, cells=None):
     assert bad.size == 0, f"{bad.size} node records differ, first {bad[:5]}"
     badg = np.nonzero(g != ref.guide)[0]
     assert badg.size == 0, f"{badg.size} guide cells differ, first {badg[:5]}"
-    # guide records: a copy of each root's record, {0, ~i, ~i} for one interval
-    rec = f.guide_nodes.view(torch.int32).view(f.num_cells, 4)[guide_off:guide_off + cells]
-    rec = rec.cpu().numpy()
-    rec_c = rec[:, 0:2].copy().view(np.uint64).reshape(-1)
+    # guide records: a copy of each root's record with the bounds C_{j0-1} and
+    # C_{j1+1} of the cell's outer intervals; {C_i, ~i, ~i, C_i, C_{i+1}} for a
+    # cell that one interval i covers
+    rec = f.guide_records()[guide_off:guide_off + cells].cpu().numpy()
+    rec_c = rec[:, 0].view(np.uint64)
+    rec_ch = rec[:, 1:2].copy().view(np.int32)
+    rec_lo = rec[:, 2].view(np.uint64)
+    rec_hi = rec[:, 3].view(np.uint64)
+    _, cell = orc.keys(ref.C, cells)
+    g_idx = np.arange(cells)
     root = ref.guide >= 0
     j0 = np.where(root, ref.guide, 0)
-    exp_c = np.where(root, ref.C[j0], np.uint64(0))
+    j1 = np.searchsorted(cell, g_idx, side="right") - 1  # last leaf whose key lies in g
+    i = np.where(root, 0, ~ref.guide)
+    exp_c = np.where(root, ref.C[j0], ref.C[i])
     exp_c0 = np.where(root, ref.nodes[j0, 0], ref.guide)
     exp_c1 = np.where(root, ref.nodes[j0, 1], ref.guide)
+    exp_lo = np.where(root, ref.C[np.maximum(j0 - 1, 0)], ref.C[i])
+    exp_hi = np.where(root, ref.C[np.clip(j1 + 1, 0, n)], ref.C[i + 1])
     assert np.array_equal(rec_c, exp_c), "guide record CDF"
-    assert np.array_equal(rec[:, 2], exp_c0) and np.array_equal(rec[:, 3], exp_c1), "guide record children"
+    assert np.array_equal(rec_ch[:, 0], exp_c0) and np.array_equal(rec_ch[:, 1], exp_c1), \
+        "guide record children"
+    assert np.array_equal(rec_lo, exp_lo), "guide record lower bound"
+    assert np.array_equal(rec_hi, exp_hi), "guide record upper bound"
 
 
 def check_samples(idx, pos, ridx, rpos):
