@@ -33,6 +33,22 @@ METRIC = "samples/s & build elem/s at n=2^24 (bit-exact); batched vs looped; % H
 N_W = 1 << 24
 M_BITS = 20
 N_S = 1 << 28
+# kernels of this library per step: build 7 (init_dists, scale, tile_sum,
+# tile_scan, forest, forest_merge, guide), sampling 2, backward 3 (scatter,
+# bin_total, suffix)
+LAUNCHES_PER_STEP = 12
+
+
+# DRAM bytes per unit measured by ncu at full size (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch / units per launch; profiles/launches_bench_n24.md).
+# Valid for the kernels as they were captured; set an entry to None when its
+# kernel changes until the capture is repeated.
+DRAM_BYTES_PER_UNIT = {
+    "sample_iid": (38.208e9 + 2.144e9) / (1 << 28),
+    "sample_sorted": (1.376e9 + 2.085e9) / (1 << 28),
+    "backward": None,
+    "build": None,
+}
 
 
 def measured_peaks():
@@ -298,6 +314,9 @@ def gpu_arm(args):
     }
     dom = max(avg, key=avg.get)
     achieved = alg[dom] / (avg[dom] * 1e-3) / 1e9
+    units = {"build": N_W, "sample_iid": N_S, "sample_sorted": N_S, "backward": N_S}
+    per_unit = DRAM_BYTES_PER_UNIT.get(dom)
+    traffic = per_unit * units[dom] if per_unit is not None else None
     value = world * 2 * N_S / (ms * 1e-3)
     lg = N_S.bit_length() - 1
     line = {
@@ -314,12 +333,13 @@ def gpu_arm(args):
         "sample_iid_per_s": N_S / (avg["sample_iid"] * 1e-3),
         "sample_sorted_per_s": N_S / (avg["sample_sorted"] * 1e-3),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_GBps": traffic / (avg[dom] * 1e-3) / 1e9 if traffic else None,
                      "peak_kind": peak_kind},
         "fractions_of_hbm": {k: alg[k] / (avg[k] * 1e-3) / 1e9 / peak for k in avg},
         "e2e": {"value": world * 2 * N_S / (e2e_ms * 1e-3), "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_extras:
