@@ -214,6 +214,43 @@ __global__ void __launch_bounds__(kScanThreads)
   const int wo = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
   const int dfirst = dfirst_s;
 
+  if (!SEG) {
+    // one distribution: the tile's sum of q; the last tile also holds the
+    // distribution's end (finished here when the tile is also the first)
+    const int S = dist_scale(dists[0], dmax, 0, n_shared);
+    const int l0 = threadIdx.x * kScanPer;
+    uint64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if (t0 + l0 + k < t1) {
+        const uint32_t b = weight_bits(wsm[wo + l0 + k]);
+        run += weight_bad(b) ? 0ull : quantize_bits(b, S);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
+    if ((threadIdx.x & 31) == 0) wtot[threadIdx.x >> 5].s = run;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t sum = 0;
+      for (int k = 0; k < kScanThreads / 32; ++k) sum += wtot[k].s;
+      const bool head0 = t0 == 0;
+      uint32_t meta = head0 ? 3u : 0u;
+      if (t1 == Nw) {
+        if (head0) {
+          finish_dist(dists, 0, sum, S, status);
+        } else {
+          ts.first[tile] = sum;
+          meta |= 4u;
+        }
+      }
+      ts.sum[tile] = sum;
+      ts.meta[tile] = meta;
+      ts.dist0[tile] = 0;
+    }
+    return;
+  }
+
   // per-thread run of kScanPer consecutive weights
   const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
   uint64_t incl[kScanPer];
@@ -538,7 +575,7 @@ __device__ void run_deferred(const ForestArgs& a, uint4 it) {
 
 // Minimum resident forest blocks per SM given to the register allocator.
 #ifndef RTF_FOREST_MINB
-#define RTF_FOREST_MINB 1
+#define RTF_FOREST_MINB 3
 #endif
 
 template <bool SEG>
@@ -832,7 +869,7 @@ __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t
 // ---------------------------------------------------------------------------
 // guide: cells without keys take the interval of the last key before them
 // ---------------------------------------------------------------------------
-constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 16
+constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 4
 
 __global__ void __launch_bounds__(kGuideThreads)
     guide_kernel(int64_t G, const int32_t* __restrict__ last, const uint64_t* __restrict__ last_lo,

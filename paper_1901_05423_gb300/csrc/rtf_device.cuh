@@ -19,8 +19,8 @@ namespace rtf {
 constexpr int kTile = 2048;           // weights per scan / forest tile
 constexpr int kScanThreads = 256;     // scan kernel: 8 weights per thread
 constexpr int kForestThreads = 512;   // forest kernel: 4 leaves per thread
-constexpr int kGuideTile = 4096;      // guide cells per guide-fill tile
-constexpr int kGuideThreads = 256;    // 16 cells per thread
+constexpr int kGuideTile = 1024;      // guide cells per guide-fill tile
+constexpr int kGuideThreads = 256;    // 4 cells per thread
 constexpr int kMaxThreads = 512;
 constexpr uint32_t kDeltaInf = 64;    // distance across a cell / distribution boundary
 constexpr long long kSpinLimit = 1ll << 22;   // bounded waits

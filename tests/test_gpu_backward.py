@@ -53,6 +53,18 @@ def test_backward_small():
     assert rel_err(gw, gref) <= TOL
 
 
+def test_backward_few_samples_per_bin():
+    """Far fewer samples than bins: most bins get no sample."""
+    gw, gref = run_1d(1 << 16, 5000, 12, seed=5)
+    assert rel_err(gw, gref) <= TOL
+
+
+def test_backward_ragged_tail():
+    """n not a multiple of the 2048-element tiles of the suffix scan."""
+    gw, gref = run_1d(3 * 8192 + 1234, 1 << 18, 12, seed=6)
+    assert rel_err(gw, gref) <= TOL
+
+
 def test_backward_single_bin_is_zero():
     w = np.array([3.0], np.float32)
     u = W.iid_u32(4096, seed=1)
