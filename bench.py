@@ -344,7 +344,8 @@ def gpu_arm(args):
     }
     if rank == 0 and not args.no_extras:
         line["extras"] = {"ragged_batch": extra_ragged(dev), "env_map_2d": extra_env_map(dev),
-                          "backward_vs_forward": extra_backward(dev)}
+                          "backward_vs_forward": extra_backward(dev),
+                          "forest_vs_binary_search": extra_methods(dev)}
     if rank == 0 and not args.no_cpu_baseline:
         cb = time_oracle(w, u_iid, u_sorted, gx)
         line["cpu_baseline"] = {"value": cb["value"], "unit": "samples/s", "cores": 1,
@@ -525,6 +526,51 @@ def extra_backward(dev, reps=5):
     bwd = b.elapsed_time(c) / reps
     return {"workload": "n=2^20 lognormal(0,1), 2^18 guide cells, 2^24 iid samples",
             "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd}
+
+
+def extra_methods(dev, reps=5):
+    """The radix forest against the paper's comparator, the cutpoint method
+    with binary search, on the same structure: the load statistics of
+    Table 1 (maximum, average, average over groups of 32 of the group maximum)
+    for its four densities at n = 1024 with 2^10 cells and 2^20 i.i.d.
+    samples, and both methods timed at n = 2^24, 2^20 cells on 2^26 i.i.d. and
+    2^26 sorted samples (bins and positions are identical)."""
+    import torch
+    from paper_1901_05423_gb300 import api
+    from paper_1901_05423_gb300 import workloads as W
+    methods = (("radix_forest", api.SAMPLE_1D), ("binary_search", api.SAMPLE_1D | api.SAMPLE_BSEARCH))
+    table = {}
+    u = api.u32_tensor(W.iid_u32(1 << 20, seed=5), dev)
+    for kind in W.TABLE1_KINDS:
+        f = api.rtf_build(torch.from_numpy(W.table1_weights(kind)).to(dev), 10)
+        table[kind] = {name: api.load_statistics(api.rtf_sample_loads(f, u, mode=mode))
+                       for name, mode in methods}
+        f.check_status()
+    w = torch.from_numpy(W.lognormal_weights(N_W, seed=0, sigma=2.0)).to(dev)
+    f = api.rtf_build(w, M_BITS)
+    main_loads = {name: api.load_statistics(api.rtf_sample_loads(f, u, mode=mode))
+                  for name, mode in methods}
+    ns = 1 << 26
+    times = {}
+    for set_name, uh in (("iid", W.iid_u32(ns, seed=6)), ("sorted", W.sorted_radical_inverse_u32(ns))):
+        ud = api.u32_tensor(uh, dev)
+        idx = torch.empty(ns, dtype=torch.int32, device=dev)
+        pos = torch.empty(ns, dtype=torch.float32, device=dev)
+        for name, mode in methods:
+            api.rtf_sample(f, ud, mode=mode, idx_out=idx, pos_out=pos)
+            torch.cuda.synchronize()
+            a, b = _events()
+            a.record()
+            for _ in range(reps):
+                api.rtf_sample(f, ud, mode=mode, idx_out=idx, pos_out=pos)
+            b.record()
+            torch.cuda.synchronize()
+            times[f"{set_name}_{name}_ms"] = a.elapsed_time(b) / reps
+        del ud, idx, pos
+    f.check_status()
+    return {"workload": "Table 1 densities (n=1024, 2^10 cells, 2^20 iid samples); "
+                        "n=2^24 lognormal(0,2), 2^20 cells, 2^26 iid / sorted samples",
+            "table1_loads": table, "n24_loads": main_loads, **times}
 
 
 def main():

@@ -74,6 +74,10 @@ typedef enum rtf_status {
 /* rtf_sample / rtf_sample_backward modes */
 #define RTF_SAMPLE_1D 0 /* one sample u per output; dist_id selects the distribution */
 #define RTF_SAMPLE_2D 1 /* (u1, u2) pairs; row from the marginal, column from the row */
+/* flag OR-ed into the mode of rtf_sample: the cutpoint method with a binary
+   search (the paper's comparator, Sec. 2.5) on the same structure instead of
+   the radix forest; identical bins and positions */
+#define RTF_SAMPLE_BSEARCH 0x100
 
 /*
  * One node record, 16 bytes, in device memory.  Record j of a distribution
@@ -251,11 +255,27 @@ rtf_status rtf_build_batched(const float *w, const int64_t *offsets,
  *   marginal, u2 the column through that row (Sec. 5).  idx_out int32[2 count]
  *   receives (row, column), pos_out float32[2 count] (row position, column
  *   position).
+ * RTF_SAMPLE_BSEARCH may be OR-ed into either mode: each sample is then
+ *   found by a binary search over the CDF between the first intervals of its
+ *   cell and of the next cell (the cutpoint method), not by a tree descent.
  * u, idx_out and pos_out must be 16-byte aligned; count >= 0.
  */
 rtf_status rtf_sample(const rtf_forest *f, const uint32_t *u,
                       const int32_t *dist_id, int64_t count, int32_t mode,
                       int32_t *idx_out, float *pos_out, void *stream);
+
+/*
+ * Number of loads from the structure that each sample takes under the method
+ * of `mode` (RTF_SAMPLE_1D, optionally | RTF_SAMPLE_BSEARCH): guide records
+ * plus node records (radix forest) or CDF values (binary search), the
+ * quantity of the paper's Table 1.  u and dist_id as for rtf_sample (4-byte
+ * alignment suffices); loads_out int32[count] receives the counts, -1 for a
+ * sample that found no interval.  One thread per sample, no positions: an
+ * analysis aid, not a sampling path.
+ */
+rtf_status rtf_sample_loads(const rtf_forest *f, const uint32_t *u,
+                            const int32_t *dist_id, int64_t count, int32_t mode,
+                            int32_t *loads_out, void *stream);
 
 /* Bytes of workspace rtf_sample_backward needs. */
 size_t rtf_backward_workspace_size(int64_t num_elems, int32_t num_dists);

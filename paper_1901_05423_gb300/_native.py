@@ -117,6 +117,9 @@ EXPORTS = {
     "rtf_sample": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "rtf_sample_loads": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     "rtf_backward_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
     "rtf_sample_backward": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -24,6 +24,7 @@ STATUS_BAD_PLAN = 0x8
 FOREST_MARGINAL = 0x1
 SAMPLE_1D = 0
 SAMPLE_2D = 1
+SAMPLE_BSEARCH = 0x100  # flag: cutpoint method + binary search instead of the forest
 NODE_BYTES = 16
 GUIDE_REC_BYTES = 32
 DIST_BYTES = 64
@@ -221,8 +222,9 @@ def rtf_sample(forest: Forest, u: torch.Tensor, dist_id: torch.Tensor | None = N
     _need(u, u.dtype, "u")
     if dist_id is not None:
         _need(dist_id, torch.int32, "dist_id")
-    count = u.numel() // (2 if mode == SAMPLE_2D else 1)
-    shape = (count, 2) if mode == SAMPLE_2D else (count,)
+    two_d = (mode & 0xFF) == SAMPLE_2D
+    count = u.numel() // (2 if two_d else 1)
+    shape = (count, 2) if two_d else (count,)
     if idx_out is None:
         idx_out = torch.empty(shape, dtype=torch.int32, device=u.device)
     if pos_out is None:
@@ -232,6 +234,32 @@ def rtf_sample(forest: Forest, u: torch.Tensor, dist_id: torch.Tensor | None = N
     _check(lib.rtf_sample(ctypes.byref(cf), _ptr(u), _ptr(dist_id), count, mode, _ptr(idx_out),
                           _ptr(pos_out), _stream_ptr(u.device)), "rtf_sample")
     return idx_out, pos_out
+
+
+def rtf_sample_loads(forest: Forest, u: torch.Tensor, dist_id: torch.Tensor | None = None,
+                     mode: int = SAMPLE_1D) -> torch.Tensor:
+    """Structure loads per sample under the method of `mode` (``rtf_sample_loads``)."""
+    if u.dtype not in (torch.int32, torch.uint32):
+        raise TypeError("u must hold uint32 bit patterns (int32 or uint32 tensor)")
+    count = u.numel()
+    loads = torch.empty(count, dtype=torch.int32, device=u.device)
+    lib = _native.load()
+    cf = forest.c_struct()
+    _check(lib.rtf_sample_loads(ctypes.byref(cf), _ptr(u), _ptr(dist_id), count, mode,
+                                _ptr(loads), _stream_ptr(u.device)), "rtf_sample_loads")
+    return loads
+
+
+def load_statistics(loads, group: int = 32) -> dict:
+    """Maximum, average and average over consecutive groups of `group` samples
+    of the group's maximum (the cost of samples that run in lockstep), the
+    three columns of the paper's Table 1."""
+    a = np.asarray(loads.cpu() if torch.is_tensor(loads) else loads, dtype=np.int64)
+    if a.size == 0 or (a < 0).any():
+        raise ValueError("load counts must be non-empty and non-negative")
+    g = a[: a.size - a.size % group].reshape(-1, group) if a.size >= group else a.reshape(1, -1)
+    return {"maximum": int(a.max()), "average": float(a.mean()),
+            "average32": float(g.max(axis=1).mean())}
 
 
 def rtf_sample_backward(forest: Forest, w: torch.Tensor, u: torch.Tensor,

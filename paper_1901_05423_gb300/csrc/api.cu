@@ -15,6 +15,8 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
 cudaError_t launch_sample(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
                           int64_t count, int mode, int32_t* idx_out, float* pos_out,
                           cudaStream_t st);
+cudaError_t launch_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
+                                int64_t count, int mode, int32_t* loads_out, cudaStream_t st);
 size_t backward_ws_bytes(int64_t N, int32_t D);
 cudaError_t launch_backward(const rtf_forest* f, const float* w, const uint32_t* u,
                             const int32_t* dist_id, const int32_t* idx, const float* pos,
@@ -101,13 +103,26 @@ rtf_status rtf_sample(const rtf_forest* f, const uint32_t* u, const int32_t* dis
   if (count == 0) return RTF_OK;
   if (!u || !idx_out || !pos_out) return RTF_EINVAL;
   if (!aligned(u, 16) || !aligned(idx_out, 16) || !aligned(pos_out, 16)) return RTF_EINVAL;
-  if (mode == RTF_SAMPLE_2D) {
+  if (mode & ~(0xFF | RTF_SAMPLE_BSEARCH)) return RTF_EINVAL;
+  const int32_t base = mode & 0xFF;
+  if (base == RTF_SAMPLE_2D) {
     if (!(f->flags & RTF_FOREST_MARGINAL) || dist_id) return RTF_EINVAL;
-  } else if (mode != RTF_SAMPLE_1D) {
+  } else if (base != RTF_SAMPLE_1D) {
     return RTF_EINVAL;
   }
   return cuda_status(rtf::launch_sample(f, u, dist_id, count, mode, idx_out, pos_out,
                                         static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
+                            int64_t count, int32_t mode, int32_t* loads_out, void* stream) {
+  if (!forest_ok(f) || count < 0) return RTF_EINVAL;
+  if (mode != RTF_SAMPLE_1D && mode != (RTF_SAMPLE_1D | RTF_SAMPLE_BSEARCH)) return RTF_EINVAL;
+  if (count == 0) return RTF_OK;
+  if (!u || !loads_out || !aligned(u, 4) || !aligned(loads_out, 4)) return RTF_EINVAL;
+  if (dist_id && !aligned(dist_id, 4)) return RTF_EINVAL;
+  return cuda_status(rtf::launch_sample_loads(f, u, dist_id, count, mode, loads_out,
+                                              static_cast<cudaStream_t>(stream)));
 }
 
 size_t rtf_backward_workspace_size(int64_t num_elems, int32_t num_dists) {

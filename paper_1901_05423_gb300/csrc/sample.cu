@@ -80,6 +80,18 @@ __device__ __forceinline__ void load_guide(const rtf_guide_rec* p, uint64_t pol,
   c1 = (int32_t)(uint32_t)(b >> 32);
 }
 
+__device__ __forceinline__ uint64_t load_cdf(const rtf_node* p, uint64_t pol) {
+  uint64_t a;
+  asm("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(a) : "l"(p), "l"(pol));
+  return a;
+}
+
+__device__ __forceinline__ int32_t load_child0(const rtf_guide_rec* p, uint64_t pol) {
+  int32_t a;
+  asm("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(a) : "l"(&p->child[0]), "l"(pol));
+  return a;
+}
+
 // t = floor(u T / 2^32) and r = (u T) mod 2^32 from two 32 x 32 -> 64 products
 // (T < 2^62, so u T_hi + floor(u T_lo / 2^32) cannot overflow).
 __device__ __forceinline__ void scale_sample(uint32_t u, uint64_t T, uint64_t& t, uint32_t& r) {
@@ -139,7 +151,8 @@ __device__ __forceinline__ DistView dist_view(const rtf_dist* dists, int d, cons
 template <int K, bool SMEM>
 __device__ __forceinline__ void sample_group(const DistView& v, const rtf_guide_rec* gsm,
                                              const uint32_t (&uu)[K], uint64_t pol,
-                                             int32_t (&idx)[K], float (&pos)[K]) {
+                                             int32_t (&idx)[K], float (&pos)[K],
+                                             int32_t (&nl)[K]) {
   const uint32_t n32 = (uint32_t)v.n;
   int32_t j[K];
   uint64_t t[K], lo[K], hi[K];
@@ -167,6 +180,7 @@ __device__ __forceinline__ void sample_group(const DistView& v, const rtf_guide_
     j[k] = left ? c0 : c1;
     lo[k] = left ? glo : c;
     hi[k] = left ? c : ghi;
+    nl[k] = 1;
   }
   bool live = false;
 #pragma unroll
@@ -184,6 +198,7 @@ __device__ __forceinline__ void sample_group(const DistView& v, const rtf_guide_
           j[k] = -1;
         } else {
           load_node(v.nodes + j[k], pol, c[k], c0[k], c1[k]);
+          ++nl[k];
         }
       }
     }
@@ -215,20 +230,139 @@ __device__ __forceinline__ void sample_group(const DistView& v, const rtf_guide_
   }
 }
 
-template <bool SMEM>
+// The comparator of the paper (Sec. 2.5): the cutpoint method, a guide table
+// that brackets the bins a cell can reach, with a binary search over the CDF
+// inside the bracket.  It runs on the same structure: the first interval of
+// cell g is ~child[0] of its guide record, the bracket ends at the first
+// interval of cell g + 1 (n - 1 after the last cell), a covered cell needs no
+// search, and lo, hi of the record are the CDF bounds of the bracket.  The
+// search keeps C_a <= t < C_{b+1} for its bracket [a, b], so both bounds of
+// the final interval are known when it ends.  Same bins and positions as the
+// radix forest; the number of dependent loads differs.
+template <int K, bool SMEM>
+__device__ __forceinline__ void sample_group_bsearch(const DistView& v, const rtf_guide_rec* gsm,
+                                                     const uint32_t (&uu)[K], uint64_t pol,
+                                                     int32_t (&idx)[K], float (&pos)[K],
+                                                     int32_t (&nl)[K]) {
+  const uint32_t n32 = (uint32_t)v.n;
+  const uint32_t cells = 1u << v.m;
+  uint32_t a[K], b[K];
+  uint64_t t[K], lo[K], hi[K];
+  uint32_t r[K];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t g = v.m ? (uu[k] >> (32 - v.m)) : 0u;
+    scale_sample(uu[k], v.T, t[k], r[k]);
+    uint64_t c, glo, ghi;
+    int32_t c0, c1;
+    if (SMEM) {
+      const uint4* e = reinterpret_cast<const uint4*>(gsm + g);
+      const uint4 x = e[0], y = e[1];
+      c = ((uint64_t)x.y << 32) | x.x;
+      c0 = (int32_t)x.z;
+      c1 = (int32_t)x.w;
+      glo = ((uint64_t)y.y << 32) | y.x;
+      ghi = ((uint64_t)y.w << 32) | y.z;
+    } else {
+      load_guide(v.guide + g, pol, c, c0, c1, glo, ghi);
+    }
+    (void)c;
+    a[k] = (uint32_t)~c0;
+    b[k] = a[k];
+    nl[k] = 1;
+    if (c0 != c1) {  // a cell with a tree: bracket up to the next cell's first interval
+      ++nl[k];
+      const int32_t nxt = g + 1 < cells ? (SMEM ? gsm[g + 1].child[0] : load_child0(v.guide + g + 1, pol))
+                                        : ~(int32_t)(n32 - 1);
+      b[k] = (uint32_t)~nxt;
+    }
+    if (a[k] >= n32 || b[k] >= n32 || a[k] > b[k]) {
+      bad = true;  // invalid structure
+      a[k] = b[k] = 0;
+    }
+    lo[k] = glo;
+    hi[k] = ghi;
+  }
+  bool live = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) live |= a[k] < b[k];
+#pragma unroll 1
+  for (int step = 0; live && step < 32; ++step) {
+    uint64_t cm[K];
+    uint32_t mid[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      mid[k] = a[k] + ((b[k] - a[k] + 1) >> 1);
+      if (a[k] < b[k]) {
+        cm[k] = load_cdf(v.nodes + mid[k], pol);
+        ++nl[k];
+      }
+    }
+    live = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (a[k] < b[k]) {
+        if (cm[k] <= t[k]) {
+          a[k] = mid[k];
+          lo[k] = cm[k];
+        } else {
+          b[k] = mid[k] - 1;
+          hi[k] = cm[k];
+        }
+        live |= a[k] < b[k];
+      }
+    }
+  }
+  bad |= live;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!bad && lo[k] <= t[k] && t[k] < hi[k]) {
+      idx[k] = (int32_t)a[k];
+      pos[k] = in_bin_position(t[k] - lo[k], r[k], hi[k] - lo[k]);
+    } else {
+      idx[k] = -1;
+      pos[k] = 0.0f;
+    }
+  }
+}
+
+// One of the two methods; nl receives the number of structure loads of each
+// sample (guide records, node or CDF records), which only the statistics
+// kernel stores.
+template <int K, bool SMEM, bool BS>
+__device__ __forceinline__ void sample_any(const DistView& v, const rtf_guide_rec* gsm,
+                                           const uint32_t (&uu)[K], uint64_t pol,
+                                           int32_t (&idx)[K], float (&pos)[K],
+                                           int32_t (&nl)[K]) {
+  if (BS)
+    sample_group_bsearch<K, SMEM>(v, gsm, uu, pol, idx, pos, nl);
+  else
+    sample_group<K, SMEM>(v, gsm, uu, pol, idx, pos, nl);
+}
+
+template <int K, bool SMEM, bool BS>
+__device__ __forceinline__ void sample_any(const DistView& v, const rtf_guide_rec* gsm,
+                                           const uint32_t (&uu)[K], uint64_t pol,
+                                           int32_t (&idx)[K], float (&pos)[K]) {
+  int32_t nl[K];
+  sample_any<K, SMEM, BS>(v, gsm, uu, pol, idx, pos, nl);
+}
+
+template <bool SMEM, bool BS>
 __device__ __forceinline__ void sample_one(const DistView& v, const rtf_guide_rec* gsm, uint32_t u,
                                            uint64_t pol, int32_t& idx, float& pos) {
   uint32_t uu[1] = {u};
   int32_t ii[1];
   float pp[1];
-  sample_group<1, SMEM>(v, gsm, uu, pol, ii, pp);
+  sample_any<1, SMEM, BS>(v, gsm, uu, pol, ii, pp);
   idx = ii[0];
   pos = pp[0];
 }
 
 // 1-D, one distribution (dist 0); RTF_SAMPLE_K samples per thread per step
 // (u, idx and pos move as 16-byte vectors, four samples each).
-template <bool SMEM>
+template <bool SMEM, bool BS>
 __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
     sample_single_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                          const rtf_dist* __restrict__ dists, const uint32_t* __restrict__ u,
@@ -272,7 +406,7 @@ __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
         uu[4 * t + 2] = x.z;
         uu[4 * t + 3] = x.w;
       }
-      sample_group<K, SMEM>(v, gsm, uu, pol, ii, pp);
+      sample_any<K, SMEM, BS>(v, gsm, uu, pol, ii, pp);
 #pragma unroll
       for (int t = 0; t < V; ++t) {
         __stcs(i4 + q * V + t, make_int4(ii[4 * t], ii[4 * t + 1], ii[4 * t + 2], ii[4 * t + 3]));
@@ -288,7 +422,7 @@ __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
       float pp[K];
 #pragma unroll
       for (int t = 0; t < K; ++t) uu[t] = __ldcs(u + q * K + t);
-      sample_group<K, SMEM>(v, gsm, uu, pol, ii, pp);
+      sample_any<K, SMEM, BS>(v, gsm, uu, pol, ii, pp);
 #pragma unroll
       for (int t = 0; t < K; ++t) {
         __stcs(idx_out + q * K + t, ii[t]);
@@ -302,13 +436,14 @@ __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
        s += (int64_t)gridDim.x * blockDim.x) {
     int32_t ii;
     float pp;
-    sample_one<SMEM>(v, gsm, u[s], pol, ii, pp);
+    sample_one<SMEM, BS>(v, gsm, u[s], pol, ii, pp);
     idx_out[s] = ii;
     pos_out[s] = pp;
   }
 }
 
 // 1-D with a distribution id per sample.
+template <bool BS>
 __global__ void __launch_bounds__(kSampleThreads)
     sample_tagged_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                          const rtf_dist* __restrict__ dists, int D,
@@ -324,7 +459,7 @@ __global__ void __launch_bounds__(kSampleThreads)
     float pp = 0.0f;
     if (d >= 0 && d < D) {
       const DistView v = dist_view(dists, d, nodes, guide);
-      sample_one<false>(v, nullptr, uu, pol, ii, pp);
+      sample_one<false, BS>(v, nullptr, uu, pol, ii, pp);
     } else {
       raise_status(status, RTF_STATUS_BAD_PLAN);
     }
@@ -333,8 +468,37 @@ __global__ void __launch_bounds__(kSampleThreads)
   }
 }
 
+// Structure loads per sample (the statistics of Table 1): one thread per
+// sample, guide records from global memory, 1-D modes.
+template <bool BS>
+__global__ void __launch_bounds__(kSampleThreads)
+    sample_loads_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
+                        const rtf_dist* __restrict__ dists, int D, const uint32_t* __restrict__ u,
+                        const int32_t* __restrict__ dist_id, int64_t count,
+                        int32_t* __restrict__ loads_out, uint32_t* status) {
+  const uint64_t pol = l2_evict_last_policy();
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < count;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int d = dist_id ? dist_id[s] : 0;
+    int32_t nl[1] = {0};
+    if (d >= 0 && d < D) {
+      const DistView v = dist_view(dists, d, nodes, guide);
+      uint32_t uu[1] = {u[s]};
+      int32_t ii[1];
+      float pp[1];
+      sample_any<1, false, BS>(v, nullptr, uu, pol, ii, pp, nl);
+      if (ii[0] < 0) nl[0] = -1;
+    } else {
+      raise_status(status, RTF_STATUS_BAD_PLAN);
+      nl[0] = -1;
+    }
+    loads_out[s] = nl[0];
+  }
+}
+
 // 2-D: the row through the marginal (last distribution) with u1, the column
 // through that row's distribution with u2 (Sec. 5).
+template <bool BS>
 __global__ void __launch_bounds__(kSampleThreads)
     sample_2d_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                      const rtf_dist* __restrict__ dists, int D, const uint2* __restrict__ u,
@@ -346,12 +510,12 @@ __global__ void __launch_bounds__(kSampleThreads)
     uint2 uu = __ldcs(u + s);
     int32_t r, c;
     float pr, pc;
-    sample_one<false>(marg, nullptr, uu.x, pol, r, pr);
+    sample_one<false, BS>(marg, nullptr, uu.x, pol, r, pr);
     c = -1;
     pc = 0.0f;
     if (r >= 0 && r < D - 1) {
       const DistView row = dist_view(dists, r, nodes, guide);
-      sample_one<false>(row, nullptr, uu.y, pol, c, pc);
+      sample_one<false, BS>(row, nullptr, uu.y, pol, c, pc);
     }
     __stcs(idx_out + s, make_int2(r, c));
     __stcs(pos_out + s, make_float2(pr, pc));
@@ -370,36 +534,59 @@ static int num_sms() {
   return g_num_sms;
 }
 
+template <bool BS>
+static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
+                            int64_t count, int mode, int32_t* idx_out, float* pos_out,
+                            cudaStream_t st) {
+  const int sms = num_sms();
+  if (mode == RTF_SAMPLE_2D) {
+    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
+    sample_2d_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
+        f->nodes, f->guide_recs, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
+        reinterpret_cast<int2*>(idx_out), reinterpret_cast<float2*>(pos_out));
+    return;
+  }
+  if (dist_id != nullptr) {
+    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
+    sample_tagged_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
+        f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
+        f->status);
+    return;
+  }
+  const int64_t per_block = (int64_t)kSampleThreads * 4;
+  int64_t blocks = min((int64_t)sms * 8, (count + per_block - 1) / per_block);
+  if (f->max_m <= kSmemGuideMaxBits) {
+    size_t smem = sizeof(rtf_guide_rec) << f->max_m;
+    sample_single_kernel<true, BS><<<(unsigned)blocks, kSampleThreads, smem, st>>>(
+        f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out, f->max_m, f->status);
+  } else {
+    sample_single_kernel<false, BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
+        f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out, 31, f->status);
+  }
+}
+
+cudaError_t launch_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
+                                int64_t count, int mode, int32_t* loads_out, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const int64_t blocks = min((int64_t)num_sms() * 8, (count + kSampleThreads - 1) / kSampleThreads);
+  if (mode & RTF_SAMPLE_BSEARCH)
+    sample_loads_kernel<true><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
+        f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, loads_out, f->status);
+  else
+    sample_loads_kernel<false><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
+        f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, loads_out, f->status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sample(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
                           int64_t count, int mode, int32_t* idx_out, float* pos_out,
                           cudaStream_t st) {
   if (count == 0) return cudaSuccess;
-  const int sms = num_sms();
-  if (mode == RTF_SAMPLE_2D) {
-    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
-    sample_2d_kernel<<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide_recs, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
-        reinterpret_cast<int2*>(idx_out), reinterpret_cast<float2*>(pos_out));
-    return cudaGetLastError();
-  }
-  if (dist_id != nullptr) {
-    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
-    sample_tagged_kernel<<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
-        f->status);
-    return cudaGetLastError();
-  }
-  const int64_t per_block = (int64_t)kSampleThreads * 4;
-  if (f->max_m <= kSmemGuideMaxBits && f->num_dists >= 1) {
-    size_t smem = sizeof(rtf_guide_rec) << f->max_m;
-    int64_t blocks = min((int64_t)sms * 8, (count + per_block - 1) / per_block);
-    sample_single_kernel<true><<<(unsigned)blocks, kSampleThreads, smem, st>>>(
-        f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out, f->max_m, f->status);
-  } else {
-    int64_t blocks = min((int64_t)sms * 8, (count + per_block - 1) / per_block);
-    sample_single_kernel<false><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
-        f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out, 31, f->status);
-  }
+  const int base = mode & 0xFF;
+  if (mode & RTF_SAMPLE_BSEARCH)
+    launch_sample_t<true>(f, u, dist_id, count, base, idx_out, pos_out, st);
+  else
+    launch_sample_t<false>(f, u, dist_id, count, base, idx_out, pos_out, st);
   return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "radical_inverse_u32", "sorted_radical_inverse_u32", "iid_u32",
     "uniform_weights", "lognormal_weights", "env_map", "ragged_batch",
-    "normal_f32",
+    "normal_f32", "table1_weights", "TABLE1_KINDS",
 ]
 
 
@@ -107,3 +107,36 @@ def dist_ids(count: int, num: int, seed: int) -> np.ndarray:
     """count distribution ids uniform on 0..num-1, int32."""
     rng = np.random.default_rng(seed)
     return rng.integers(0, num, size=count, dtype=np.int32)
+
+
+TABLE1_KINDS = ("i^20", "(i mod 32 + 1)^25", "(i mod 64 + 1)^35", "4 spikes")
+
+
+def table1_weights(kind: str, n: int = 1024, seed: int = 0) -> np.ndarray:
+    """The four density shapes of the paper's Table 1 (Fig. 13), scaled so the
+    largest weight is 1 (evaluated in float64, then rounded to float32, so the
+    smallest powers underflow to zero as they would in any float32 input):
+
+    ``i^20``, ``(i mod 32 + 1)^25``, ``(i mod 64 + 1)^35`` for i = 0..n-1, and
+    ``4 spikes``: the paper shows but does not define it; here four Gaussian
+    bumps of width n/256 at uniform random positions with heights 1, 1/2,
+    1/4, 1/8 over a floor of 1e-3.
+    """
+    i = np.arange(n, dtype=np.float64)
+    if kind == "i^20":
+        w = (i / (n - 1)) ** 20
+    elif kind == "(i mod 32 + 1)^25":
+        w = ((i % 32 + 1) / 32.0) ** 25
+    elif kind == "(i mod 64 + 1)^35":
+        w = ((i % 64 + 1) / 64.0) ** 35
+    elif kind == "4 spikes":
+        rng = np.random.default_rng(seed)
+        c = rng.uniform(0, n, 4)
+        s = n / 256.0
+        w = np.full(n, 1e-3)
+        for k in range(4):
+            w += 0.5 ** k * np.exp(-0.5 * ((i - c[k]) / s) ** 2)
+    else:
+        raise ValueError(f"unknown kind {kind!r}")
+    return w.astype(np.float32)
+

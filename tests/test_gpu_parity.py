@@ -388,3 +388,107 @@ def test_misaligned_weights(shift):
     for d in range(len(sizes)):
         ref = orc.build(w[shift + off[d]:shift + off[d + 1]], 1 << [2, 8, 7, 9][d])
         check_structure(fb, ref, elem_off=int(off[d]), guide_off=int(fb.guide_offsets[d]))
+
+
+# ---------------------------------------------------------------------------
+# cutpoint method + binary search on the same structure (RTF_SAMPLE_BSEARCH)
+# ---------------------------------------------------------------------------
+
+BS = api.SAMPLE_BSEARCH
+
+
+@pytest.mark.parametrize("m", [0, 3, 10, 11, 14])
+def test_bsearch_matches_oracle_all_weight_kinds(m):
+    """Shared-memory guide (m <= 10) and global guide (m >= 11) variants."""
+    rng = np.random.default_rng(100 + m)
+    for n, kind, w in weight_cases():
+        f = api.rtf_build(to_dev(w), m)
+        u = rng.integers(0, 1 << 32, 4096, dtype=np.uint64).astype(np.uint32)
+        u[:3] = [0, 1, 0xFFFFFFFF]
+        idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV), mode=api.SAMPLE_1D | BS)
+        torch.cuda.synchronize()
+        f.check_status()
+        ref = orc.build(w, 1 << m)
+        ridx, rpos = orc.sample(ref.C, u)
+        try:
+            check_samples(idx, pos, ridx, rpos)
+        except AssertionError as e:
+            raise AssertionError(f"n={n} kind={kind} m={m}: {e}")
+
+
+def test_bsearch_equals_forest_at_full_size(big):
+    """Bit-identical bins and positions of the two methods, 2^24 samples of
+    each set at n = 2^24."""
+    w, f, ref = big
+    for u in (W.iid_u32(1 << 24, seed=3), W.sorted_radical_inverse_u32(1 << 28)[::16]):
+        ud = api.u32_tensor(u, DEV)
+        i1, p1 = api.rtf_sample(f, ud)
+        i2, p2 = api.rtf_sample(f, ud, mode=api.SAMPLE_1D | BS)
+        assert torch.equal(i1, i2)
+        assert torch.equal(p1.view(torch.int32), p2.view(torch.int32))
+        assert int(i1.min()) >= 0
+
+
+def test_bsearch_tagged_and_2d():
+    rng = np.random.default_rng(11)
+    sizes = np.concatenate([[1, 2, 2049], rng.integers(1, 3000, 100)])
+    w = np.concatenate([W.lognormal_weights(int(s), seed=int(i), sigma=1.5)
+                        for i, s in enumerate(sizes)])
+    ms = np.clip(np.ceil(np.log2(np.maximum(sizes, 1))).astype(int), 0, 12)
+    f = api.rtf_build_batched(to_dev(w), sizes, ms)
+    dist = rng.integers(0, len(sizes), 1 << 16).astype(np.int32)
+    u = rng.integers(0, 1 << 32, dist.size, dtype=np.uint64).astype(np.uint32)
+    ud, dd = api.u32_tensor(u, DEV), to_dev(dist)
+    i1, p1 = api.rtf_sample(f, ud, dist_id=dd)
+    i2, p2 = api.rtf_sample(f, ud, dist_id=dd, mode=api.SAMPLE_1D | BS)
+    assert torch.equal(i1, i2) and torch.equal(p1.view(torch.int32), p2.view(torch.int32))
+    H, Wd = 48, 80
+    lum = W.env_map(H, Wd, seed=12)
+    fe = api.rtf_build_batched(to_dev(lum.reshape(-1)), [Wd] * H + [H], [6] * H + [5],
+                               marginal=True)
+    u2 = rng.integers(0, 1 << 32, 2 * (1 << 15), dtype=np.uint64).astype(np.uint32)
+    u2d = api.u32_tensor(u2, DEV)
+    j1, q1 = api.rtf_sample(fe, u2d, mode=api.SAMPLE_2D)
+    j2, q2 = api.rtf_sample(fe, u2d, mode=api.SAMPLE_2D | BS)
+    assert torch.equal(j1, j2) and torch.equal(q1.view(torch.int32), q2.view(torch.int32))
+    rows, marg = orc.build_env(lum, 1 << 5, 1 << 6)
+    r, c, _, _ = orc.sample_env(rows, marg, u2[0::2], u2[1::2])
+    jj = j2.cpu().numpy()
+    assert np.array_equal(jj[:, 0], r) and np.array_equal(jj[:, 1], c)
+
+
+# ---------------------------------------------------------------------------
+# load counts per sample (the statistics of Table 1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [0, 4, 10])
+def test_forest_load_counts_equal_oracle_descent(m):
+    """Radix forest: one guide record plus the nodes below the root, i.e. the
+    oracle's descent from the guide entry (at least 1)."""
+    for n, kind, w in weight_cases()[::3]:
+        f = api.rtf_build(to_dev(w), m)
+        ref = orc.build(w, 1 << m)
+        K, _ = orc.keys(ref.C, 1 << m)
+        u = W.iid_u32(2048, seed=n)
+        loads = api.rtf_sample_loads(f, api.u32_tensor(u, DEV)).cpu().numpy()
+        steps = np.array([orc.descend_steps(ref.guide, ref.nodes, K, 1 << m, int(x)) for x in u])
+        assert np.array_equal(loads, np.maximum(steps, 1)), f"n={n} kind={kind}"
+
+
+def test_bsearch_load_counts_bounded():
+    """Binary search: guide record(s) plus at most ceil(log2(bracket + 1))
+    probes; exactly 1 in a cell that one interval covers."""
+    w = W.lognormal_weights(50000, seed=9, sigma=2.0)
+    m = 12
+    f = api.rtf_build(to_dev(w), m)
+    ref = orc.build(w, 1 << m)
+    u = W.iid_u32(1 << 14, seed=10)
+    loads = api.rtf_sample_loads(f, api.u32_tensor(u, DEV), mode=api.SAMPLE_1D | BS).cpu().numpy()
+    g = (u.astype(np.uint64) >> np.uint64(32 - m)).astype(np.int64)
+    lo = np.where(ref.guide >= 0, np.maximum(ref.guide - 1, 0), ~ref.guide)
+    nxt = np.concatenate([lo[1:], [ref.n - 1]])
+    covered = ref.guide < 0
+    span = np.where(covered, 0, nxt - lo)[g]
+    bound = np.where(covered[g], 1, 2 + np.ceil(np.log2(span + 1)).astype(np.int64))
+    assert (loads >= 1).all() and (loads <= bound).all()
+    assert (loads[covered[g]] == 1).all()

@@ -80,6 +80,9 @@ def test_bad_arguments_rejected_without_gpu_work(lib):
                           ctypes.c_void_p(16), None) == EINVAL
     assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 5, 1, ctypes.c_void_p(16),
                           ctypes.c_void_p(16), None) == EINVAL  # 2-D needs a marginal
+    for mode in (2, 0x200, 0x101, 0x80):  # unknown mode or flag; 2-D + bsearch needs a marginal
+        assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 5, mode,
+                              ctypes.c_void_p(16), ctypes.c_void_p(16), None) == EINVAL
     assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 0, 0, None, None,
                           None) == 0  # nothing to do
 
@@ -114,3 +117,16 @@ def test_guide_bits_lookup_without_gpu():
     table = {3: 2, 4: 4, 5: 5, 6: 7}
     ms = autotune.guide_bits_for([1, 8, 11, 16, 40, 64, 10 ** 6], table)
     assert ms.tolist() == [2, 2, 2, 4, 5, 7, 7]
+
+
+def test_load_statistics_columns():
+    from paper_1901_05423_gb300.api import load_statistics
+    a = np.ones(64, np.int32)
+    a[5] = 7
+    a[40] = 3
+    st = load_statistics(a)
+    assert st["maximum"] == 7
+    assert abs(st["average"] - (62 + 7 + 3) / 64) < 1e-12
+    assert st["average32"] == (7 + 3) / 2
+    with pytest.raises(ValueError):
+        load_statistics(np.array([1, -1]))
