@@ -51,6 +51,23 @@ DRAM_BYTES_PER_UNIT = {
 }
 
 
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """Per-step time of the job: the slowest rank's (each rank runs a full
+    replica of the workload on its own GPU)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, ms: float) -> float:
+    """Units of all ranks per second (weak scaling: every rank maps its own
+    2 x 2^28 samples)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -261,11 +278,7 @@ def gpu_arm(args):
         for i, nm in enumerate(names):
             part[nm].append(evs[k][i].elapsed_time(evs[k][i + 1]))
     f.check_status()
-    ms = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(total_ms / args.steps, dist, dev)
 
     # end-to-end through the API with host buffers (pinned), copies inside
     h_w = torch.from_numpy(w).pin_memory()
@@ -317,7 +330,7 @@ def gpu_arm(args):
     units = {"build": N_W, "sample_iid": N_S, "sample_sorted": N_S, "backward": N_S}
     per_unit = DRAM_BYTES_PER_UNIT.get(dom)
     traffic = per_unit * units[dom] if per_unit is not None else None
-    value = world * 2 * N_S / (ms * 1e-3)
+    value = job_throughput(world, 2 * N_S, ms)
     lg = N_S.bit_length() - 1
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
@@ -337,7 +350,8 @@ def gpu_arm(args):
                      "traffic_GBps": traffic / (avg[dom] * 1e-3) / 1e9 if traffic else None,
                      "peak_kind": peak_kind},
         "fractions_of_hbm": {k: alg[k] / (avg[k] * 1e-3) / 1e9 / peak for k in avg},
-        "e2e": {"value": world * 2 * N_S / (e2e_ms * 1e-3), "unit": "samples/s",
+        "e2e": {"value": job_throughput(world, 2 * N_S, max_over_ranks(e2e_ms, dist, dev)),
+                "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clk.summary(),
