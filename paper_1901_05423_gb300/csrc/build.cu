@@ -661,11 +661,20 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
       run += qq;
       incl[k] = run;
     }
-    SegPair agg{run, headmask ? 1u : 0u};
-    SegPair ex = block_seg_exclusive(agg, s.wtot, &s.btot);  // also retires s.wo.w
-    const bool head0 = SEG ? (a.dists[dfirst].elem_off == t0) : (t0 == 0);
-    const uint64_t E = head0 ? 0ull : s.prefix;
-    const uint64_t base = ex.f ? ex.s : ex.s + E;
+    // exclusive prefix of the thread's run within the tile (its barriers also
+    // retire s.wo.w); one distribution has its only head at element 0, where
+    // the running sum is 0 anyway, so a plain scan serves
+    uint64_t base;
+    if (SEG) {
+      const SegPair ex = block_seg_exclusive(SegPair{run, headmask ? 1u : 0u}, s.wtot, &s.btot);
+      const bool head0 = a.dists[dfirst].elem_off == t0;
+      const uint64_t E = head0 ? 0ull : s.prefix;
+      base = ex.f ? ex.s : ex.s + E;
+    } else {
+      base = block_exclusive_u64(run, reinterpret_cast<uint64_t*>(s.wtot), &s.btot.s) +
+             (t0 == 0 ? 0ull : s.prefix);
+      headmask = 0u;
+    }
     int dP = -1;
     uint64_t T = 0, R = 0;
     int z = 0;
@@ -810,12 +819,12 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
   __syncthreads();
 
   // ---- node records and the tile's otherBounds slice -------------------------
-  // otherBounds: the far bound of every first arrival still waiting for its
-  // sibling, -1 everywhere else
-  int ob4[kForestPer];
+  // Records go out with consecutive threads on consecutive records (leaf
+  // l = tid + k * blockDim); otherBounds holds the far bound of every first
+  // arrival still waiting for its sibling, -1 everywhere else.
 #pragma unroll
   for (int k = 0; k < kForestPer; ++k) {
-    const int l = l0 + k;
+    const int l = tid + k * kForestThreads;
     if (l >= tn) break;
     const int32_t c0 = s.child[l][0], c1 = s.child[l][1];
     const uint64_t C = s.C[l + 1];
@@ -831,7 +840,12 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
       if (c0 != kUnset) rec->child[0] = c0;
       if (c1 != kUnset) rec->child[1] = c1;
     }
-    const int o = s.wo.other[l];
+  }
+  int ob4[kForestPer];
+#pragma unroll
+  for (int k = 0; k < kForestPer; ++k) {
+    const int l = l0 + k;
+    const int o = l < tn ? s.wo.other[l] : -1;
     ob4[k] = o >= 0 ? (int)(t0 + o) : -1;
   }
   if (l0 + kForestPer <= tn) {

@@ -385,6 +385,34 @@ __device__ inline SegPair block_seg_exclusive(SegPair x, SegPair* warp_tot, SegP
   return r;
 }
 
+// Plain (unsegmented) exclusive block scan of u64 values; *total receives the
+// block's sum.
+__device__ inline uint64_t block_exclusive_u64(uint64_t x, uint64_t* warp_tot, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint64_t inc = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t v = lane < nw ? warp_tot[lane] : 0ull;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t o = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += o;
+    }
+    if (lane < nw) warp_tot[lane] = v;
+    if (lane == nw - 1) *total = v;
+  }
+  __syncthreads();
+  const uint64_t r = (warp > 0 ? warp_tot[warp - 1] : 0ull) + inc - x;
+  __syncthreads();
+  return r;
+}
+
 // Plain (unsegmented) exclusive block scan of u32 values.
 __device__ inline uint32_t block_exclusive_u32(uint32_t x, uint32_t* warp_tot, uint32_t* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
