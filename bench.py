@@ -291,17 +291,34 @@ def gpu_arm(args):
     o_pos_s = torch.empty_like(o_pos_i).pin_memory()
     o_gw = torch.empty_like(h_w).pin_memory()
 
+    # The end-to-end step through the public API: the weights and dL/dpos go
+    # up on a side stream while the samples stream through the pipelined
+    # sampler (copies in, sampling and copies back of different chunks
+    # overlap); the step ends when every result is back in host memory.
+    s_up = torch.cuda.Stream(dev)
+    ev_w, ev_g = torch.cuda.Event(), torch.cuda.Event()
+    ev_i, ev_s = torch.cuda.Event(), torch.cuda.Event()
+    chunk = 1 << 22
+
     def e2e_step():
-        wd.copy_(h_w, non_blocking=True)
-        ui.copy_(h_ui, non_blocking=True)
-        us.copy_(h_us, non_blocking=True)
-        gd.copy_(h_g, non_blocking=True)
-        step()
-        o_idx_i.copy_(idx_i, non_blocking=True)
-        o_pos_i.copy_(pos_i, non_blocking=True)
-        o_idx_s.copy_(idx_s, non_blocking=True)
-        o_pos_s.copy_(pos_s, non_blocking=True)
+        cur = torch.cuda.current_stream(dev)
+        s_up.wait_stream(cur)
+        with torch.cuda.stream(s_up):
+            wd.copy_(h_w, non_blocking=True)
+            ev_w.record(s_up)
+            gd.copy_(h_g, non_blocking=True)
+            ev_g.record(s_up)
+        cur.wait_event(ev_w)
+        api.rtf_build(wd, M_BITS, forest=f)
+        api.rtf_sample_pipelined(f, h_ui, ui, idx_i, pos_i, o_idx_i, o_pos_i, chunk=chunk,
+                                 done_event=ev_i)
+        api.rtf_sample_pipelined(f, h_us, us, idx_s, pos_s, o_idx_s, o_pos_s, chunk=chunk,
+                                 done_event=ev_s)
+        cur.wait_event(ev_g)
+        api.rtf_sample_backward(f, wd, ui, None, idx_i, pos_i, gd, grad_w=grad_w)
         o_gw.copy_(grad_w, non_blocking=True)
+        cur.wait_event(ev_i)
+        cur.wait_event(ev_s)
 
     e2e_steps = max(1, min(args.steps, 3))
     e2e_step()

@@ -265,6 +265,42 @@ rtf_status rtf_sample(const rtf_forest *f, const uint32_t *u,
                       int32_t *idx_out, float *pos_out, void *stream);
 
 /*
+ * rtf_sample for samples that live in host memory: the samples are copied to
+ * the device, mapped and the results copied back in chunks of `chunk` samples
+ * (a multiple of 4), with the copies of one chunk overlapping the sampling of
+ * another.  Not in the paper: the host-side counterpart of the sampler.
+ *
+ *   u_host       uint32[count] (2 count in 2-D), or NULL when u_dev already
+ *                holds the samples.  Page-locked host memory lets the copies
+ *                run asynchronously; pageable memory works but serialises.
+ *   u_dev        device uint32[count] (2 count), 16-byte aligned: receives
+ *                the samples (when u_host is given), read by the kernels.
+ *   dist_id_host / dist_id_dev   as u for the per-sample distribution ids
+ *                (1-D only); both NULL for distribution 0.
+ *   idx_dev, pos_dev   device outputs as for rtf_sample (16-byte aligned);
+ *                they keep the results for later device work (a backward).
+ *   idx_host, pos_host host outputs (either may be NULL: no copy back).
+ *   mode         as for rtf_sample.
+ *
+ *   done_event   NULL, or a cudaEvent_t of the caller (see below).
+ *
+ * Ordering: the copies start after the work already queued on `stream`.
+ * With done_event NULL, `stream` waits for the last copy of both directions,
+ * so synchronising it makes the host outputs complete.  With an event,
+ * `stream` waits for the input copies only and the event is recorded after
+ * the last copy back: later work on `stream` overlaps those copies, and the
+ * caller waits for the event before it reads the host outputs or reuses
+ * idx_dev / pos_dev.  The library keeps two copy streams and four events per
+ * device for the rest of the process.
+ */
+rtf_status rtf_sample_pipelined(const rtf_forest *f, const uint32_t *u_host,
+                                uint32_t *u_dev, const int32_t *dist_id_host,
+                                int32_t *dist_id_dev, int64_t count, int32_t mode,
+                                int32_t *idx_dev, float *pos_dev, int32_t *idx_host,
+                                float *pos_host, int64_t chunk, void *done_event,
+                                void *stream);
+
+/*
  * Number of loads from the structure that each sample takes under the method
  * of `mode` (RTF_SAMPLE_1D, optionally | RTF_SAMPLE_BSEARCH): guide records
  * plus node records (radix forest) or CDF values (binary search), the

@@ -11,5 +11,5 @@ if it cannot.
 from .api import (  # noqa: F401
     FOREST_MARGINAL, SAMPLE_1D, SAMPLE_2D, SAMPLE_BSEARCH, Forest, RtfError, load_statistics,
     plan_batched, rtf_build, rtf_build_batched, rtf_sample, rtf_sample_backward,
-    rtf_sample_loads, u32_tensor,
+    rtf_sample_loads, rtf_sample_pipelined, u32_tensor,
 )

@@ -21,7 +21,7 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _OUT_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(_OUT_DIR, "librtf.so")
-SOURCES = ["build.cu", "sample.cu", "backward.cu", "api.cu", "static_ws.cu"]
+SOURCES = ["build.cu", "sample.cu", "backward.cu", "api.cu", "static_ws.cu", "pipeline.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -117,6 +117,9 @@ EXPORTS = {
     "rtf_sample": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "rtf_sample_pipelined": (ctypes.c_int, [ctypes.POINTER(RtfForestC)] + [ctypes.c_void_p] * 4
+                             + [ctypes.c_int64, ctypes.c_int32] + [ctypes.c_void_p] * 4
+                             + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "rtf_sample_loads": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.c_void_p]),

@@ -236,6 +236,37 @@ def rtf_sample(forest: Forest, u: torch.Tensor, dist_id: torch.Tensor | None = N
     return idx_out, pos_out
 
 
+def rtf_sample_pipelined(forest: Forest, u_host: torch.Tensor | None, u_dev: torch.Tensor,
+                         idx_dev: torch.Tensor, pos_dev: torch.Tensor,
+                         idx_host: torch.Tensor | None = None, pos_host: torch.Tensor | None = None,
+                         dist_id_host: torch.Tensor | None = None,
+                         dist_id_dev: torch.Tensor | None = None, mode: int = SAMPLE_1D,
+                         chunk: int = 1 << 22, done_event: torch.cuda.Event | None = None):
+    """``rtf_sample_pipelined``: samples from host memory, results to device
+    and (optionally) host memory, copies overlapping the sampling chunk by
+    chunk.  Host tensors should be page-locked (``Tensor.pin_memory()``).
+    With `done_event` the current stream does not wait for the copies back;
+    the event marks their end."""
+    for t, name in ((u_host, "u_host"), (idx_host, "idx_host"), (pos_host, "pos_host"),
+                    (dist_id_host, "dist_id_host")):
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    two_d = (mode & 0xFF) == SAMPLE_2D
+    count = u_dev.numel() // (2 if two_d else 1)
+    lib = _native.load()
+    cf = forest.c_struct()
+    ev = ctypes.c_void_p(0)
+    if done_event is not None:
+        if not done_event.cuda_event:  # torch creates the event at its first record
+            done_event.record(torch.cuda.current_stream(u_dev.device))
+        ev = ctypes.c_void_p(done_event.cuda_event)
+    _check(lib.rtf_sample_pipelined(ctypes.byref(cf), _ptr(u_host), _ptr(u_dev), _ptr(dist_id_host),
+                                    _ptr(dist_id_dev), count, mode, _ptr(idx_dev), _ptr(pos_dev),
+                                    _ptr(idx_host), _ptr(pos_host), chunk, ev,
+                                    _stream_ptr(u_dev.device)), "rtf_sample_pipelined")
+    return idx_dev, pos_dev
+
+
 def rtf_sample_loads(forest: Forest, u: torch.Tensor, dist_id: torch.Tensor | None = None,
                      mode: int = SAMPLE_1D) -> torch.Tensor:
     """Structure loads per sample under the method of `mode` (``rtf_sample_loads``)."""

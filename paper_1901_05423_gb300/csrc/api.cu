@@ -15,6 +15,11 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
 cudaError_t launch_sample(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
                           int64_t count, int mode, int32_t* idx_out, float* pos_out,
                           cudaStream_t st);
+cudaError_t launch_sample_pipelined(const rtf_forest* f, const uint32_t* u_host, uint32_t* u_dev,
+                                    const int32_t* dist_host, int32_t* dist_dev, int64_t count,
+                                    int mode, int32_t* idx_dev, float* pos_dev,
+                                    int32_t* idx_host, float* pos_host, int64_t chunk,
+                                    cudaEvent_t done, cudaStream_t st);
 cudaError_t launch_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
                                 int64_t count, int mode, int32_t* loads_out, cudaStream_t st);
 size_t backward_ws_bytes(int64_t N, int32_t D);
@@ -112,6 +117,29 @@ rtf_status rtf_sample(const rtf_forest* f, const uint32_t* u, const int32_t* dis
   }
   return cuda_status(rtf::launch_sample(f, u, dist_id, count, mode, idx_out, pos_out,
                                         static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_sample_pipelined(const rtf_forest* f, const uint32_t* u_host, uint32_t* u_dev,
+                                const int32_t* dist_id_host, int32_t* dist_id_dev, int64_t count,
+                                int32_t mode, int32_t* idx_dev, float* pos_dev,
+                                int32_t* idx_host, float* pos_host, int64_t chunk,
+                                void* done_event, void* stream) {
+  if (!forest_ok(f) || count < 0 || chunk < 4 || (chunk & 3)) return RTF_EINVAL;
+  if (mode & ~(0xFF | RTF_SAMPLE_BSEARCH)) return RTF_EINVAL;
+  const int32_t base = mode & 0xFF;
+  if (base == RTF_SAMPLE_2D) {
+    if (!(f->flags & RTF_FOREST_MARGINAL) || dist_id_dev || dist_id_host) return RTF_EINVAL;
+  } else if (base != RTF_SAMPLE_1D) {
+    return RTF_EINVAL;
+  }
+  if (count == 0) return RTF_OK;
+  if (!u_dev || !idx_dev || !pos_dev) return RTF_EINVAL;
+  if (!aligned(u_dev, 16) || !aligned(idx_dev, 16) || !aligned(pos_dev, 16)) return RTF_EINVAL;
+  if (dist_id_host && !dist_id_dev) return RTF_EINVAL;
+  if (dist_id_dev && !aligned(dist_id_dev, 4)) return RTF_EINVAL;
+  return cuda_status(rtf::launch_sample_pipelined(
+      f, u_host, u_dev, dist_id_host, dist_id_dev, count, mode, idx_dev, pos_dev, idx_host,
+      pos_host, chunk, static_cast<cudaEvent_t>(done_event), static_cast<cudaStream_t>(stream)));
 }
 
 rtf_status rtf_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,

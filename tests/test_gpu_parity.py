@@ -492,3 +492,124 @@ def test_bsearch_load_counts_bounded():
     bound = np.where(covered[g], 1, 2 + np.ceil(np.log2(span + 1)).astype(np.int64))
     assert (loads >= 1).all() and (loads <= bound).all()
     assert (loads[covered[g]] == 1).all()
+
+
+# ---------------------------------------------------------------------------
+# host-streamed sampling (rtf_sample_pipelined)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("chunk", [4, 4096, 1 << 20])
+def test_pipelined_equals_device_sampling(chunk):
+    """Host samples in, device and host results out, chunked with overlap; a
+    count that is not a multiple of the chunk."""
+    w = W.lognormal_weights(100000, seed=70, sigma=2.0)
+    f = api.rtf_build(to_dev(w), 14)
+    n_s = 50001 if chunk > 4 else 999
+    u = W.iid_u32(n_s, seed=71)
+    u_host = torch.from_numpy(u.view(np.int32)).pin_memory()
+    u_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
+    idx_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
+    pos_dev = torch.empty(n_s, dtype=torch.float32, device=DEV)
+    idx_host = torch.empty(n_s, dtype=torch.int32).pin_memory()
+    pos_host = torch.empty(n_s, dtype=torch.float32).pin_memory()
+    api.rtf_sample_pipelined(f, u_host, u_dev, idx_dev, pos_dev, idx_host, pos_host, chunk=chunk)
+    torch.cuda.synchronize()
+    ridx, rpos = orc.sample(orc.build(w, 1 << 14).C, u)
+    check_samples(idx_host.numpy(), pos_host.numpy(), ridx, rpos)
+    check_samples(idx_dev, pos_dev, ridx, rpos)
+    assert np.array_equal(u_dev.cpu().numpy().view(np.uint32), u)
+
+
+def test_pipelined_tagged_and_2d():
+    rng = np.random.default_rng(72)
+    sizes = rng.integers(1, 3000, 50)
+    w = np.concatenate([W.lognormal_weights(int(s), seed=int(i), sigma=1.5)
+                        for i, s in enumerate(sizes)])
+    f = api.rtf_build_batched(to_dev(w), sizes, np.full(len(sizes), 9))
+    n_s = 1 << 16
+    dist = rng.integers(0, len(sizes), n_s).astype(np.int32)
+    u = W.iid_u32(n_s, seed=73)
+    ref_idx, ref_pos = api.rtf_sample(f, api.u32_tensor(u, DEV), dist_id=to_dev(dist))
+    u_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
+    d_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
+    idx_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
+    pos_dev = torch.empty(n_s, dtype=torch.float32, device=DEV)
+    idx_host = torch.empty(n_s, dtype=torch.int32).pin_memory()
+    pos_host = torch.empty(n_s, dtype=torch.float32).pin_memory()
+    api.rtf_sample_pipelined(f, torch.from_numpy(u.view(np.int32)).pin_memory(), u_dev, idx_dev,
+                             pos_dev, idx_host, pos_host,
+                             dist_id_host=torch.from_numpy(dist).pin_memory(), dist_id_dev=d_dev,
+                             chunk=8192)
+    torch.cuda.synchronize()
+    assert torch.equal(idx_host, ref_idx.cpu()) and torch.equal(pos_host, ref_pos.cpu())
+    H, Wd = 40, 64
+    lum = W.env_map(H, Wd, seed=74)
+    fe = api.rtf_build_batched(to_dev(lum.reshape(-1)), [Wd] * H + [H], [6] * H + [5],
+                               marginal=True)
+    u2 = W.iid_u32(2 * 30000, seed=75)
+    r_idx, r_pos = api.rtf_sample(fe, api.u32_tensor(u2, DEV), mode=api.SAMPLE_2D)
+    u2_dev = torch.empty(2 * 30000, dtype=torch.int32, device=DEV)
+    i2 = torch.empty((30000, 2), dtype=torch.int32, device=DEV)
+    p2 = torch.empty((30000, 2), dtype=torch.float32, device=DEV)
+    i2h = torch.empty((30000, 2), dtype=torch.int32).pin_memory()
+    p2h = torch.empty((30000, 2), dtype=torch.float32).pin_memory()
+    api.rtf_sample_pipelined(fe, torch.from_numpy(u2.view(np.int32)).pin_memory(), u2_dev, i2, p2,
+                             i2h, p2h, mode=api.SAMPLE_2D, chunk=4096)
+    torch.cuda.synchronize()
+    assert torch.equal(i2h, r_idx.cpu()) and torch.equal(p2h, r_pos.cpu())
+
+
+def test_pipelined_graph_capture():
+    """The fork and join onto the copy streams is captured as graph edges;
+    replays with new host samples give their results."""
+    w = W.lognormal_weights(20000, seed=76, sigma=1.0)
+    f = api.rtf_build(to_dev(w), 12)
+    ref = orc.build(w, 1 << 12)
+    n_s = 1 << 15
+    u_host = torch.empty(n_s, dtype=torch.int32).pin_memory()
+    u_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
+    idx_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
+    pos_dev = torch.empty(n_s, dtype=torch.float32, device=DEV)
+    idx_host = torch.empty(n_s, dtype=torch.int32).pin_memory()
+    pos_host = torch.empty(n_s, dtype=torch.float32).pin_memory()
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        api.rtf_sample_pipelined(f, u_host, u_dev, idx_dev, pos_dev, idx_host, pos_host,
+                                 chunk=8192)
+    for seed in (77, 78):
+        u = W.iid_u32(n_s, seed=seed)
+        u_host.copy_(torch.from_numpy(u.view(np.int32)))
+        g.replay()
+        torch.cuda.synchronize()
+        ridx, rpos = orc.sample(ref.C, u)
+        check_samples(idx_host.numpy(), pos_host.numpy(), ridx, rpos)
+
+
+def test_pipelined_done_event_overlaps_next_call():
+    """With done events the stream does not wait for the copies back; after
+    waiting for the events both calls' host outputs are complete."""
+    w = W.lognormal_weights(30000, seed=80, sigma=2.0)
+    f = api.rtf_build(to_dev(w), 13)
+    ref = orc.build(w, 1 << 13)
+    n_s = 40000
+    outs = []
+    for seed in (81, 82):
+        u = W.iid_u32(n_s, seed=seed)
+        bufs = dict(u_host=torch.from_numpy(u.view(np.int32)).pin_memory(),
+                    u_dev=torch.empty(n_s, dtype=torch.int32, device=DEV),
+                    idx_dev=torch.empty(n_s, dtype=torch.int32, device=DEV),
+                    pos_dev=torch.empty(n_s, dtype=torch.float32, device=DEV),
+                    idx_host=torch.empty(n_s, dtype=torch.int32).pin_memory(),
+                    pos_host=torch.empty(n_s, dtype=torch.float32).pin_memory())
+        ev = torch.cuda.Event()
+        api.rtf_sample_pipelined(f, chunk=4096, done_event=ev, **bufs)
+        outs.append((u, bufs, ev))
+    cur = torch.cuda.current_stream()
+    for u, bufs, ev in outs:
+        cur.wait_event(ev)
+    cur.synchronize()
+    for u, bufs, ev in outs:
+        ridx, rpos = orc.sample(ref.C, u)
+        check_samples(bufs["idx_host"].numpy(), bufs["pos_host"].numpy(), ridx, rpos)

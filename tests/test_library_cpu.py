@@ -85,6 +85,16 @@ def test_bad_arguments_rejected_without_gpu_work(lib):
                               ctypes.c_void_p(16), ctypes.c_void_p(16), None) == EINVAL
     assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 0, 0, None, None,
                           None) == 0  # nothing to do
+    P = ctypes.c_void_p
+    for chunk in (0, 3, 6):  # chunks are positive multiples of 4
+        assert lib.rtf_sample_pipelined(ctypes.byref(f), None, P(16), None, None, 8, 0, P(16),
+                                        P(16), None, None, chunk, None, None) == EINVAL
+    assert lib.rtf_sample_pipelined(ctypes.byref(f), None, P(16), P(16), None, 8, 0, P(16),
+                                    P(16), None, None, 4, None, None) == EINVAL  # ids need a device buffer
+    assert lib.rtf_sample_pipelined(ctypes.byref(f), None, P(8), None, None, 8, 0, P(16),
+                                    P(16), None, None, 4, None, None) == EINVAL  # misaligned
+    assert lib.rtf_sample_pipelined(ctypes.byref(f), None, None, None, None, 0, 0, None,
+                                    None, None, None, 4, None, None) == 0  # nothing to do
 
 
 def test_plan_batched_host_logic():
