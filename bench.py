@@ -185,6 +185,7 @@ def reference_arm(args):
             times.append(res["step_s"])
     step = float(np.mean(times))
     value = 2 * N_S / step
+    lg = N_S.bit_length() - 1
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

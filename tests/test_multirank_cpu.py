@@ -52,3 +52,20 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(4.0) == 4.0
     assert bench.job_throughput(1, 500, 2.0) == pytest.approx(250000.0)
+
+
+def test_reference_arm_prints_its_line():
+    """`bench.py --impl reference` (the oracle timed on the host cores) runs
+    without a GPU and prints one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--samples-log2", "12"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "ms_per_step", "higher_is_better", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
