@@ -299,7 +299,7 @@ def gpu_arm(args):
     s_up = torch.cuda.Stream(dev)
     ev_w, ev_g = torch.cuda.Event(), torch.cuda.Event()
     ev_i, ev_s = torch.cuda.Event(), torch.cuda.Event()
-    chunk = 1 << 22
+    chunk = 1 << 24
 
     def e2e_step():
         cur = torch.cuda.current_stream(dev)
