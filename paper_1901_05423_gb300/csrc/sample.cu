@@ -442,7 +442,99 @@ __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
   }
 }
 
-// 1-D with a distribution id per sample.
+// Algorithm 2 and the position for K samples of K distributions (a distribution
+// id per sample): as sample_group, with the distribution's parameters per
+// slot.  A sample with an invalid id yields idx = -1 and sets bad_id.
+template <int K>
+__device__ __forceinline__ void sample_group_tagged(const rtf_node* __restrict__ nodes,
+                                                    const rtf_guide_rec* __restrict__ guide,
+                                                    const rtf_dist* __restrict__ dists, int D,
+                                                    const uint32_t (&uu)[K], const int32_t (&dd)[K],
+                                                    uint64_t pol, int32_t (&idx)[K],
+                                                    float (&pos)[K], bool& bad_id) {
+  int32_t j[K];
+  uint64_t t[K], lo[K], hi[K];
+  uint32_t r[K], n32[K];
+  int64_t off[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    j[k] = -1;
+    t[k] = 0;
+    lo[k] = 1;
+    hi[k] = 0;
+    r[k] = 0;
+    n32[k] = 0;
+    off[k] = 0;
+    if (dd[k] < 0 || dd[k] >= D) {
+      bad_id = true;
+      continue;
+    }
+    const rtf_dist* P = dists + dd[k];
+    off[k] = __ldg(&P->elem_off);
+    n32[k] = (uint32_t)__ldg(&P->n);
+    const uint64_t T = __ldg(&P->total);
+    const int m = __ldg(&P->m);
+    const int64_t goff = __ldg(&P->guide_off);
+    const uint32_t g = m ? (uu[k] >> (32 - m)) : 0u;
+    scale_sample(uu[k], T, t[k], r[k]);
+    uint64_t c, glo, ghi;
+    int32_t c0, c1;
+    load_guide(guide + goff + g, pol, c, c0, c1, glo, ghi);
+    const bool left = t[k] < c;
+    j[k] = left ? c0 : c1;
+    lo[k] = left ? glo : c;
+    hi[k] = left ? c : ghi;
+  }
+  bool live = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) live |= j[k] >= 0;
+  bool bad = false;
+#pragma unroll 1
+  for (int step = 0; live && step < 64; ++step) {
+    uint64_t c[K];
+    int32_t c0[K], c1[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (j[k] >= 0) {
+        if ((uint32_t)j[k] >= n32[k]) {
+          bad = true;  // invalid structure: stop this descent
+          j[k] = -1;
+        } else {
+          load_node(nodes + off[k] + j[k], pol, c[k], c0[k], c1[k]);
+        }
+      }
+    }
+    live = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (j[k] >= 0) {
+        const bool left = t[k] < c[k];
+        j[k] = left ? c0[k] : c1[k];
+        if (left)
+          hi[k] = c[k];
+        else
+          lo[k] = c[k];
+        live |= j[k] >= 0;
+      }
+    }
+  }
+  bad |= live;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t i = (uint32_t)~j[k];
+    if (!bad && i < n32[k] && lo[k] <= t[k] && t[k] < hi[k]) {
+      idx[k] = (int32_t)i;
+      pos[k] = in_bin_position(t[k] - lo[k], r[k], hi[k] - lo[k]);
+    } else {
+      idx[k] = -1;
+      pos[k] = 0.0f;
+    }
+  }
+}
+
+// 1-D with a distribution id per sample: four samples per thread in lockstep
+// (u, idx and pos as 16-byte vectors) for the radix forest; one per thread
+// for the binary search.
 template <bool BS>
 __global__ void __launch_bounds__(kSampleThreads)
     sample_tagged_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
@@ -451,8 +543,38 @@ __global__ void __launch_bounds__(kSampleThreads)
                          int64_t count, int32_t* __restrict__ idx_out,
                          float* __restrict__ pos_out, uint32_t* status) {
   const uint64_t pol = l2_evict_last_policy();
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < count;
-       s += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (!BS) {
+    bool bad_id = false;
+    const int64_t groups = count >> 2;
+    const uint4* u4 = reinterpret_cast<const uint4*>(u);
+    int4* i4 = reinterpret_cast<int4*>(idx_out);
+    float4* p4 = reinterpret_cast<float4*>(pos_out);
+    for (int64_t q = gtid; q < groups; q += stride) {
+      const uint4 x = __ldcs(u4 + q);
+      const uint32_t uu[4] = {x.x, x.y, x.z, x.w};
+      const int32_t dd[4] = {__ldcs(dist_id + 4 * q), __ldcs(dist_id + 4 * q + 1),
+                             __ldcs(dist_id + 4 * q + 2), __ldcs(dist_id + 4 * q + 3)};
+      int32_t ii[4];
+      float pp[4];
+      sample_group_tagged<4>(nodes, guide, dists, D, uu, dd, pol, ii, pp, bad_id);
+      __stcs(i4 + q, make_int4(ii[0], ii[1], ii[2], ii[3]));
+      __stcs(p4 + q, make_float4(pp[0], pp[1], pp[2], pp[3]));
+    }
+    for (int64_t s = 4 * groups + gtid; s < count; s += stride) {
+      const uint32_t uu[1] = {__ldcs(u + s)};
+      const int32_t dd[1] = {__ldcs(dist_id + s)};
+      int32_t ii[1];
+      float pp[1];
+      sample_group_tagged<1>(nodes, guide, dists, D, uu, dd, pol, ii, pp, bad_id);
+      __stcs(idx_out + s, ii[0]);
+      __stcs(pos_out + s, pp[0]);
+    }
+    if (bad_id) raise_status(status, RTF_STATUS_BAD_PLAN);
+    return;
+  }
+  for (int64_t s = gtid; s < count; s += stride) {
     int d = __ldcs(dist_id + s);
     uint32_t uu = __ldcs(u + s);
     int32_t ii = -1;
@@ -547,7 +669,8 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
     return;
   }
   if (dist_id != nullptr) {
-    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
+    const int64_t per = BS ? 1 : 4;  // samples per thread and step
+    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads * per - 1) / (kSampleThreads * per));
     sample_tagged_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
         f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
         f->status);
