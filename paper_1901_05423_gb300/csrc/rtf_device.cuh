@@ -511,8 +511,21 @@ __device__ __forceinline__ uint64_t block_lookback(const uint64_t* st, int64_t t
 // Index of the distribution that owns element `e`// Index of the distribution that owns element `e`: the largest d with
 // dists[d].elem_off <= e (binary search over [lo, hi]).
 __device__ inline int find_dist(const rtf_dist* dists, int lo, int hi, int64_t e) {
+  // galloping from lo (callers pass the first distribution of a tile, and an
+  // element usually lies in it or in one of the next few), then bisection
+  int step = 1;
   while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
+    const int probe = lo + step < hi ? lo + step : hi;
+    if (dists[probe].elem_off <= e) {
+      lo = probe;
+      step <<= 1;
+    } else {
+      hi = probe - 1;
+      break;
+    }
+  }
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
     if (dists[mid].elem_off <= e)
       lo = mid;
     else
