@@ -214,19 +214,11 @@ __device__ __forceinline__ uint32_t key_distance(uint64_t a, uint64_t b) {
   return 32u - (uint32_t)__clz((uint32_t)(a ^ b));
 }
 
-// Round a 64-bit unsigned integer to the nearest float32 (ties to even)
-// without the 64-bit conversion instruction (which GB300 runs on its slow fp64
-// pipe): normalise, keep the top 32 bits with every lower bit folded into a
-// sticky bit 0 (enough for a correctly rounded 24-bit result), convert those
-// 32 bits, and scale by an exact power of two.
-__device__ __forceinline__ float u64_to_f32(uint64_t x) {
-  const uint32_t hi = (uint32_t)(x >> 32), lo = (uint32_t)x;
-  if (hi == 0) return __uint2float_rn(lo);
-  const int lz = __clz(hi);                              // 0..31
-  uint32_t top = __funnelshift_l(lo, hi, lz);            // high word of x << lz
-  top |= ((lo << lz) != 0u) ? 1u : 0u;                   // sticky
-  return __uint2float_rn(top) * __uint_as_float((uint32_t)(127 + 32 - lz) << 23);
-}
+// Round a 64-bit unsigned integer to the nearest float32 (ties to even), the
+// hardware conversion.  (A variant that normalises, folds the low bits into a
+// sticky bit and converts 32 bits gives the same values; on GB300 it took more
+// issue slots in the sorted sampler, 2.09 vs 1.93 ms for 2^28 samples.)
+__device__ __forceinline__ float u64_to_f32(uint64_t x) { return __ull2float_rn(x); }
 
 // ---------------------------------------------------------------------------
 // memory ordering helpers// ---------------------------------------------------------------------------
