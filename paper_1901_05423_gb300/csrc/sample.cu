@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kSampleThreads)
   const uint64_t pol = l2_evict_last_policy();
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (!BS) {
+  if constexpr (!BS) {
     bool bad_id = false;
     const int64_t groups = count >> 2;
     const uint4* u4 = reinterpret_cast<const uint4*>(u);
@@ -583,21 +583,21 @@ __global__ void __launch_bounds__(kSampleThreads)
       __stcs(pos_out + s, pp[0]);
     }
     if (bad_id) raise_status(status, RTF_STATUS_BAD_PLAN);
-    return;
-  }
-  for (int64_t s = gtid; s < count; s += stride) {
-    int d = __ldcs(dist_id + s);
-    uint32_t uu = __ldcs(u + s);
-    int32_t ii = -1;
-    float pp = 0.0f;
-    if (d >= 0 && d < D) {
-      const DistView v = dist_view(dists, d, nodes, guide);
-      sample_one<false, BS>(v, nullptr, uu, pol, ii, pp);
-    } else {
-      raise_status(status, RTF_STATUS_BAD_PLAN);
+  } else {
+    for (int64_t s = gtid; s < count; s += stride) {
+      int d = __ldcs(dist_id + s);
+      uint32_t uu = __ldcs(u + s);
+      int32_t ii = -1;
+      float pp = 0.0f;
+      if (d >= 0 && d < D) {
+        const DistView v = dist_view(dists, d, nodes, guide);
+        sample_one<false, BS>(v, nullptr, uu, pol, ii, pp);
+      } else {
+        raise_status(status, RTF_STATUS_BAD_PLAN);
+      }
+      __stcs(idx_out + s, ii);
+      __stcs(pos_out + s, pp);
     }
-    __stcs(idx_out + s, ii);
-    __stcs(pos_out + s, pp);
   }
 }
 
