@@ -124,9 +124,12 @@ __device__ __forceinline__ int floor_log2_bits(uint32_t b) {
 }
 
 __host__ __device__ inline int ceil_log2_i64(int64_t n) {
-  int c = 0;
-  while ((int64_t(1) << c) < n) ++c;
-  return c;
+  if (n <= 1) return 0;
+#ifdef __CUDA_ARCH__
+  return 64 - __clzll((long long)(n - 1));
+#else
+  return 64 - __builtin_clzll((unsigned long long)(n - 1));
+#endif
 }
 
 // S = B - 1 - e_max with B = 62 - ceil(log2 n_group).
