@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(kScanThreads)
   uint64_t incl[kScanPer];
   int dk[kScanPer];
   uint32_t headmask = 0;
+  uint32_t lastmask = 0;  // elements that end their distribution
   SegPair agg{0ull, 0u};
   {
     int d = dfirst;
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(kScanThreads)
         }
         const uint32_t b = weight_bits(wsm[wo + (e - t0)]);
         q = weight_bad(b) ? 0ull : quantize_bits(b, S);
+        if (e + 1 == min(next, Nw)) lastmask |= 1u << k;
       }
       run += q;
       incl[k] = run;
@@ -302,17 +304,14 @@ __global__ void __launch_bounds__(kScanThreads)
   const bool head0 = SEG ? (dists[dfirst].elem_off == t0) : (t0 == 0);
 
   // distributions whose last element lies in this tile
-  if (e0 < t1) {
+  if (lastmask) {
     const uint64_t base = ex.s;  // the tile's own partial sums (no incoming prefix)
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      const int64_t e = e0 + k;
-      if (e >= t1) break;
       const bool seen_head = (headmask & ((2u << k) - 1u)) != 0;
       const uint64_t v = seen_head ? incl[k] : base + incl[k];
       const int d = dk[k];
-      const int64_t end = SEG ? (d + 1 < Dw ? dists[d + 1].elem_off : Nw) : Nw;
-      if (e + 1 == end) {
+      if (lastmask & (1u << k)) {
         if (seen_head || ex.f) {
           const rtf_dist P = dists[d];  // began inside the tile: complete
           finish_dist(dists, d, v, dist_scale(P, dmax, d, n_shared), status);
