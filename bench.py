@@ -237,6 +237,8 @@ def gpu_arm(args):
 
     stream = torch.cuda.current_stream(dev)
     names = ["build", "sample_iid", "sample_sorted", "backward"]
+    # the sorted set is passed with the coherence hint (a sorted sequence in order)
+    SORTED_MODE = api.SAMPLE_1D | api.SAMPLE_COHERENT
 
     def step(ev=None):
         if ev is not None:
@@ -247,7 +249,7 @@ def gpu_arm(args):
         api.rtf_sample(f, ui, idx_out=idx_i, pos_out=pos_i)
         if ev is not None:
             ev[2].record(stream)
-        api.rtf_sample(f, us, idx_out=idx_s, pos_out=pos_s)
+        api.rtf_sample(f, us, mode=SORTED_MODE, idx_out=idx_s, pos_out=pos_s)
         if ev is not None:
             ev[3].record(stream)
         api.rtf_sample_backward(f, wd, ui, None, idx_i, pos_i, gd, grad_w=grad_w)
@@ -314,7 +316,7 @@ def gpu_arm(args):
         api.rtf_sample_pipelined(f, h_ui, ui, idx_i, pos_i, o_idx_i, o_pos_i, chunk=chunk,
                                  done_event=ev_i)
         api.rtf_sample_pipelined(f, h_us, us, idx_s, pos_s, o_idx_s, o_pos_s, chunk=chunk,
-                                 done_event=ev_s)
+                                 done_event=ev_s, mode=SORTED_MODE)
         cur.wait_event(ev_g)
         api.rtf_sample_backward(f, wd, ui, None, idx_i, pos_i, gd, grad_w=grad_w)
         o_gw.copy_(grad_w, non_blocking=True)
@@ -588,7 +590,9 @@ def extra_methods(dev, reps=5):
         ud = api.u32_tensor(uh, dev)
         idx = torch.empty(ns, dtype=torch.int32, device=dev)
         pos = torch.empty(ns, dtype=torch.float32, device=dev)
-        for name, mode in methods:
+        hint = api.SAMPLE_COHERENT if set_name == "sorted" else 0
+        for name, mode0 in methods:
+            mode = mode0 | hint
             api.rtf_sample(f, ud, mode=mode, idx_out=idx, pos_out=pos)
             torch.cuda.synchronize()
             a, b = _events()

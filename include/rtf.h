@@ -78,6 +78,12 @@ typedef enum rtf_status {
    search (the paper's comparator, Sec. 2.5) on the same structure instead of
    the radix forest; identical bins and positions */
 #define RTF_SAMPLE_BSEARCH 0x100
+/* hint OR-ed into the mode of rtf_sample: neighbouring samples are close (a
+   sorted or low-discrepancy sequence in order), so the sampler runs with the
+   full grid; without it, a structure larger than L2 is sampled by fewer
+   resident threads, which keeps more of it in L2 for scattered samples.
+   Results do not depend on the hint. */
+#define RTF_SAMPLE_COHERENT 0x200
 
 /*
  * One node record, 16 bytes, in device memory.  Record j of a distribution
@@ -255,6 +261,7 @@ rtf_status rtf_build_batched(const float *w, const int64_t *offsets,
  *   marginal, u2 the column through that row (Sec. 5).  idx_out int32[2 count]
  *   receives (row, column), pos_out float32[2 count] (row position, column
  *   position).
+ * RTF_SAMPLE_COHERENT may be OR-ed into either mode (a performance hint).
  * RTF_SAMPLE_BSEARCH may be OR-ed into either mode: each sample is then
  *   found by a binary search over the CDF between the first intervals of its
  *   cell and of the next cell (the cutpoint method), not by a tree descent.

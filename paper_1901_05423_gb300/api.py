@@ -25,6 +25,7 @@ FOREST_MARGINAL = 0x1
 SAMPLE_1D = 0
 SAMPLE_2D = 1
 SAMPLE_BSEARCH = 0x100  # flag: cutpoint method + binary search instead of the forest
+SAMPLE_COHERENT = 0x200  # hint: neighbouring samples are close (sorted / low-discrepancy order)
 NODE_BYTES = 16
 GUIDE_REC_BYTES = 32
 DIST_BYTES = 64

@@ -108,7 +108,7 @@ rtf_status rtf_sample(const rtf_forest* f, const uint32_t* u, const int32_t* dis
   if (count == 0) return RTF_OK;
   if (!u || !idx_out || !pos_out) return RTF_EINVAL;
   if (!aligned(u, 16) || !aligned(idx_out, 16) || !aligned(pos_out, 16)) return RTF_EINVAL;
-  if (mode & ~(0xFF | RTF_SAMPLE_BSEARCH)) return RTF_EINVAL;
+  if (mode & ~(0xFF | RTF_SAMPLE_BSEARCH | RTF_SAMPLE_COHERENT)) return RTF_EINVAL;
   const int32_t base = mode & 0xFF;
   if (base == RTF_SAMPLE_2D) {
     if (!(f->flags & RTF_FOREST_MARGINAL) || dist_id) return RTF_EINVAL;
@@ -125,7 +125,7 @@ rtf_status rtf_sample_pipelined(const rtf_forest* f, const uint32_t* u_host, uin
                                 int32_t* idx_host, float* pos_host, int64_t chunk,
                                 void* done_event, void* stream) {
   if (!forest_ok(f) || count < 0 || chunk < 4 || (chunk & 3)) return RTF_EINVAL;
-  if (mode & ~(0xFF | RTF_SAMPLE_BSEARCH)) return RTF_EINVAL;
+  if (mode & ~(0xFF | RTF_SAMPLE_BSEARCH | RTF_SAMPLE_COHERENT)) return RTF_EINVAL;
   const int32_t base = mode & 0xFF;
   if (base == RTF_SAMPLE_2D) {
     if (!(f->flags & RTF_FOREST_MARGINAL) || dist_id_dev || dist_id_host) return RTF_EINVAL;

@@ -680,8 +680,8 @@ static int num_sms() {
 
 template <bool BS>
 static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
-                            int64_t count, int mode, int32_t* idx_out, float* pos_out,
-                            cudaStream_t st) {
+                            int64_t count, int mode, bool coherent, int32_t* idx_out,
+                            float* pos_out, cudaStream_t st) {
   const int sms = num_sms();
   if (mode == RTF_SAMPLE_2D) {
     int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
@@ -701,7 +701,8 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
   const int64_t per_block = (int64_t)kSampleThreads * 4;
   const int64_t records = (int64_t)sizeof(rtf_node) * f->num_elems +
                           (int64_t)sizeof(rtf_guide_rec) * f->num_cells;
-  const int per_sm = records > l2_bytes() ? RTF_SAMPLE_BLOCKS_PER_SM_BIG : RTF_SAMPLE_BLOCKS_PER_SM;
+  const int per_sm = !coherent && records > l2_bytes() ? RTF_SAMPLE_BLOCKS_PER_SM_BIG
+                                                       : RTF_SAMPLE_BLOCKS_PER_SM;
   int64_t blocks = min((int64_t)sms * per_sm, (count + per_block - 1) / per_block);
   if (f->max_m <= kSmemGuideMaxBits) {
     size_t smem = sizeof(rtf_guide_rec) << f->max_m;
@@ -731,10 +732,11 @@ cudaError_t launch_sample(const rtf_forest* f, const uint32_t* u, const int32_t*
                           cudaStream_t st) {
   if (count == 0) return cudaSuccess;
   const int base = mode & 0xFF;
+  const bool coherent = (mode & RTF_SAMPLE_COHERENT) != 0;
   if (mode & RTF_SAMPLE_BSEARCH)
-    launch_sample_t<true>(f, u, dist_id, count, base, idx_out, pos_out, st);
+    launch_sample_t<true>(f, u, dist_id, count, base, coherent, idx_out, pos_out, st);
   else
-    launch_sample_t<false>(f, u, dist_id, count, base, idx_out, pos_out, st);
+    launch_sample_t<false>(f, u, dist_id, count, base, coherent, idx_out, pos_out, st);
   return cudaGetLastError();
 }
 

@@ -613,3 +613,15 @@ def test_pipelined_done_event_overlaps_next_call():
     for u, bufs, ev in outs:
         ridx, rpos = orc.sample(ref.C, u)
         check_samples(bufs["idx_host"].numpy(), bufs["pos_host"].numpy(), ridx, rpos)
+
+
+def test_coherent_hint_changes_nothing_but_the_grid(big):
+    """RTF_SAMPLE_COHERENT only selects the launch shape: identical results on
+    scattered and on sorted samples, both methods."""
+    w, f, ref = big
+    for u in (W.iid_u32(1 << 22, seed=90), W.sorted_radical_inverse_u32(1 << 26)[::16]):
+        ud = api.u32_tensor(u, DEV)
+        for method in (0, api.SAMPLE_BSEARCH):
+            i1, p1 = api.rtf_sample(f, ud, mode=api.SAMPLE_1D | method)
+            i2, p2 = api.rtf_sample(f, ud, mode=api.SAMPLE_1D | method | api.SAMPLE_COHERENT)
+            assert torch.equal(i1, i2) and torch.equal(p1.view(torch.int32), p2.view(torch.int32))

@@ -80,7 +80,7 @@ def test_bad_arguments_rejected_without_gpu_work(lib):
                           ctypes.c_void_p(16), None) == EINVAL
     assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 5, 1, ctypes.c_void_p(16),
                           ctypes.c_void_p(16), None) == EINVAL  # 2-D needs a marginal
-    for mode in (2, 0x200, 0x101, 0x80):  # unknown mode or flag; 2-D + bsearch needs a marginal
+    for mode in (2, 0x400, 0x101, 0x301, 0x80):  # unknown mode or flag; 2-D + bsearch needs a marginal
         assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 5, mode,
                               ctypes.c_void_p(16), ctypes.c_void_p(16), None) == EINVAL
     assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 0, 0, None, None,
