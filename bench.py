@@ -240,21 +240,40 @@ def gpu_arm(args):
     # the sorted set is passed with the coherence hint (a sorted sequence in order)
     SORTED_MODE = api.SAMPLE_1D | api.SAMPLE_COHERENT
 
+    # With --streams 2 the sorted set is sampled on a second stream, at the
+    # same time as the i.i.d. set and its backward: the two sides stress
+    # different parts of the chip (DRAM lines and L2 updates on one, issue
+    # slots on the other).
+    side = torch.cuda.Stream(dev) if args.streams == 2 else stream
+    ev_built = torch.cuda.Event()
+
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
         api.rtf_build(wd, M_BITS, forest=f)
         if ev is not None:
             ev[1].record(stream)
+        if side is not stream:
+            ev_built.record(stream)
+            side.wait_event(ev_built)
+            with torch.cuda.stream(side):
+                if ev is not None:
+                    ev[5].record(side)
+                api.rtf_sample(f, us, mode=SORTED_MODE, idx_out=idx_s, pos_out=pos_s)
+                if ev is not None:
+                    ev[6].record(side)
         api.rtf_sample(f, ui, idx_out=idx_i, pos_out=pos_i)
         if ev is not None:
             ev[2].record(stream)
-        api.rtf_sample(f, us, mode=SORTED_MODE, idx_out=idx_s, pos_out=pos_s)
+        if side is stream:
+            api.rtf_sample(f, us, mode=SORTED_MODE, idx_out=idx_s, pos_out=pos_s)
         if ev is not None:
             ev[3].record(stream)
         api.rtf_sample_backward(f, wd, ui, None, idx_i, pos_i, gd, grad_w=grad_w)
         if ev is not None:
             ev[4].record(stream)
+        if side is not stream:
+            stream.wait_stream(side)
 
     for _ in range(args.warmup):
         step()
@@ -262,7 +281,7 @@ def gpu_arm(args):
     f.check_status()
 
     part = {k: [] for k in names}
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     if dist:
@@ -278,8 +297,12 @@ def gpu_arm(args):
         dist.barrier()
     total_ms = start.elapsed_time(end)
     for k in range(args.steps):
-        for i, nm in enumerate(names):
-            part[nm].append(evs[k][i].elapsed_time(evs[k][i + 1]))
+        e = evs[k]
+        part["build"].append(e[0].elapsed_time(e[1]))
+        part["sample_iid"].append(e[1].elapsed_time(e[2]))
+        part["backward"].append(e[3].elapsed_time(e[4]))
+        part["sample_sorted"].append(e[5].elapsed_time(e[6]) if side is not stream
+                                     else e[2].elapsed_time(e[3]))
     f.check_status()
     ms = max_over_ranks(total_ms / args.steps, dist, dev)
 
@@ -360,7 +383,9 @@ def gpu_arm(args):
         "config": {"workload": f"n=2^24 lognormal(0,2) weights, 2^20 guide cells, "
                                f"2^{lg} iid + 2^{lg} sorted radical-inverse samples, "
                                f"backward on the iid set",
-                   "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
+                   "l2": "inputs larger than L2", "parallelism": f"replicas{world}",
+                   "streams": (f"{args.streams}: sorted set concurrent with the i.i.d. set and "
+                               f"the backward" if args.streams == 2 else "1")},
         "breakdown_ms": avg,
         "build_elem_per_s": N_W / (avg["build"] * 1e-3),
         "sample_iid_per_s": N_S / (avg["sample_iid"] * 1e-3),
@@ -618,6 +643,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged-batch, 2-D map and backward measurements")
+    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
+                    help="2: sample the sorted set on a second stream, concurrently with the "
+                         "i.i.d. set and the backward")
     ap.add_argument("--samples-log2", type=int, default=28,
                     help="2^k samples per set; the benchmarked workload is k = 28, smaller k "
                          "gives the same structure with fewer samples (profiler captures)")
