@@ -244,8 +244,16 @@ def gpu_arm(args):
     # same time as the i.i.d. set and its backward: the two sides stress
     # different parts of the chip (DRAM lines and L2 updates on one, issue
     # slots on the other).
-    side = torch.cuda.Stream(dev) if args.streams == 2 else stream
+    # With --streams 3 the backward of the i.i.d. set also overlaps its
+    # sampling: the set is mapped in ACC_CHUNKS chunks and each chunk's terms
+    # are added to the per-bin sums on a third stream as soon as the chunk is
+    # mapped (rtf_backward_accumulate); the gradient is finished once all are in.
+    side = torch.cuda.Stream(dev) if args.streams >= 2 else stream
+    acc_stream = torch.cuda.Stream(dev) if args.streams == 3 else None
+    accum = api.GradientAccumulator(f) if args.streams == 3 else None
+    ACC_CHUNKS = 8
     ev_built = torch.cuda.Event()
+    ev_chunk = [torch.cuda.Event() for _ in range(ACC_CHUNKS)]
 
     def step(ev=None):
         if ev is not None:
@@ -253,6 +261,35 @@ def gpu_arm(args):
         api.rtf_build(wd, M_BITS, forest=f)
         if ev is not None:
             ev[1].record(stream)
+        if accum is not None:
+            ev_built.record(stream)
+            side.wait_event(ev_built)
+            acc_stream.wait_event(ev_built)
+            with torch.cuda.stream(side):
+                if ev is not None:
+                    ev[5].record(side)
+                api.rtf_sample(f, us, mode=SORTED_MODE, idx_out=idx_s, pos_out=pos_s)
+                if ev is not None:
+                    ev[6].record(side)
+            with torch.cuda.stream(acc_stream):
+                accum.begin()
+            cs = N_S // ACC_CHUNKS
+            for k in range(ACC_CHUNKS):
+                sl = slice(k * cs, (k + 1) * cs)
+                api.rtf_sample(f, ui[sl], idx_out=idx_i[sl], pos_out=pos_i[sl])
+                ev_chunk[k].record(stream)
+                acc_stream.wait_event(ev_chunk[k])
+                with torch.cuda.stream(acc_stream):
+                    accum.accumulate(idx_i[sl], pos_i[sl], gd[sl])
+            if ev is not None:
+                ev[2].record(stream)
+                ev[3].record(stream)
+            stream.wait_stream(acc_stream)
+            accum.finish(wd, grad_w=grad_w)
+            if ev is not None:
+                ev[4].record(stream)
+            stream.wait_stream(side)
+            return
         if side is not stream:
             ev_built.record(stream)
             side.wait_event(ev_built)
@@ -384,8 +421,10 @@ def gpu_arm(args):
                                f"2^{lg} iid + 2^{lg} sorted radical-inverse samples, "
                                f"backward on the iid set",
                    "l2": "inputs larger than L2", "parallelism": f"replicas{world}",
-                   "streams": (f"{args.streams}: sorted set concurrent with the i.i.d. set and "
-                               f"the backward" if args.streams == 2 else "1")},
+                   "streams": {1: "1", 2: "2: sorted set concurrent with the i.i.d. set and "
+                                           "the backward",
+                               3: "3: sorted set concurrent; backward accumulated per chunk of "
+                                  "the i.i.d. set while later chunks are mapped"}[args.streams]},
         "breakdown_ms": avg,
         "build_elem_per_s": N_W / (avg["build"] * 1e-3),
         "sample_iid_per_s": N_S / (avg["sample_iid"] * 1e-3),
@@ -398,7 +437,8 @@ def gpu_arm(args):
         "e2e": {"value": job_throughput(world, 2 * N_S, max_over_ranks(e2e_ms, dist, dev)),
                 "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": (LAUNCHES_PER_STEP + (2 * (ACC_CHUNKS - 1) if args.streams == 3 else 0))
+                        * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_extras:
@@ -643,9 +683,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ragged-batch, 2-D map and backward measurements")
-    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
+    ap.add_argument("--streams", type=int, default=2, choices=[1, 2, 3],
                     help="2: sample the sorted set on a second stream, concurrently with the "
-                         "i.i.d. set and the backward")
+                         "i.i.d. set and the backward; 3: also accumulate the backward chunk by "
+                         "chunk on a third stream while the i.i.d. set is mapped")
     ap.add_argument("--samples-log2", type=int, default=28,
                     help="2^k samples per set; the benchmarked workload is k = 28, smaller k "
                          "gives the same structure with fewer samples (profiler captures)")

@@ -352,6 +352,33 @@ rtf_status rtf_sample_backward(const rtf_forest *f, const float *w,
                                int32_t mode, float *grad_w, void *ws,
                                size_t ws_bytes, void *stream);
 
+/*
+ * The backward in three steps, for gradients accumulated over several sample
+ * batches or computed while later samples are still being drawn
+ * (rtf_sample_backward is the three in a row):
+ *
+ *   rtf_backward_begin       clears the per-bin sums held in ws.
+ *   rtf_backward_accumulate  adds the terms {dL/dpos, dL/dpos * pos} of
+ *                            `count` samples (inputs as for
+ *                            rtf_sample_backward) to the per-bin sums; any
+ *                            number of calls, any split of the samples.
+ *   rtf_backward_finish      turns the sums into grad_w (float32[offsets[D_w]]).
+ *
+ * The calls on one workspace must be ordered (one stream, or events); the
+ * workspace holds the sums between them.  Summation order differs between
+ * splits, so results agree to float rounding, not bit for bit.
+ */
+rtf_status rtf_backward_begin(const rtf_forest *f, void *ws, size_t ws_bytes,
+                              void *stream);
+rtf_status rtf_backward_accumulate(const rtf_forest *f, const int32_t *dist_id,
+                                   const int32_t *idx, const float *pos,
+                                   const float *grad_pos, int64_t count,
+                                   int32_t mode, void *ws, size_t ws_bytes,
+                                   void *stream);
+rtf_status rtf_backward_finish(const rtf_forest *f, const float *w, int32_t mode,
+                               float *grad_w, void *ws, size_t ws_bytes,
+                               void *stream);
+
 #ifdef __cplusplus
 } /* extern "C" */
 #endif

@@ -123,6 +123,14 @@ EXPORTS = {
     "rtf_sample_loads": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "rtf_backward_begin": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.c_void_p]),
+    "rtf_backward_accumulate": (ctypes.c_int, [ctypes.POINTER(RtfForestC)] + [ctypes.c_void_p] * 4
+                                + [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                   ctypes.c_size_t, ctypes.c_void_p]),
+    "rtf_backward_finish": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_void_p]),
     "rtf_backward_workspace_size": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
     "rtf_sample_backward": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -315,6 +315,44 @@ def rtf_sample_backward(forest: Forest, w: torch.Tensor, u: torch.Tensor,
     return grad_w
 
 
+class GradientAccumulator:
+    """``rtf_backward_begin`` / ``_accumulate`` / ``_finish`` with a workspace of
+    its own: dL/dw summed over any number of sample batches, each call on the
+    current stream (the caller orders calls made on different streams)."""
+
+    def __init__(self, forest: Forest, mode: int = SAMPLE_1D):
+        self.forest = forest
+        self.mode = mode
+        self.lib = _native.load()
+        nbytes = self.lib.rtf_backward_workspace_size(forest.num_elems, forest.num_dists)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=forest.device)
+        self.cf = forest.c_struct()
+
+    def begin(self):
+        _check(self.lib.rtf_backward_begin(ctypes.byref(self.cf), _ptr(self.ws), self.ws.numel(),
+                                           _stream_ptr(self.ws.device)), "rtf_backward_begin")
+        return self
+
+    def accumulate(self, idx: torch.Tensor, pos: torch.Tensor, grad_pos: torch.Tensor,
+                   dist_id: torch.Tensor | None = None):
+        _need(grad_pos, torch.float32, "grad_pos")
+        count = pos.numel() // (2 if (self.mode & 0xFF) == SAMPLE_2D else 1)
+        _check(self.lib.rtf_backward_accumulate(ctypes.byref(self.cf), _ptr(dist_id), _ptr(idx),
+                                                _ptr(pos), _ptr(grad_pos), count, self.mode,
+                                                _ptr(self.ws), self.ws.numel(),
+                                                _stream_ptr(self.ws.device)),
+               "rtf_backward_accumulate")
+
+    def finish(self, w: torch.Tensor, grad_w: torch.Tensor | None = None) -> torch.Tensor:
+        _need(w, torch.float32, "w")
+        if grad_w is None:
+            grad_w = torch.empty_like(w)
+        _check(self.lib.rtf_backward_finish(ctypes.byref(self.cf), _ptr(w), self.mode,
+                                            _ptr(grad_w), _ptr(self.ws), self.ws.numel(),
+                                            _stream_ptr(self.ws.device)), "rtf_backward_finish")
+        return grad_w
+
+
 def u32_tensor(a: np.ndarray, device) -> torch.Tensor:
     """Host uint32 samples -> device int32 tensor holding the same bits."""
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).to(device)

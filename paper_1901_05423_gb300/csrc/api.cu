@@ -23,6 +23,12 @@ cudaError_t launch_sample_pipelined(const rtf_forest* f, const uint32_t* u_host,
 cudaError_t launch_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
                                 int64_t count, int mode, int32_t* loads_out, cudaStream_t st);
 size_t backward_ws_bytes(int64_t N, int32_t D);
+cudaError_t launch_backward_begin(const rtf_forest* f, void* ws, cudaStream_t st);
+cudaError_t launch_backward_accumulate(const rtf_forest* f, const int32_t* dist_id,
+                                       const int32_t* idx, const float* pos, const float* gpos,
+                                       int64_t count, int mode, void* ws, cudaStream_t st);
+cudaError_t launch_backward_finish(const rtf_forest* f, const float* w, int mode, float* grad_w,
+                                   void* ws, cudaStream_t st);
 cudaError_t launch_backward(const rtf_forest* f, const float* w, const uint32_t* u,
                             const int32_t* dist_id, const int32_t* idx, const float* pos,
                             const float* gpos, int64_t count, int mode, float* grad_w, void* ws,
@@ -176,6 +182,43 @@ rtf_status rtf_sample_backward(const rtf_forest* f, const float* w, const uint32
   if (ws_bytes < rtf_backward_workspace_size(f->num_elems, f->num_dists)) return RTF_EWORKSPACE;
   return cuda_status(rtf::launch_backward(f, w, u, dist_id, idx, pos, grad_pos, count, mode,
                                           grad_w, ws, static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_backward_begin(const rtf_forest* f, void* ws, size_t ws_bytes, void* stream) {
+  if (!forest_ok(f) || !ws || !aligned(ws, 256)) return RTF_EINVAL;
+  if (ws_bytes < rtf_backward_workspace_size(f->num_elems, f->num_dists)) return RTF_EWORKSPACE;
+  return cuda_status(rtf::launch_backward_begin(f, ws, static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_backward_accumulate(const rtf_forest* f, const int32_t* dist_id,
+                                   const int32_t* idx, const float* pos, const float* grad_pos,
+                                   int64_t count, int32_t mode, void* ws, size_t ws_bytes,
+                                   void* stream) {
+  if (!forest_ok(f) || !ws || !aligned(ws, 256) || count < 0) return RTF_EINVAL;
+  if (count > 0 && (!idx || !pos || !grad_pos)) return RTF_EINVAL;
+  if (mode == RTF_SAMPLE_2D) {
+    if (!(f->flags & RTF_FOREST_MARGINAL) || dist_id) return RTF_EINVAL;
+    if (count > 0 && (!aligned(idx, 8) || !aligned(pos, 8) || !aligned(grad_pos, 8)))
+      return RTF_EINVAL;
+  } else if (mode != RTF_SAMPLE_1D) {
+    return RTF_EINVAL;
+  }
+  if (ws_bytes < rtf_backward_workspace_size(f->num_elems, f->num_dists)) return RTF_EWORKSPACE;
+  return cuda_status(rtf::launch_backward_accumulate(f, dist_id, idx, pos, grad_pos, count, mode,
+                                                     ws, static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_backward_finish(const rtf_forest* f, const float* w, int32_t mode, float* grad_w,
+                               void* ws, size_t ws_bytes, void* stream) {
+  if (!forest_ok(f) || !w || !grad_w || !ws || !aligned(ws, 256)) return RTF_EINVAL;
+  if (mode == RTF_SAMPLE_2D) {
+    if (!(f->flags & RTF_FOREST_MARGINAL)) return RTF_EINVAL;
+  } else if (mode != RTF_SAMPLE_1D) {
+    return RTF_EINVAL;
+  }
+  if (ws_bytes < rtf_backward_workspace_size(f->num_elems, f->num_dists)) return RTF_EWORKSPACE;
+  return cuda_status(
+      rtf::launch_backward_finish(f, w, mode, grad_w, ws, static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

@@ -440,52 +440,86 @@ static int bw_sms() {
 
 size_t backward_ws_bytes(int64_t N, int32_t D) { return bw_layout(N, D).total; }
 
-cudaError_t launch_backward(const rtf_forest* f, const float* w, const uint32_t* u,
-                            const int32_t* dist_id, const int32_t* idx, const float* pos,
-                            const float* gpos, int64_t count, int mode, float* grad_w, void* ws,
-                            cudaStream_t st) {
-  (void)u;  // xi follows exactly from the bin and the position (see the file comment)
+// The backward in three steps: clear the per-bin sums, add the samples' terms
+// (any number of times), turn the sums into the gradient.
+struct BwPtrs {
+  BwLayout L;
+  char* base;
+  float2* acc;
+};
+
+static BwPtrs bw_ptrs(const rtf_forest* f, void* ws) {
+  BwPtrs p;
+  p.L = bw_layout(f->num_elems, f->num_dists);
+  p.base = static_cast<char*>(ws);
+  p.acc = reinterpret_cast<float2*>(p.base + p.L.acc);
+  return p;
+}
+
+cudaError_t launch_backward_begin(const rtf_forest* f, void* ws, cudaStream_t st) {
+  const BwPtrs p = bw_ptrs(f, ws);
+  return cudaMemsetAsync(p.base, 0, p.L.zero_end, st);
+}
+
+cudaError_t launch_backward_accumulate(const rtf_forest* f, const int32_t* dist_id,
+                                       const int32_t* idx, const float* pos, const float* gpos,
+                                       int64_t count, int mode, void* ws, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const BwPtrs p = bw_ptrs(f, ws);
+  const int D = f->num_dists;
+  const int sms = bw_sms();
+  const int64_t blocks = std::min<int64_t>((int64_t)sms * 8, (count + kBwThreads - 1) / kBwThreads);
+  if (mode == RTF_SAMPLE_2D)
+    scatter_2d_kernel<<<(unsigned)blocks, kBwThreads, 0, st>>>(
+        f->dists, D, reinterpret_cast<const int2*>(idx), reinterpret_cast<const float2*>(pos),
+        reinterpret_cast<const float2*>(gpos), count, p.acc);
+  else
+    scatter_1d_kernel<<<(unsigned)blocks, kBwThreads, 0, st>>>(f->dists, D, dist_id, idx, pos,
+                                                               gpos, count, p.acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_finish(const rtf_forest* f, const float* w, int mode, float* grad_w,
+                                   void* ws, cudaStream_t st) {
+  const BwPtrs p = bw_ptrs(f, ws);
+  const BwLayout& L = p.L;
   const int64_t N = f->num_elems;
   const int D = f->num_dists;
   const bool two_d = mode == RTF_SAMPLE_2D;
-  BwLayout L = bw_layout(N, D);
-  char* base = static_cast<char*>(ws);
-  float2* acc = reinterpret_cast<float2*>(base + L.acc);
-  double* G = reinterpret_cast<double*>(base + L.G);
-  uint32_t* flags = reinterpret_cast<uint32_t*>(base + L.flags);
-  double* carry = reinterpret_cast<double*>(base + L.carry);
-  double* incl = reinterpret_cast<double*>(base + L.incl);
-  uint32_t* ticket = reinterpret_cast<uint32_t*>(base + L.ticket);
-  float* R = reinterpret_cast<float*>(base + L.R);
-  float* gradR = reinterpret_cast<float*>(base + L.gradR);
+  double* G = reinterpret_cast<double*>(p.base + L.G);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(p.base + L.flags);
+  double* carry = reinterpret_cast<double*>(p.base + L.carry);
+  double* incl = reinterpret_cast<double*>(p.base + L.incl);
+  uint32_t* ticket = reinterpret_cast<uint32_t*>(p.base + L.ticket);
+  float* R = reinterpret_cast<float*>(p.base + L.R);
+  float* gradR = reinterpret_cast<float*>(p.base + L.gradR);
   const int64_t Nw = two_d ? N - (D - 1) : N;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(base, 0, L.zero_end, st))) return e;
   const int sms = bw_sms();
   if (two_d) {
     row_sum_kernel<<<(unsigned)std::min<int64_t>(sms * 4, (D + 7) / 8), 256, 0, st>>>(
         w, f->dists, D - 1, R);
   }
-  if (count > 0) {
-    int64_t blocks = std::min<int64_t>((int64_t)sms * 8, (count + kBwThreads - 1) / kBwThreads);
-    if (two_d)
-      scatter_2d_kernel<<<(unsigned)blocks, kBwThreads, 0, st>>>(
-          f->dists, D, reinterpret_cast<const int2*>(idx), reinterpret_cast<const float2*>(pos),
-          reinterpret_cast<const float2*>(gpos), count, acc);
-    else
-      scatter_1d_kernel<<<(unsigned)blocks, kBwThreads, 0, st>>>(f->dists, D, dist_id, idx, pos,
-                                                                 gpos, count, acc);
-  }
   const int64_t tiles = (N + kBwTile - 1) / kBwTile;
-  bin_total_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(acc, f->nodes, w, R, f->dists, D, N,
+  bin_total_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, f->nodes, w, R, f->dists, D, N,
                                                            Nw, G);
-  suffix_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(acc, w, R, f->dists, D, N, Nw, G, flags,
+  suffix_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, w, R, f->dists, D, N, Nw, G, flags,
                                                         carry, incl, ticket, grad_w, gradR,
                                                         f->status);
   if (two_d)
     add_row_kernel<<<(unsigned)std::min<int64_t>(sms * 4, D - 1), 256, 0, st>>>(
         grad_w, f->dists, D - 1, gradR);
   return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const rtf_forest* f, const float* w, const uint32_t* u,
+                            const int32_t* dist_id, const int32_t* idx, const float* pos,
+                            const float* gpos, int64_t count, int mode, float* grad_w, void* ws,
+                            cudaStream_t st) {
+  (void)u;  // xi follows exactly from the bin and the position (see the file comment)
+  cudaError_t e;
+  if ((e = launch_backward_begin(f, ws, st))) return e;
+  if ((e = launch_backward_accumulate(f, dist_id, idx, pos, gpos, count, mode, ws, st))) return e;
+  return launch_backward_finish(f, w, mode, grad_w, ws, st);
 }
 
 }  // namespace rtf

@@ -216,3 +216,59 @@ def test_autograd_function_2d_matches_oracle():
     r, c, _, _ = orc.sample_env(rows, marg, u_h[0::2], u_h[1::2])
     gref = orc.grad_env(lum_h, u_h[0::2], u_h[1::2], r, c, c_h[:, 0].copy(), c_h[:, 1].copy())
     assert rel_err(lum.grad.cpu().numpy(), gref) <= TOL
+
+
+def test_accumulated_backward_equals_one_call():
+    """begin / accumulate over uneven chunks / finish gives the one-call
+    gradient up to float summation order, and the oracle's within 1e-4."""
+    n, n_s, m = 50000, 300001, 13
+    w = W.lognormal_weights(n, seed=100, sigma=1.5)
+    u = W.iid_u32(n_s, seed=101)
+    g = W.normal_f32(n_s, seed=102)
+    wd, ud, gd = to_dev(w), api.u32_tensor(u, DEV), to_dev(g)
+    f = api.rtf_build(wd, m)
+    idx, pos = api.rtf_sample(f, ud)
+    one = api.rtf_sample_backward(f, wd, ud, None, idx, pos, gd).cpu().numpy()
+    acc = api.GradientAccumulator(f).begin()
+    cuts = [0, 7, 100000, 100004, 250000, n_s]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        acc.accumulate(idx[a:b], pos[a:b], gd[a:b])
+    split = acc.finish(wd).cpu().numpy()
+    assert rel_err(split, one.astype(np.float64)) <= 1e-5
+    ref = orc.build(w, 1 << m)
+    ridx, _ = orc.sample(ref.C, u)
+    assert rel_err(split, orc.grad(w, u, ridx, g)) <= TOL
+
+
+def test_accumulated_backward_2d_and_on_a_second_stream():
+    """2-D accumulation, with the accumulate calls on a side stream ordered by
+    events after the samples they read."""
+    H, Wd, n_s = 64, 96, 1 << 16
+    lum = W.env_map(H, Wd, seed=110)
+    wd = to_dev(lum.reshape(-1))
+    f = api.rtf_build_batched(wd, [Wd] * H + [H], [7] * H + [6], marginal=True)
+    rng = np.random.default_rng(111)
+    u = rng.integers(0, 1 << 32, 2 * n_s, dtype=np.uint64).astype(np.uint32)
+    g = W.normal_f32(2 * n_s, seed=112)
+    ud, gd = api.u32_tensor(u, DEV), to_dev(g)
+    idx = torch.empty((n_s, 2), dtype=torch.int32, device=DEV)
+    pos = torch.empty((n_s, 2), dtype=torch.float32, device=DEV)
+    side = torch.cuda.Stream()
+    acc = api.GradientAccumulator(f, mode=api.SAMPLE_2D)
+    ev0 = torch.cuda.Event()
+    ev0.record()
+    side.wait_event(ev0)
+    with torch.cuda.stream(side):
+        acc.begin()
+    half = n_s // 2
+    for a, b in ((0, half), (half, n_s)):
+        api.rtf_sample(f, ud[2 * a:2 * b], mode=api.SAMPLE_2D, idx_out=idx[a:b], pos_out=pos[a:b])
+        ev = torch.cuda.Event()
+        ev.record()
+        side.wait_event(ev)
+        with torch.cuda.stream(side):
+            acc.accumulate(idx[a:b], pos[a:b], gd[2 * a:2 * b])
+    torch.cuda.current_stream().wait_stream(side)
+    split = acc.finish(wd).cpu().numpy()
+    one = api.rtf_sample_backward(f, wd, ud, None, idx, pos, gd, mode=api.SAMPLE_2D).cpu().numpy()
+    assert rel_err(split, one.astype(np.float64)) <= 1e-5

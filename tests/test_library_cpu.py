@@ -85,6 +85,15 @@ def test_bad_arguments_rejected_without_gpu_work(lib):
                               ctypes.c_void_p(16), ctypes.c_void_p(16), None) == EINVAL
     assert lib.rtf_sample(ctypes.byref(f), ctypes.c_void_p(16), None, 0, 0, None, None,
                           None) == 0  # nothing to do
+    P0 = ctypes.c_void_p
+    assert lib.rtf_backward_begin(ctypes.byref(f), P0(8), 1 << 30, None) == EINVAL  # ws alignment
+    assert lib.rtf_backward_begin(ctypes.byref(f), P0(256), 16, None) == 2  # workspace too small
+    assert lib.rtf_backward_accumulate(ctypes.byref(f), None, None, None, None, 5, 0, P0(256),
+                                       1 << 30, None) == EINVAL  # count > 0 needs inputs
+    assert lib.rtf_backward_accumulate(ctypes.byref(f), None, P0(16), P0(16), P0(16), 5, 1,
+                                       P0(256), 1 << 30, None) == EINVAL  # 2-D needs a marginal
+    assert lib.rtf_backward_finish(ctypes.byref(f), None, 0, P0(16), P0(256), 1 << 30,
+                                   None) == EINVAL  # weights needed
     P = ctypes.c_void_p
     for chunk in (0, 3, 6):  # chunks are positive multiples of 4
         assert lib.rtf_sample_pipelined(ctypes.byref(f), None, P(16), None, None, 8, 0, P(16),
