@@ -79,10 +79,14 @@ typedef enum rtf_status {
    the radix forest; identical bins and positions */
 #define RTF_SAMPLE_BSEARCH 0x100
 /* hint OR-ed into the mode of rtf_sample: neighbouring samples are close (a
-   sorted or low-discrepancy sequence in order), so the sampler runs with the
-   full grid; without it, a structure larger than L2 is sampled by fewer
-   resident threads, which keeps more of it in L2 for scattered samples.
-   Results do not depend on the hint. */
+   sorted or low-discrepancy sequence in order).  For one distribution in 1-D
+   with the radix forest, each thread then maps runs of consecutive samples,
+   reusing the previous sample's bin or stepping to the next bins and
+   descending (Algorithm 2) only where neither holds; otherwise the hint only
+   selects the full grid (without it, a structure larger than L2 is sampled by
+   fewer resident threads, which keeps more of it in L2 for scattered
+   samples).  Results do not depend on the hint: every way finds the unique
+   bin with C_i <= t < C_{i+1}. */
 #define RTF_SAMPLE_COHERENT 0x200
 
 /*

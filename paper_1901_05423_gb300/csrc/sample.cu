@@ -453,6 +453,134 @@ __global__ void __launch_bounds__(kSampleThreads, RTF_SAMPLE_MINB)
   }
 }
 
+// Algorithm 2 for one sample from its guide record down to the leaf, the
+// bounds C_i and C_{i+1} tracked on the way as in sample_group.  False when the
+// structure is invalid (an index out of range, a path longer than any
+// reachable one, or bounds that do not bracket t).
+__device__ __forceinline__ bool descend_one(const DistView& v, uint32_t u, uint64_t t,
+                                            uint64_t pol, int32_t& i, uint64_t& lo,
+                                            uint64_t& hi) {
+  const uint32_t n32 = (uint32_t)v.n;
+  const uint32_t g = v.m ? (u >> (32 - v.m)) : 0u;
+  uint64_t c, glo, ghi;
+  int32_t c0, c1;
+  load_guide(v.guide + g, pol, c, c0, c1, glo, ghi);
+  const bool left = t < c;
+  int32_t j = left ? c0 : c1;
+  lo = left ? glo : c;
+  hi = left ? c : ghi;
+  for (int step = 0; j >= 0 && step < 64; ++step) {
+    if ((uint32_t)j >= n32) return false;
+    uint64_t cj;
+    int32_t a, b;
+    load_node(v.nodes + j, pol, cj, a, b);
+    if (t < cj) {
+      j = a;
+      hi = cj;
+    } else {
+      j = b;
+      lo = cj;
+    }
+  }
+  i = ~j;
+  return j < 0 && (uint32_t)i < n32 && lo <= t && t < hi;
+}
+
+// Samples that arrive in ascending order (sorted or low-discrepancy sequences,
+// the monotone mapping of Sec. 3.2) mostly fall into the bin of the sample
+// before them or into the next one.  Each thread maps a run of R consecutive
+// samples: a sample whose t lies in [C_i, C_{i+1}) of the previous sample's
+// bin i takes bin i; one with t >= C_{i+1} steps forward over at most
+// kRunSteps bins (bin i + 1 is [C_{i+1}, C_{i+2}), one CDF load each;
+// zero-width bins are passed over); any other sample, and the first of every
+// run, descends from its guide record (Algorithm 2).  Each way yields the
+// unique bin with C_i <= t < C_{i+1} and its two bounds, so indices and
+// positions are the bits of sample_group for every input order; the order only
+// decides the speed.  The kernel is bound by the latency of the loads of the
+// lanes that step or descend while the others wait; short runs keep the
+// registers low enough for five resident blocks per SM (GB300, 2^28 sorted
+// samples at n = 2^24: 1.04 ms with runs of 8, 1.17 ms with runs of 16 at four
+// blocks per SM, 1.37 ms with runs of 4; 1.93 ms for the per-sample descent).
+#ifndef RTF_RUN_SAMPLES
+#define RTF_RUN_SAMPLES 8
+#endif
+#ifndef RTF_RUN_MINB
+#define RTF_RUN_MINB 5
+#endif
+constexpr int kRunSamples = RTF_RUN_SAMPLES;
+constexpr int kRunSteps = 4;
+
+template <int R>
+__global__ void __launch_bounds__(kSampleThreads, RTF_RUN_MINB)
+    sample_runs_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
+                       const rtf_dist* __restrict__ dists, const uint32_t* __restrict__ u,
+                       int64_t count, int32_t* __restrict__ idx_out,
+                       float* __restrict__ pos_out) {
+  static_assert(R % 4 == 0 && R >= 4, "runs move as 16-byte vectors");
+  constexpr int V = R / 4;
+  const DistView v = dist_view(dists, 0, nodes, guide);
+  const uint64_t pol = l2_evict_last_policy();
+  const int64_t n = v.n;
+  const int64_t runs = count / R;
+  const uint4* u4 = reinterpret_cast<const uint4*>(u);
+  int4* i4 = reinterpret_cast<int4*>(idx_out);
+  float4* p4 = reinterpret_cast<float4*>(pos_out);
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = gtid; q < runs; q += stride) {
+    uint32_t uu[R];
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+      const uint4 x = __ldcs(u4 + q * V + c);
+      uu[4 * c] = x.x;
+      uu[4 * c + 1] = x.y;
+      uu[4 * c + 2] = x.z;
+      uu[4 * c + 3] = x.w;
+    }
+    int32_t ii[R];
+    float pp[R];
+    int32_t cur = -1;  // bin of the previous sample, -1 before the first
+    uint64_t lo = 0, hi = 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      uint64_t t;
+      uint32_t r;
+      scale_sample(uu[k], v.T, t, r);
+      bool ok = cur >= 0 && lo <= t && t < hi;
+      if (!ok && cur >= 0 && t >= hi) {
+        for (int s = 0; s < kRunSteps && cur + 2 <= n; ++s) {
+          const uint64_t c2 = cur + 2 < n ? load_cdf(v.nodes + cur + 2, pol) : v.T;
+          ++cur;
+          lo = hi;
+          hi = c2;
+          if (t < hi) {
+            ok = true;
+            break;
+          }
+        }
+      }
+      if (!ok) {
+        ok = descend_one(v, uu[k], t, pol, cur, lo, hi);
+        if (!ok) cur = -1;
+      }
+      ii[k] = ok ? cur : -1;
+      pp[k] = ok ? in_bin_position(t - lo, r, hi - lo) : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+      __stcs(i4 + q * V + c, make_int4(ii[4 * c], ii[4 * c + 1], ii[4 * c + 2], ii[4 * c + 3]));
+      __stcs(p4 + q * V + c, make_float4(pp[4 * c], pp[4 * c + 1], pp[4 * c + 2], pp[4 * c + 3]));
+    }
+  }
+  for (int64_t s = runs * R + gtid; s < count; s += stride) {
+    int32_t ii;
+    float pp;
+    sample_one<false, false>(v, nullptr, u[s], pol, ii, pp);
+    idx_out[s] = ii;
+    pos_out[s] = pp;
+  }
+}
+
 // Algorithm 2 and the position for K samples of K distributions (a distribution
 // id per sample): as sample_group, with the distribution's parameters per
 // slot.  A sample with an invalid id yields idx = -1 and sets bad_id.
@@ -696,6 +824,23 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
     sample_tagged_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
         f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
         f->status);
+    return;
+  }
+  if (coherent && !BS) {
+    // one wave of resident blocks (grid-stride over the runs)
+    static int resident = 0;
+    if (resident == 0) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sample_runs_kernel<kRunSamples>,
+                                                        kSampleThreads, 0) != cudaSuccess ||
+          b <= 0)
+        b = RTF_RUN_MINB;
+      resident = b;
+    }
+    const int64_t per = (int64_t)kSampleThreads * kRunSamples;
+    const int64_t blocks = min((int64_t)sms * resident, (count + per - 1) / per);
+    sample_runs_kernel<kRunSamples><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
+        f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out);
     return;
   }
   const int64_t per_block = (int64_t)kSampleThreads * 4;

@@ -241,10 +241,19 @@ def test_full_size_samples(big):
     the benchmark; the oracle checks every 64th sample of each."""
     w, f, ref = big
     n_s = 1 << 28
-    for name, u in (("iid", W.iid_u32(n_s, seed=1)), ("sorted", W.sorted_radical_inverse_u32(n_s))):
+    # the benchmark maps the sorted set with the coherence hint (runs of
+    # consecutive samples per thread)
+    for name, u, mode in (("iid", W.iid_u32(n_s, seed=1), api.SAMPLE_1D),
+                          ("sorted", W.sorted_radical_inverse_u32(n_s),
+                           api.SAMPLE_1D | api.SAMPLE_COHERENT)):
         ud = api.u32_tensor(u, DEV)
-        idx, pos = api.rtf_sample(f, ud)
+        idx, pos = api.rtf_sample(f, ud, mode=mode)
         torch.cuda.synchronize()
+        if mode & api.SAMPLE_COHERENT:
+            # every sample, against the per-sample descent
+            i2, p2 = api.rtf_sample(f, ud)
+            assert torch.equal(idx, i2) and torch.equal(pos.view(torch.int32), p2.view(torch.int32))
+            del i2, p2
         sel = np.arange(0, n_s, 64)
         sel = np.concatenate([sel, np.arange(n_s - 4096, n_s)])
         ridx, rpos = orc.sample(ref.C, u[sel])
@@ -625,3 +634,45 @@ def test_coherent_hint_changes_nothing_but_the_grid(big):
             i1, p1 = api.rtf_sample(f, ud, mode=api.SAMPLE_1D | method)
             i2, p2 = api.rtf_sample(f, ud, mode=api.SAMPLE_1D | method | api.SAMPLE_COHERENT)
             assert torch.equal(i1, i2) and torch.equal(p1.view(torch.int32), p2.view(torch.int32))
+
+
+@pytest.mark.parametrize("m", [0, 4, 14])
+def test_coherent_runs_match_oracle_all_weight_kinds(m):
+    """The run sampler (RTF_SAMPLE_COHERENT): a sample in the previous
+    sample's bin, a step forward over zero-width bins, a step backward and a
+    jump all give the oracle's bin and position.  Counts leave a ragged tail
+    (not a multiple of the 16-sample run)."""
+    rng = np.random.default_rng(50 + m)
+    for n, kind, w in weight_cases():
+        f = api.rtf_build(to_dev(w), m)
+        ref = orc.build(w, 1 << m)
+        base = np.sort(rng.integers(0, 1 << 32, 4096 + 13, dtype=np.uint64)).astype(np.uint32)
+        dense = np.sort(rng.integers(0, 1 << 32, 64, dtype=np.uint64)).astype(np.uint32)
+        dense = (dense[:, None] + np.arange(0, 4096, 16, dtype=np.uint32)).ravel()  # tight runs
+        orders = (base, base[::-1].copy(), np.repeat(base[:1000], 3),
+                  np.concatenate([base[:2000], base[100:1700]]), np.sort(dense))
+        for u in orders:
+            u = u.copy()
+            u[:2] = [0, 1]
+            u[-1] = 0xFFFFFFFF
+            idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV),
+                                      mode=api.SAMPLE_1D | api.SAMPLE_COHERENT)
+            torch.cuda.synchronize()
+            f.check_status()
+            ridx, rpos = orc.sample(ref.C, u)
+            try:
+                check_samples(idx, pos, ridx, rpos)
+            except AssertionError as e:
+                raise AssertionError(f"n={n} kind={kind} m={m} count={u.size}: {e}")
+
+
+def test_coherent_runs_tiny_counts():
+    """Fewer samples than one run, exactly one run, one run and a tail."""
+    w = W.lognormal_weights(5000, seed=8, sigma=2.0)
+    f = api.rtf_build(to_dev(w), 10)
+    ref = orc.build(w, 1 << 10)
+    for count in (1, 3, 15, 16, 17, 31, 33):
+        u = np.sort(W.iid_u32(count, seed=count))
+        idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV), mode=api.SAMPLE_1D | api.SAMPLE_COHERENT)
+        ridx, rpos = orc.sample(ref.C, u)
+        check_samples(idx, pos, ridx, rpos)
