@@ -13,7 +13,8 @@ Sampling of Discrete or Piecewise Constant Probability Distributions":
   ``index``, ``position``);
 * Algorithm 1 run sequentially (``forest``), the guide table of the Cutpoint
   method with the two's complement encoding of Sec. 3.2 (``guide``);
-* Algorithm 2 (``descend``);
+* Algorithm 2 (``descend``), and over 4-ary records that collapse two binary
+  levels (``quad``, ``descend_quad``; the section on k-ary trees);
 * the 2-D component-wise scheme of Sec. 5 (``build_env``, ``sample_env``);
 * the fp64 gradient of the in-bin position (``grad``; not in the paper).
 
@@ -75,6 +76,8 @@ def _load():
             "orc_guide": (None, [P, P, P, i64, i64, P]),
             "orc_descend": (i64, [P, P, P, i64, ctypes.c_uint32]),
             "orc_descend_steps": (i32, [P, P, P, i64, ctypes.c_uint32]),
+            "orc_quad": (None, [P, i64, P, P]),
+            "orc_descend_quad": (i64, [P, P, P, P, P, i64, ctypes.c_uint32, P]),
             "orc_build": (ctypes.c_int, [P, i64, i64, i64, P, P, P, P]),
             "orc_build_int": (ctypes.c_int, [P, i64, i64, P, P, P]),
             "orc_grad": (None, [P, i64, P, P, P, i64, P]),
@@ -191,6 +194,29 @@ def descend_steps(guide_tab, nodes, K, M: int, u: int) -> int:
     nd = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1)
     K = np.ascontiguousarray(K, dtype=np.uint64)
     return int(_load().orc_descend_steps(_p(g), _p(nd), _p(K), int(M), int(u)))
+
+
+def quad(nodes):
+    """``orc_quad`` (two binary levels collapsed into one 4-ary record):
+    split node ids int32[n, 3] and grandchildren int32[n, 4]."""
+    nd = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1)
+    n = nd.size // 2
+    split = np.zeros(3 * n, np.int32)
+    child = np.zeros(4 * n, np.int32)
+    _load().orc_quad(_p(nd), n, _p(split), _p(child))
+    return split.reshape(n, 3), child.reshape(n, 4)
+
+
+def descend_quad(guide_tab, nodes, split, child, K, M: int, u: int):
+    """``orc_descend_quad``: (interval, 4-ary records read)."""
+    g = np.ascontiguousarray(guide_tab, dtype=np.int32)
+    nd = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1)
+    sp = np.ascontiguousarray(split, dtype=np.int32).reshape(-1)
+    ch = np.ascontiguousarray(child, dtype=np.int32).reshape(-1)
+    K = np.ascontiguousarray(K, dtype=np.uint64)
+    r = np.zeros(1, np.int32)
+    i = int(_load().orc_descend_quad(_p(g), _p(nd), _p(sp), _p(ch), _p(K), int(M), int(u), _p(r)))
+    return i, int(r[0])
 
 
 class Structure:

@@ -32,6 +32,9 @@
 //       of a grid.
 //   orc_guide                            - Fig. 11 guide cells; brute force of
 //       "single interval covers the cell" on tiny inputs.
+//   orc_quad / orc_descend_quad          - the 4-ary descent equals orc_index
+//       for every u of a grid; its record count is ceil((v - 1) / 2) for v
+//       binary visits of Algorithm 2; record splits ascend in key order.
 //   orc_grad                             - central finite differences of an
 //       independent fp64 relaxed forward; n = 1 gives zero; two-bin closed form.
 
@@ -271,6 +274,66 @@ int32_t orc_descend_steps(const int32_t* guide, const int32_t* nodes,
     ++steps;
   }
   return steps;
+}
+
+// k-ary trees (the section on k-ary trees and the remark on branching factors
+// at the end of Sec. 5): a branching factor of four results from collapsing two
+// levels of a binary tree.  For node j with children a = child0(j) and
+// b = child1(j), the 4-ary record holds the three splits in key order as node
+// ids, (a, j, b), and the four grandchildren (child0(a), child1(a), child0(b),
+// child1(b)).  Reading: a child that is a leaf has no split of its own, so its
+// side repeats the split of j and names the leaf in both of its slots; the
+// second comparison on that side then always picks the leaf (u < K_j holds on
+// the left, fails on the right).
+void orc_quad(const int32_t* nodes, int64_t n, int32_t* split, int32_t* child) {
+  for (int64_t j = 0; j < n; ++j) {
+    const int32_t a = nodes[2 * j + 0];
+    const int32_t b = nodes[2 * j + 1];
+    split[3 * j + 1] = (int32_t)j;
+    if (a >= 0) {
+      split[3 * j + 0] = a;
+      child[4 * j + 0] = nodes[2 * a + 0];
+      child[4 * j + 1] = nodes[2 * a + 1];
+    } else {
+      split[3 * j + 0] = (int32_t)j;
+      child[4 * j + 0] = a;
+      child[4 * j + 1] = a;
+    }
+    if (b >= 0) {
+      split[3 * j + 2] = b;
+      child[4 * j + 2] = nodes[2 * b + 0];
+      child[4 * j + 3] = nodes[2 * b + 1];
+    } else {
+      split[3 * j + 2] = (int32_t)j;
+      child[4 * j + 2] = b;
+      child[4 * j + 3] = b;
+    }
+  }
+}
+
+// Algorithm 2 over the 4-ary records: the guide entry and the decision at the
+// cell's root node as in Algorithm 2 (the root's record sits in the guide
+// entry), then one 4-ary record per two levels below it: compare with the
+// middle split, then with the split of the chosen side.  Returns the interval;
+// *records receives the number of 4-ary records read.
+int64_t orc_descend_quad(const int32_t* guide, const int32_t* nodes, const int32_t* split,
+                         const int32_t* child, const uint64_t* K, int64_t M, uint32_t u,
+                         int32_t* records) {
+  int64_t g = (int64_t)(((u128)u * (u128)M) >> 32);
+  int32_t j = guide[g];
+  int32_t r = 0;
+  if (j >= 0) j = ((uint64_t)u < K[j]) ? nodes[2 * j + 0] : nodes[2 * j + 1];
+  while (j >= 0) {
+    const int32_t* s = split + 3 * (int64_t)j;
+    const int32_t* c = child + 4 * (int64_t)j;
+    if ((uint64_t)u < K[s[1]])
+      j = ((uint64_t)u < K[s[0]]) ? c[0] : c[1];
+    else
+      j = ((uint64_t)u < K[s[2]]) ? c[2] : c[3];
+    ++r;
+  }
+  *records = r;
+  return (int64_t)(~j);
 }
 
 // Whole build of one distribution: scale, quantise, CDF, keys, forest, guide.

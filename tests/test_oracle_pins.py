@@ -438,6 +438,59 @@ def test_descent_depth_bound_power_of_two_cells():
 
 
 # ----------------------------------------------------------------------------
+# 4-ary records (two binary levels collapsed)
+# ----------------------------------------------------------------------------
+
+def test_quad_descent_equals_inverse_cdf_everywhere():
+    """The 4-ary descent finds the interval of the definition P_{i-1} <= xi < P_i
+    at every grid point and at every key and key - 1 (deep single-cell trees
+    included: M = 1)."""
+    for w, M, st in forest_cases(21, 150, nmax=120):
+        K, _ = o.keys(st.C, M)
+        split, child = o.quad(st.nodes)
+        us = grid_samples(8, extra=[int(x) for x in K[1:-1] if int(x) < TWO32] +
+                          [int(x) - 1 for x in K[1:-1] if 0 < int(x) <= TWO32] +
+                          [TWO32 - 1])
+        for u in us:
+            i, _ = o.descend_quad(st.guide, st.nodes, split, child, K, M, u)
+            assert i == o.index(st.C, u), (w.tolist(), M, u)
+
+
+def test_quad_records_halve_the_binary_visits():
+    """Below the root decision, a path of v - 1 binary node visits reads
+    ceil((v - 1) / 2) 4-ary records (v = visits of Algorithm 2, root included)."""
+    rng = np.random.default_rng(22)
+    for w, M, st in forest_cases(22, 120, nmax=300):
+        K, _ = o.keys(st.C, M)
+        split, child = o.quad(st.nodes)
+        for u in rng.integers(0, TWO32, 200, dtype=np.uint64):
+            v = o.descend_steps(st.guide, st.nodes, K, M, int(u))
+            _, r = o.descend_quad(st.guide, st.nodes, split, child, K, M, int(u))
+            assert r == (0 if v == 0 else v // 2), (v, r)
+
+
+def test_quad_record_splits_in_key_order():
+    """The three splits of a record are the left child, the node and the right
+    child (or the node itself for a leaf side): keys ascend, and a leaf side
+    names its leaf twice."""
+    for w, M, st in forest_cases(23, 100, nmax=200):
+        K, _ = o.keys(st.C, M)
+        split, child = o.quad(st.nodes)
+        for j in range(st.n):
+            a, b = st.nodes[j]
+            assert split[j, 1] == j
+            assert K[split[j, 0]] <= K[j] <= K[split[j, 2]]
+            if a < 0:
+                assert split[j, 0] == j and child[j, 0] == child[j, 1] == a
+            else:
+                assert split[j, 0] == a and tuple(child[j, :2]) == tuple(st.nodes[a])
+            if b < 0:
+                assert split[j, 2] == j and child[j, 2] == child[j, 3] == b
+            else:
+                assert split[j, 2] == b and tuple(child[j, 2:]) == tuple(st.nodes[b])
+
+
+# ----------------------------------------------------------------------------
 # batched and 2-D
 # ----------------------------------------------------------------------------
 
