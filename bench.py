@@ -651,41 +651,60 @@ def extra_backward(dev, reps=5):
 
 def extra_methods(dev, reps=5):
     """The radix forest against the paper's comparator, the cutpoint method
-    with binary search, on the same structure: the load statistics of
+    with binary search, and against 4-ary records (two levels collapsed, the
+    section on k-ary trees), all on the same structure: the load statistics of
     Table 1 (maximum, average, average over groups of 32 of the group maximum)
     for its four densities at n = 1024 with 2^10 cells and 2^20 i.i.d.
-    samples, and both methods timed at n = 2^24, 2^20 cells on 2^26 i.i.d. and
-    2^26 sorted samples (bins and positions are identical)."""
+    samples, and the three methods timed at n = 2^24, 2^20 cells on 2^26 i.i.d.
+    and 2^26 sorted samples (bins and positions are identical)."""
     import torch
     from paper_1901_05423_gb300 import api
     from paper_1901_05423_gb300 import workloads as W
     methods = (("radix_forest", api.SAMPLE_1D), ("binary_search", api.SAMPLE_1D | api.SAMPLE_BSEARCH))
+
+    def loads_of(f, quad, u):
+        out = {name: api.load_statistics(api.rtf_sample_loads(f, u, mode=mode))
+               for name, mode in methods}
+        lq = torch.empty(u.numel(), dtype=torch.int32, device=dev)
+        api.rtf_sample_quad(f, quad, u, loads_out=lq)
+        out["quad_records"] = api.load_statistics(lq)
+        return out
+
     table = {}
     u = api.u32_tensor(W.iid_u32(1 << 20, seed=5), dev)
     for kind in W.TABLE1_KINDS:
         f = api.rtf_build(torch.from_numpy(W.table1_weights(kind)).to(dev), 10)
-        table[kind] = {name: api.load_statistics(api.rtf_sample_loads(f, u, mode=mode))
-                       for name, mode in methods}
+        table[kind] = loads_of(f, api.rtf_build_quad(f), u)
         f.check_status()
     w = torch.from_numpy(W.lognormal_weights(N_W, seed=0, sigma=2.0)).to(dev)
     f = api.rtf_build(w, M_BITS)
-    main_loads = {name: api.load_statistics(api.rtf_sample_loads(f, u, mode=mode))
-                  for name, mode in methods}
+    quad = api.rtf_build_quad(f)
+    main_loads = loads_of(f, quad, u)
+    a, b = _events()
+    a.record()
+    for _ in range(reps):
+        api.rtf_build_quad(f, quad)
+    b.record()
+    torch.cuda.synchronize()
+    times = {"build_quad_ms": a.elapsed_time(b) / reps}
     ns = 1 << 26
-    times = {}
     for set_name, uh in (("iid", W.iid_u32(ns, seed=6)), ("sorted", W.sorted_radical_inverse_u32(ns))):
         ud = api.u32_tensor(uh, dev)
         idx = torch.empty(ns, dtype=torch.int32, device=dev)
         pos = torch.empty(ns, dtype=torch.float32, device=dev)
         hint = api.SAMPLE_COHERENT if set_name == "sorted" else 0
-        for name, mode0 in methods:
-            mode = mode0 | hint
-            api.rtf_sample(f, ud, mode=mode, idx_out=idx, pos_out=pos)
+        runs = [(name, lambda mode=mode0 | hint: api.rtf_sample(f, ud, mode=mode, idx_out=idx,
+                                                                 pos_out=pos))
+                for name, mode0 in methods]
+        runs.append(("quad_records", lambda: api.rtf_sample_quad(f, quad, ud, mode=api.SAMPLE_1D | hint,
+                                                                 idx_out=idx, pos_out=pos)))
+        for name, run in runs:
+            run()
             torch.cuda.synchronize()
             a, b = _events()
             a.record()
             for _ in range(reps):
-                api.rtf_sample(f, ud, mode=mode, idx_out=idx, pos_out=pos)
+                run()
             b.record()
             torch.cuda.synchronize()
             times[f"{set_name}_{name}_ms"] = a.elapsed_time(b) / reps

@@ -324,6 +324,52 @@ rtf_status rtf_sample_loads(const rtf_forest *f, const uint32_t *u,
                             const int32_t *dist_id, int64_t count, int32_t mode,
                             int32_t *loads_out, void *stream);
 
+/*
+ * 4-ary record, 32 bytes (one L2 sector), in device memory: two levels of a
+ * radix tree collapsed into one (the section on k-ary trees; the closing
+ * remark on branching factors of Sec. 5).  Record j belongs to node j of the
+ * same distribution; with a = child[0] and b = child[1] of node j:
+ *
+ *   cdf[0..2]  the three splits in order: C_a, C_j, C_b.  A side whose child is
+ *              a leaf has no split of its own and repeats C_j.
+ *   ref[0..3]  the four grandchildren child[0](a), child[1](a), child[0](b),
+ *              child[1](b) (a leaf side names its leaf twice), each relative
+ *              to j: 2 (k - j) for node k, 2 (i - j) + 1 for leaf (bin) i.
+ *
+ * A descent compares t with cdf[1], then with cdf[0] or cdf[2], and moves to
+ * ref[0..3]: one load per two levels.  When a reference does not fit in
+ * 16 bits (trees over more than 2^14 bins), bit RTF_QUAD_FAR of cdf[1] is set
+ * and the descent takes one binary step through the node record instead.
+ */
+typedef struct rtf_quad_rec {
+  uint64_t cdf[3];
+  int16_t ref[4];
+} rtf_quad_rec;
+
+#define RTF_QUAD_FAR 0x8000000000000000ull
+
+/*
+ * Writes the 4-ary records of a built forest: quad must hold f->num_elems
+ * records (32 bytes each, 32-byte aligned, device memory).  Stream-ordered
+ * after the build that filled f; one thread per node.
+ */
+rtf_status rtf_build_quad(const rtf_forest *f, rtf_quad_rec *quad, void *stream);
+
+/*
+ * rtf_sample through the 4-ary records written by rtf_build_quad: the guide
+ * record takes the decision of the cell's root, then each record two levels.
+ * Same arguments, modes (RTF_SAMPLE_1D with or without dist_id, RTF_SAMPLE_2D;
+ * RTF_SAMPLE_COHERENT is accepted as a hint, RTF_SAMPLE_BSEARCH is not) and
+ * results as rtf_sample: the same bins and bit-identical positions.  When
+ * loads_out (int32[count], or int32[2 count] in 2-D) is not NULL it receives
+ * the structure loads of each sample (guide records plus 4-ary and node
+ * records; -1 where no interval was found).
+ */
+rtf_status rtf_sample_quad(const rtf_forest *f, const rtf_quad_rec *quad,
+                           const uint32_t *u, const int32_t *dist_id, int64_t count,
+                           int32_t mode, int32_t *idx_out, float *pos_out,
+                           int32_t *loads_out, void *stream);
+
 /* Bytes of workspace rtf_sample_backward needs. */
 size_t rtf_backward_workspace_size(int64_t num_elems, int32_t num_dists);
 

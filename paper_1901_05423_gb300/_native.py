@@ -21,7 +21,8 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _OUT_DIR = os.path.join(_PKG, "_lib")
 LIB_PATH = os.path.join(_OUT_DIR, "librtf.so")
-SOURCES = ["build.cu", "sample.cu", "backward.cu", "api.cu", "static_ws.cu", "pipeline.cu"]
+SOURCES = ["build.cu", "sample.cu", "backward.cu", "api.cu", "static_ws.cu", "pipeline.cu",
+           "quad.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -123,6 +124,12 @@ EXPORTS = {
     "rtf_sample_loads": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "rtf_build_quad": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "rtf_sample_quad": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "rtf_backward_begin": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                           ctypes.c_size_t, ctypes.c_void_p]),
     "rtf_backward_accumulate": (ctypes.c_int, [ctypes.POINTER(RtfForestC)] + [ctypes.c_void_p] * 4

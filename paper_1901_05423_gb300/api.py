@@ -28,6 +28,8 @@ SAMPLE_BSEARCH = 0x100  # flag: cutpoint method + binary search instead of the f
 SAMPLE_COHERENT = 0x200  # hint: neighbouring samples are close (sorted / low-discrepancy order)
 NODE_BYTES = 16
 GUIDE_REC_BYTES = 32
+QUAD_REC_BYTES = 32
+QUAD_FAR = 1 << 63  # bit of a 4-ary record's middle split: references too far for 16 bits
 DIST_BYTES = 64
 
 _workspaces: dict = {}
@@ -280,6 +282,49 @@ def rtf_sample_loads(forest: Forest, u: torch.Tensor, dist_id: torch.Tensor | No
     _check(lib.rtf_sample_loads(ctypes.byref(cf), _ptr(u), _ptr(dist_id), count, mode,
                                 _ptr(loads), _stream_ptr(u.device)), "rtf_sample_loads")
     return loads
+
+
+def rtf_build_quad(forest: Forest, quad: torch.Tensor | None = None) -> torch.Tensor:
+    """4-ary records of a built forest (``rtf_build_quad``): int64 [N, 4] per
+    node j, {C_a, C_j (| QUAD_FAR), C_b, four 16-bit grandchild references}."""
+    dev = forest.nodes.device
+    if quad is None:
+        quad = torch.empty((forest.num_elems, 4), dtype=torch.int64, device=dev)
+    elif quad.shape != (forest.num_elems, 4) or quad.dtype != torch.int64:
+        raise RtfError("quad must be int64 [num_elems, 4]")
+    lib = _native.load()
+    cf = forest.c_struct()
+    _check(lib.rtf_build_quad(ctypes.byref(cf), _ptr(quad), _stream_ptr(dev)), "rtf_build_quad")
+    return quad
+
+
+def rtf_sample_quad(forest: Forest, quad: torch.Tensor, u: torch.Tensor,
+                    dist_id: torch.Tensor | None = None, mode: int = SAMPLE_1D,
+                    idx_out: torch.Tensor | None = None, pos_out: torch.Tensor | None = None,
+                    loads_out: torch.Tensor | None = None):
+    """rtf_sample through the 4-ary records (``rtf_sample_quad``); loads_out
+    (int32, one per output) receives the structure loads of each sample."""
+    if u.dtype not in (torch.int32, torch.uint32):
+        raise RtfError("u must hold 32-bit samples (int32 or uint32 tensor)")
+    _need(u, u.dtype, "u")
+    _need(quad, torch.int64, "quad")
+    if dist_id is not None:
+        _need(dist_id, torch.int32, "dist_id")
+    two_d = (mode & 0xFF) == SAMPLE_2D
+    count = u.numel() // (2 if two_d else 1)
+    shape = (count, 2) if two_d else (count,)
+    if idx_out is None:
+        idx_out = torch.empty(shape, dtype=torch.int32, device=u.device)
+    if pos_out is None:
+        pos_out = torch.empty(shape, dtype=torch.float32, device=u.device)
+    if loads_out is not None:
+        _need(loads_out, torch.int32, "loads_out")
+    lib = _native.load()
+    cf = forest.c_struct()
+    _check(lib.rtf_sample_quad(ctypes.byref(cf), _ptr(quad), _ptr(u), _ptr(dist_id), count, mode,
+                               _ptr(idx_out), _ptr(pos_out), _ptr(loads_out),
+                               _stream_ptr(u.device)), "rtf_sample_quad")
+    return idx_out, pos_out
 
 
 def load_statistics(loads, group: int = 32) -> dict:

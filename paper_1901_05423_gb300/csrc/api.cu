@@ -23,6 +23,10 @@ cudaError_t launch_sample_pipelined(const rtf_forest* f, const uint32_t* u_host,
 cudaError_t launch_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
                                 int64_t count, int mode, int32_t* loads_out, cudaStream_t st);
 size_t backward_ws_bytes(int64_t N, int32_t D);
+cudaError_t launch_build_quad(const rtf_forest* f, rtf_quad_rec* quad, cudaStream_t st);
+cudaError_t launch_sample_quad(const rtf_forest* f, const rtf_quad_rec* quad, const uint32_t* u,
+                               const int32_t* dist_id, int64_t count, int mode, int32_t* idx_out,
+                               float* pos_out, int32_t* loads_out, cudaStream_t st);
 cudaError_t launch_backward_begin(const rtf_forest* f, void* ws, cudaStream_t st);
 cudaError_t launch_backward_accumulate(const rtf_forest* f, const int32_t* dist_id,
                                        const int32_t* idx, const float* pos, const float* gpos,
@@ -157,6 +161,31 @@ rtf_status rtf_sample_loads(const rtf_forest* f, const uint32_t* u, const int32_
   if (dist_id && !aligned(dist_id, 4)) return RTF_EINVAL;
   return cuda_status(rtf::launch_sample_loads(f, u, dist_id, count, mode, loads_out,
                                               static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_build_quad(const rtf_forest* f, rtf_quad_rec* quad, void* stream) {
+  if (!forest_ok(f) || !quad || !aligned(quad, 32)) return RTF_EINVAL;
+  return cuda_status(rtf::launch_build_quad(f, quad, static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_sample_quad(const rtf_forest* f, const rtf_quad_rec* quad, const uint32_t* u,
+                           const int32_t* dist_id, int64_t count, int32_t mode, int32_t* idx_out,
+                           float* pos_out, int32_t* loads_out, void* stream) {
+  if (!forest_ok(f) || !quad || !aligned(quad, 32) || count < 0) return RTF_EINVAL;
+  if (mode & ~(0xFF | RTF_SAMPLE_COHERENT)) return RTF_EINVAL;
+  const int32_t base = mode & 0xFF;
+  if (base == RTF_SAMPLE_2D) {
+    if (!(f->flags & RTF_FOREST_MARGINAL) || dist_id) return RTF_EINVAL;
+  } else if (base != RTF_SAMPLE_1D) {
+    return RTF_EINVAL;
+  }
+  if (count == 0) return RTF_OK;
+  if (!u || !idx_out || !pos_out) return RTF_EINVAL;
+  if (!aligned(u, 16) || !aligned(idx_out, 16) || !aligned(pos_out, 16)) return RTF_EINVAL;
+  if (dist_id && !aligned(dist_id, 4)) return RTF_EINVAL;
+  if (loads_out && !aligned(loads_out, 8)) return RTF_EINVAL;
+  return cuda_status(rtf::launch_sample_quad(f, quad, u, dist_id, count, mode, idx_out, pos_out,
+                                             loads_out, static_cast<cudaStream_t>(stream)));
 }
 
 size_t rtf_backward_workspace_size(int64_t num_elems, int32_t num_dists) {

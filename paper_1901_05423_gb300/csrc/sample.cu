@@ -21,10 +21,10 @@
 #include <cstdint>
 
 #include "rtf_device.cuh"
+#include "sample_common.cuh"
 
 namespace rtf {
 
-constexpr int kSampleThreads = 256;
 constexpr int kSmemGuideMaxBits = 10;  // 32 KB of guide records in shared memory
 
 // Tunables of the single-distribution sampler (compile-time): samples per
@@ -49,110 +49,6 @@ constexpr int kSmemGuideMaxBits = 10;  // 32 KB of guide records in shared memor
 #ifndef RTF_SAMPLE_BLOCKS_PER_SM_BIG
 #define RTF_SAMPLE_BLOCKS_PER_SM_BIG 3
 #endif
-#ifndef RTF_NODE_PREFETCH
-#define RTF_NODE_PREFETCH 0
-#endif
-
-__device__ __forceinline__ uint64_t l2_evict_last_policy() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-
-__device__ __forceinline__ void load_node(const rtf_node* p, uint64_t pol, uint64_t& cdf,
-                                          int32_t& c0, int32_t& c1) {
-  uint64_t a, b;
-#if RTF_NODE_PREFETCH == 2
-  asm("ld.global.L2::cache_hint.L2::256B.v2.u64 {%0, %1}, [%2], %3;"
-      : "=l"(a), "=l"(b)
-      : "l"(p), "l"(pol));
-#elif RTF_NODE_PREFETCH == 1
-  asm("ld.global.L2::cache_hint.L2::128B.v2.u64 {%0, %1}, [%2], %3;"
-      : "=l"(a), "=l"(b)
-      : "l"(p), "l"(pol));
-#else
-  asm("ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
-      : "=l"(a), "=l"(b)
-      : "l"(p), "l"(pol));
-#endif
-  cdf = a;
-  c0 = (int32_t)(uint32_t)(b & 0xffffffffull);
-  c1 = (int32_t)(uint32_t)(b >> 32);
-}
-
-__device__ __forceinline__ void load_guide(const rtf_guide_rec* p, uint64_t pol, uint64_t& cdf,
-                                           int32_t& c0, int32_t& c1, uint64_t& lo,
-                                           uint64_t& hi) {
-  uint64_t b;
-  asm("ld.global.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], %5;"
-      : "=l"(cdf), "=l"(b), "=l"(lo), "=l"(hi)
-      : "l"(p), "l"(pol));
-  c0 = (int32_t)(uint32_t)(b & 0xffffffffull);
-  c1 = (int32_t)(uint32_t)(b >> 32);
-}
-
-__device__ __forceinline__ uint64_t load_cdf(const rtf_node* p, uint64_t pol) {
-  uint64_t a;
-  asm("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(a) : "l"(p), "l"(pol));
-  return a;
-}
-
-__device__ __forceinline__ int32_t load_child0(const rtf_guide_rec* p, uint64_t pol) {
-  int32_t a;
-  asm("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(a) : "l"(&p->child[0]), "l"(pol));
-  return a;
-}
-
-// t = floor(u T / 2^32) and r = (u T) mod 2^32 from two 32 x 32 -> 64 products
-// (T < 2^62, so u T_hi + floor(u T_lo / 2^32) cannot overflow).
-__device__ __forceinline__ void scale_sample(uint32_t u, uint64_t T, uint64_t& t, uint32_t& r) {
-  const uint64_t lo = (uint64_t)(uint32_t)T * u;
-  t = (uint64_t)(uint32_t)(T >> 32) * u + (lo >> 32);
-  r = (uint32_t)lo;
-}
-
-// In-bin position (u T - C_i 2^32) / (q 2^32) from d = t - C_i < q, the low 32
-// bits r of u T and q = C_{i+1} - C_i.  Numerator and denominator are rounded
-// to float32 once each (no fp64 pipe), the quotient is the hardware
-// reciprocal estimate refined by one fused residual step: within about 1.5 ulp
-// of the exact value.  The result is clamped below 1.
-__device__ __forceinline__ float in_bin_position(uint64_t d, uint32_t r, uint64_t q) {
-  float num, den;
-  if ((d >> 32) == 0) {
-    num = u64_to_f32((d << 32) | r);
-    den = u64_to_f32(q) * 4294967296.0f;
-  } else {
-    num = u64_to_f32(d);
-    den = u64_to_f32(q);
-  }
-  float rcp;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rcp) : "f"(den));
-  float p = num * rcp;
-  const float e = fmaf(-den, p, num);
-  p = fmaf(e, rcp, p);
-  return fminf(p, 0x1.fffffep-1f);
-}
-
-struct DistView {
-  const rtf_node* nodes;        // records of the distribution
-  const rtf_guide_rec* guide;  // its guide records
-  uint64_t T;
-  int64_t n;
-  int m;
-};
-
-__device__ __forceinline__ DistView dist_view(const rtf_dist* dists, int d, const rtf_node* nodes,
-                                              const rtf_guide_rec* guide) {
-  rtf_dist P = dists[d];
-  DistView v;
-  v.nodes = nodes + P.elem_off;
-  v.guide = guide + P.guide_off;
-  v.T = P.total;
-  v.n = P.n;
-  v.m = P.m;
-  return v;
-}
-
 // Algorithm 2 and the position for K samples of one distribution at once: the
 // K descents advance in lockstep, so each thread keeps K independent node
 // loads in flight.  Every index read from the structure is checked against n
@@ -783,28 +679,6 @@ __global__ void __launch_bounds__(kSampleThreads)
   }
 }
 
-static int g_num_sms = 0;
-static int64_t g_l2_bytes = 0;
-
-static int64_t l2_bytes() {
-  if (g_l2_bytes == 0) {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev);
-    g_l2_bytes = v > 0 ? v : (int64_t)126 << 20;
-  }
-  return g_l2_bytes;
-}
-
-static int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
-  }
-  return g_num_sms;
-}
 
 template <bool BS>
 static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,

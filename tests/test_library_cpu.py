@@ -43,6 +43,9 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header():
     from paper_1901_05423_gb300 import _native
     assert ctypes.sizeof(_native.RtfForestC) == 72
+    # rtf_quad_rec: three u64 splits and four int16 references, 32 bytes
+    text_q = open(HEADER).read()
+    assert "uint64_t cdf[3];" in text_q and "int16_t ref[4];" in text_q
     # rtf_node is 16 bytes (u64 + 2 x i32) and rtf_dist 64 bytes
     text = open(HEADER).read()
     assert "uint64_t cdf;" in text and "int32_t child[2];" in text
@@ -94,6 +97,17 @@ def test_bad_arguments_rejected_without_gpu_work(lib):
                                        P0(256), 1 << 30, None) == EINVAL  # 2-D needs a marginal
     assert lib.rtf_backward_finish(ctypes.byref(f), None, 0, P0(16), P0(256), 1 << 30,
                                    None) == EINVAL  # weights needed
+    assert lib.rtf_build_quad(ctypes.byref(f), P0(16), None) == EINVAL  # records 32-byte aligned
+    assert lib.rtf_build_quad(ctypes.byref(f), None, None) == EINVAL
+    for mode in (0x100, 0x101, 2, 0x400):  # no binary search through 4-ary records; unknown flags
+        assert lib.rtf_sample_quad(ctypes.byref(f), P0(32), P0(16), None, 8, mode, P0(16), P0(16),
+                                   None, None) == EINVAL
+    assert lib.rtf_sample_quad(ctypes.byref(f), P0(32), P0(16), None, 8, 0, P0(16), P0(16),
+                               P0(4), None) == EINVAL  # load counts 8-byte aligned
+    assert lib.rtf_sample_quad(ctypes.byref(f), P0(32), None, None, 8, 0, P0(16), P0(16),
+                               None, None) == EINVAL  # samples needed
+    assert lib.rtf_sample_quad(ctypes.byref(f), P0(32), None, None, 0, 0, None, None,
+                               None, None) == 0  # nothing to do
     P = ctypes.c_void_p
     for chunk in (0, 3, 6):  # chunks are positive multiples of 4
         assert lib.rtf_sample_pipelined(ctypes.byref(f), None, P(16), None, None, 8, 0, P(16),
