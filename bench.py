@@ -45,7 +45,7 @@ LAUNCHES_PER_STEP = 12
 # kernel changes until the capture is repeated.
 DRAM_BYTES_PER_UNIT = {
     "sample_iid": (37.956e9 + 2.143e9) / (1 << 28),
-    "sample_sorted": None,
+    "sample_sorted": (1.376e9 + 2.084e9) / (1 << 28),
     "backward": None,
     "build": None,
 }
