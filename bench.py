@@ -371,12 +371,15 @@ def gpu_arm(args):
     o_pos_s = torch.empty_like(o_pos_i).pin_memory()
     o_gw = torch.empty_like(h_w).pin_memory()
 
-    # The end-to-end step through the public API: the weights and dL/dpos go
-    # up on a side stream while the samples stream through the pipelined
-    # sampler (copies in, sampling and copies back of different chunks
-    # overlap); the step ends when every result is back in host memory.
+    # The end-to-end step through the public API: the weights go up on a side
+    # stream, the samples stream through the pipelined sampler (copies in,
+    # sampling and copies back of different chunks overlap), and dL/dpos goes
+    # up once the sample sets' inputs are in (the copies back bound the step;
+    # uploading dL/dpos beside the first sample chunks delays them: 30.5 vs
+    # 26.6 ms per step on GB300); the step ends when every result is back in
+    # host memory.
     s_up = torch.cuda.Stream(dev)
-    ev_w, ev_g = torch.cuda.Event(), torch.cuda.Event()
+    ev_w, ev_g, ev_in = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
     ev_i, ev_s = torch.cuda.Event(), torch.cuda.Event()
     chunk = 1 << 24
 
@@ -386,14 +389,17 @@ def gpu_arm(args):
         with torch.cuda.stream(s_up):
             wd.copy_(h_w, non_blocking=True)
             ev_w.record(s_up)
-            gd.copy_(h_g, non_blocking=True)
-            ev_g.record(s_up)
         cur.wait_event(ev_w)
         api.rtf_build(wd, M_BITS, forest=f)
         api.rtf_sample_pipelined(f, h_ui, ui, idx_i, pos_i, o_idx_i, o_pos_i, chunk=chunk,
                                  done_event=ev_i)
         api.rtf_sample_pipelined(f, h_us, us, idx_s, pos_s, o_idx_s, o_pos_s, chunk=chunk,
                                  done_event=ev_s, mode=SORTED_MODE)
+        ev_in.record(cur)  # both sets' inputs consumed
+        s_up.wait_event(ev_in)
+        with torch.cuda.stream(s_up):
+            gd.copy_(h_g, non_blocking=True)
+            ev_g.record(s_up)
         cur.wait_event(ev_g)
         api.rtf_sample_backward(f, wd, ui, None, idx_i, pos_i, gd, grad_w=grad_w)
         o_gw.copy_(grad_w, non_blocking=True)
