@@ -360,6 +360,29 @@ def gpu_arm(args):
     f.check_status()
     ms = max_over_ranks(total_ms / args.steps, dist, dev)
 
+    # Each part of the step alone on one stream, after the timed region (the
+    # per-kernel fractions of HBM; with two streams the spans above include
+    # the time a part waits for SMs held by the other stream).
+    def alone(fn, reps=3):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    alone_ms = {
+        "build": alone(lambda: api.rtf_build(wd, M_BITS, forest=f)),
+        "sample_iid": alone(lambda: api.rtf_sample(f, ui, idx_out=idx_i, pos_out=pos_i)),
+        "sample_sorted": alone(lambda: api.rtf_sample(f, us, mode=SORTED_MODE, idx_out=idx_s,
+                                                      pos_out=pos_s)),
+        "backward": alone(lambda: api.rtf_sample_backward(f, wd, ui, None, idx_i, pos_i, gd,
+                                                          grad_w=grad_w)),
+    }
+    f.check_status()
+
     # end-to-end through the API with host buffers (pinned), copies inside
     h_w = torch.from_numpy(w).pin_memory()
     h_ui = torch.from_numpy(u_iid.view(np.int32)).pin_memory()
@@ -454,14 +477,15 @@ def gpu_arm(args):
                                3: "3: sorted set concurrent; backward accumulated per chunk of "
                                   "the i.i.d. set while later chunks are mapped"}[args.streams]},
         "breakdown_ms": avg,
-        "build_elem_per_s": N_W / (avg["build"] * 1e-3),
-        "sample_iid_per_s": N_S / (avg["sample_iid"] * 1e-3),
-        "sample_sorted_per_s": N_S / (avg["sample_sorted"] * 1e-3),
+        "build_elem_per_s": N_W / (alone_ms["build"] * 1e-3),
+        "sample_iid_per_s": N_S / (alone_ms["sample_iid"] * 1e-3),
+        "sample_sorted_per_s": N_S / (alone_ms["sample_sorted"] * 1e-3),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "traffic_GBps": traffic / (avg[dom] * 1e-3) / 1e9 if traffic else None,
                      "peak_kind": peak_kind},
-        "fractions_of_hbm": {k: alg[k] / (avg[k] * 1e-3) / 1e9 / peak for k in avg},
+        "alone_ms": alone_ms,
+        "fractions_of_hbm": {k: alg[k] / (alone_ms[k] * 1e-3) / 1e9 / peak for k in alone_ms},
         "e2e": {"value": job_throughput(world, 2 * N_S, max_over_ranks(e2e_ms, dist, dev)),
                 "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
