@@ -361,7 +361,8 @@ rtf_status rtf_build_quad(const rtf_forest *f, rtf_quad_rec *quad, void *stream)
  * Same arguments, modes (RTF_SAMPLE_1D with or without dist_id, RTF_SAMPLE_2D;
  * RTF_SAMPLE_COHERENT is accepted as a hint, RTF_SAMPLE_BSEARCH is not) and
  * results as rtf_sample: the same bins and bit-identical positions.  When
- * loads_out (int32[count], or int32[2 count] in 2-D) is not NULL it receives
+ * loads_out (int32[count], or int32[2 count] in 2-D; 8-byte aligned) is not
+ * NULL it receives
  * the structure loads of each sample (guide records plus 4-ary and node
  * records; -1 where no interval was found).
  */
