@@ -45,7 +45,7 @@ LAUNCHES_PER_STEP = 12
 # kernel changes until the capture is repeated.
 DRAM_BYTES_PER_UNIT = {
     "sample_iid": (37.956e9 + 2.143e9) / (1 << 28),
-    "sample_sorted": (1.376e9 + 2.084e9) / (1 << 28),
+    "sample_sorted": (1.358e9 + 2.088e9) / (1 << 28),
     "backward": None,
     "build": None,
 }
@@ -147,11 +147,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs():
+def make_inputs(sorted_dense=False):
     from paper_1901_05423_gb300 import workloads as W
     w = W.lognormal_weights(N_W, seed=0, sigma=2.0)
     u_iid = W.iid_u32(N_S, seed=1)
-    u_sorted = W.sorted_radical_inverse_u32(N_S)
+    # sorted_dense: the first N_S samples of the 2^28-sample sorted set (its
+    # density, 16 u-units apart, over part of [0, 1)) instead of N_S samples
+    # spread over all of [0, 1); a profiling aid for small N_S
+    u_sorted = ((np.arange(N_S, dtype=np.uint64) * np.uint64(16)).astype(np.uint32) if sorted_dense
+                else W.sorted_radical_inverse_u32(N_S))
     gx = W.normal_f32(N_S, seed=2)
     return w, u_iid, u_sorted, gx
 
@@ -236,7 +240,7 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w, u_iid, u_sorted, gx = make_inputs()
+    w, u_iid, u_sorted, gx = make_inputs(sorted_dense=args.sorted_dense)
     wd = torch.from_numpy(w).to(dev)
     ui = api.u32_tensor(u_iid, dev)
     us = api.u32_tensor(u_sorted, dev)
@@ -469,8 +473,9 @@ def gpu_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": f"n=2^24 lognormal(0,2) weights, 2^20 guide cells, "
-                               f"2^{lg} iid + 2^{lg} sorted radical-inverse samples, "
-                               f"backward on the iid set",
+                               f"2^{lg} iid + 2^{lg} sorted radical-inverse samples"
+                               + (" (the first of the 2^28 set)" if args.sorted_dense else "")
+                               + ", backward on the iid set",
                    "l2": "inputs larger than L2", "parallelism": f"replicas{world}",
                    "streams": {1: "1", 2: "2: sorted set concurrent with the i.i.d. set and "
                                            "the backward",
@@ -758,6 +763,9 @@ def main():
                     help="2: sample the sorted set on a second stream, concurrently with the "
                          "i.i.d. set and the backward; 3: also accumulate the backward chunk by "
                          "chunk on a third stream while the i.i.d. set is mapped")
+    ap.add_argument("--sorted-dense", action="store_true",
+                    help="with --samples-log2 below 28: the sorted set at the full-size density "
+                         "(u = 16 j), a profiling aid")
     ap.add_argument("--samples-log2", type=int, default=28,
                     help="2^k samples per set; the benchmarked workload is k = 28, smaller k "
                          "gives the same structure with fewer samples (profiler captures)")

@@ -382,93 +382,215 @@ __device__ __forceinline__ bool descend_one(const DistView& v, uint32_t u, uint6
   return j < 0 && (uint32_t)i < n32 && lo <= t && t < hi;
 }
 
-// Samples that arrive in ascending order (sorted or low-discrepancy sequences,
-// the monotone mapping of Sec. 3.2) mostly fall into the bin of the sample
-// before them or into the next one.  Each thread maps a run of R consecutive
-// samples: a sample whose t lies in [C_i, C_{i+1}) of the previous sample's
-// bin i takes bin i; one with t >= C_{i+1} steps forward over at most
-// kRunSteps bins (bin i + 1 is [C_{i+1}, C_{i+2}), one CDF load each;
-// zero-width bins are passed over); any other sample, and the first of every
-// run, descends from its guide record (Algorithm 2).  Each way yields the
-// unique bin with C_i <= t < C_{i+1} and its two bounds, so indices and
-// positions are the bits of sample_group for every input order; the order only
-// decides the speed.  The kernel is bound by the latency of the loads of the
-// lanes that step or descend while the others wait; short runs keep the
-// registers low enough for five resident blocks per SM (GB300, 2^28 sorted
-// samples at n = 2^24: 1.04 ms with runs of 8, 1.17 ms with runs of 16 at four
-// blocks per SM, 1.37 ms with runs of 4; 1.93 ms for the per-sample descent).
-#ifndef RTF_RUN_SAMPLES
-#define RTF_RUN_SAMPLES 8
+constexpr int kRunSteps = 4;  // forward steps through the CDF in global memory
+
+// Coherent samples (RTF_SAMPLE_COHERENT): samples that arrive in ascending
+// order (sorted or low-discrepancy sequences, the monotone mapping of Sec. 3.2)
+// mostly fall into the bin of the sample before them or into one of the next
+// few.  A warp maps a contiguous stretch of the samples in batches of 32 R
+// (lane l takes samples [R l, R l + R) of the batch, in order) and keeps, in
+// shared memory, a window of 64 bin bounds W_j = C_{c+1+j} (T for the last bin,
+// all ones past it) from bin c on, c being the bin of the last sample the warp
+// mapped.  A lane places its first sample of a batch by a binary search of the
+// window (a sample outside it descends from its guide record, Algorithm 2),
+// then walks its run: a sample in the current bin [C_i, C_{i+1}) keeps it, one
+// above steps forward through the window (past its end through the CDF in
+// global memory, at most kRunSteps bins), anything else descends.  Each way
+// yields the unique bin with C_i <= t < C_{i+1} and its bounds, the bits of
+// Algorithm 2, whatever the input order; the order only decides the speed.
+// After a batch the window restarts at the bin of the batch's last sample once
+// that bin has moved 32 or more bins past c.  GB300, 2^28 sorted samples at
+// n = 2^24: 0.91 ms with runs of 8 (runs of 4: 0.92 ms; of 16: 1.39 ms, the
+// lanes' loads no longer coalesce); runs without the window, stepping and
+// descending through global memory: 1.06 ms; a warp-wide window searched by
+// shuffles for every sample: 1.34-1.44 ms; one descent per sample: 1.93 ms.
+#ifndef RTF_WRUN_SAMPLES
+#define RTF_WRUN_SAMPLES 8
 #endif
-#ifndef RTF_RUN_MINB
-#define RTF_RUN_MINB 5
+#ifndef RTF_WRUN_MINB
+#define RTF_WRUN_MINB 0
 #endif
-constexpr int kRunSamples = RTF_RUN_SAMPLES;
-constexpr int kRunSteps = 4;
+constexpr int kWinBounds = 64;
+
+__device__ __forceinline__ void window_fill(uint64_t* win, const DistView& v, int64_t c, int lane,
+                                            uint64_t pol) {
+#pragma unroll
+  for (int h = 0; h < kWinBounds / 32; ++h) {
+    const int64_t k = c + 1 + lane + 32 * h;
+    win[lane + 32 * h] = k < v.n ? load_cdf(v.nodes + k, pol) : (k == v.n ? v.T : ~0ull);
+  }
+  __syncwarp();
+}
+
+// The in-bin position of Sec. 5 with the bin's constants computed once per
+// bin: the same operations as in_bin_position (numerator and denominator
+// rounded once each, hardware reciprocal refined by one fused residual step),
+// so the same bits.  q = 0 marks "no bin": no t satisfies t - lo < q.
+struct BinPos {
+  uint64_t lo, q;
+  float den_a, rcp_a;  // t - lo < 2^32: numerator (t - lo) 2^32 + r, denominator q 2^32
+  float den_b, rcp_b;  // otherwise: numerator t - lo, denominator q
+  __device__ __forceinline__ void set(uint64_t l, uint64_t h) {
+    lo = l;
+    q = h - l;
+    den_b = u64_to_f32(q);
+    den_a = den_b * 4294967296.0f;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rcp_a) : "f"(den_a));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rcp_b) : "f"(den_b));
+  }
+  __device__ __forceinline__ float pos(uint64_t d, uint32_t r) const {
+    const bool small = (d >> 32) == 0;
+    const float num = small ? u64_to_f32((d << 32) | r) : u64_to_f32(d);
+    const float den = small ? den_a : den_b;
+    const float rcp = small ? rcp_a : rcp_b;
+    float p = num * rcp;
+    const float e = fmaf(-den, p, num);
+    p = fmaf(e, rcp, p);
+    return fminf(p, 0x1.fffffep-1f);
+  }
+};
 
 template <int R>
-__global__ void __launch_bounds__(kSampleThreads, RTF_RUN_MINB)
-    sample_runs_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
+__global__ void __launch_bounds__(kSampleThreads, RTF_WRUN_MINB)
+    sample_wrun_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                        const rtf_dist* __restrict__ dists, const uint32_t* __restrict__ u,
                        int64_t count, int32_t* __restrict__ idx_out,
                        float* __restrict__ pos_out) {
-  static_assert(R % 4 == 0 && R >= 4, "runs move as 16-byte vectors");
+  static_assert(R % 4 == 0, "runs move as 16-byte vectors");
   constexpr int V = R / 4;
+  __shared__ uint64_t wins[kSampleThreads / 32][kWinBounds];
   const DistView v = dist_view(dists, 0, nodes, guide);
   const uint64_t pol = l2_evict_last_policy();
+  const int lane = threadIdx.x & 31;
+  uint64_t* win = wins[threadIdx.x >> 5];
   const int64_t n = v.n;
-  const int64_t runs = count / R;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t batches = count / (32 * R);
+  const int64_t per = (batches + nwarps - 1) / nwarps;
+  const int64_t b0 = warp * per;
+  const int64_t b1 = min(b0 + per, batches);
   const uint4* u4 = reinterpret_cast<const uint4*>(u);
   int4* i4 = reinterpret_cast<int4*>(idx_out);
   float4* p4 = reinterpret_cast<float4*>(pos_out);
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = gtid; q < runs; q += stride) {
+  int64_t c = -1;   // window start (warp-uniform); -1: no window
+  uint64_t Cc = 0;  // C_c
+  for (int64_t b = b0; b < b1; ++b) {
+    const int64_t q0 = b * 32 + lane;  // this lane's run
     uint32_t uu[R];
 #pragma unroll
-    for (int c = 0; c < V; ++c) {
-      const uint4 x = __ldcs(u4 + q * V + c);
-      uu[4 * c] = x.x;
-      uu[4 * c + 1] = x.y;
-      uu[4 * c + 2] = x.z;
-      uu[4 * c + 3] = x.w;
+    for (int k = 0; k < V; ++k) {
+      const uint4 x = __ldcs(u4 + q0 * V + k);
+      uu[4 * k] = x.x;
+      uu[4 * k + 1] = x.y;
+      uu[4 * k + 2] = x.z;
+      uu[4 * k + 3] = x.w;
+    }
+
+    if (c < 0) {
+      // no window: start it at the bin of the batch's first sample
+      uint64_t t0;
+      uint32_t r0;
+      scale_sample(uu[0], v.T, t0, r0);
+      int32_t i0 = -1;
+      uint64_t l0 = 0, h0 = 0;
+      bool ok0 = false;
+      if (lane == 0) ok0 = descend_one(v, uu[0], t0, pol, i0, l0, h0);
+      const int32_t cb = __shfl_sync(0xffffffffu, ok0 ? i0 : -1, 0);
+      const uint64_t cl = __shfl_sync(0xffffffffu, (unsigned long long)l0, 0);
+      if (cb >= 0) {
+        c = cb;
+        Cc = cl;
+        window_fill(win, v, c, lane, pol);
+      }
+    }
+    // the lane's first sample: a binary search of the window
+    int32_t cur = -1;
+    int p = -1;  // window slot of the bin's upper bound (W_p = C_{cur+1}), -1: not from the window
+    BinPos bp;
+    bp.lo = 0;
+    bp.q = 0;
+    {
+      uint64_t t0;
+      uint32_t r0;
+      scale_sample(uu[0], v.T, t0, r0);
+      if (c >= 0 && t0 >= Cc && t0 < win[kWinBounds - 1]) {
+        int cnt = 0;
+#pragma unroll
+        for (int step = kWinBounds / 2; step >= 1; step >>= 1)
+          if (win[cnt + step - 1] <= t0) cnt += step;
+        cur = (int32_t)(c + cnt);
+        bp.set(cnt > 0 ? win[cnt - 1] : Cc, win[cnt]);
+        p = cnt;
+      }
     }
     int32_t ii[R];
     float pp[R];
-    int32_t cur = -1;  // bin of the previous sample, -1 before the first
-    uint64_t lo = 0, hi = 0;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       uint64_t t;
       uint32_t r;
       scale_sample(uu[k], v.T, t, r);
-      bool ok = cur >= 0 && lo <= t && t < hi;
-      if (!ok && cur >= 0 && t >= hi) {
-        for (int s = 0; s < kRunSteps && cur + 2 <= n; ++s) {
-          const uint64_t c2 = cur + 2 < n ? load_cdf(v.nodes + cur + 2, pol) : v.T;
-          ++cur;
-          lo = hi;
-          hi = c2;
-          if (t < hi) {
-            ok = true;
-            break;
+      uint64_t d = t - bp.lo;
+      if (d >= bp.q) {  // not in the current bin (or no bin)
+        bool ok = false;
+        if (cur >= 0 && t >= bp.lo + bp.q) {
+          uint64_t lo = bp.lo + bp.q;  // C_{cur+1}
+          for (int st = 0; st < kWinBounds + kRunSteps && cur + 2 <= n; ++st) {
+            uint64_t c2;
+            if (p >= 0 && p + 1 < kWinBounds) {
+              c2 = win[++p];
+            } else {
+              if (st >= kRunSteps) break;
+              p = -1;
+              c2 = cur + 2 < n ? load_cdf(v.nodes + cur + 2, pol) : v.T;
+            }
+            ++cur;
+            if (t < c2) {
+              bp.set(lo, c2);
+              ok = true;
+              break;
+            }
+            lo = c2;
           }
         }
+        if (!ok) {
+          uint64_t lo, hi;
+          ok = descend_one(v, uu[k], t, pol, cur, lo, hi);
+          p = -1;
+          if (ok) {
+            bp.set(lo, hi);
+          } else {
+            cur = -1;
+            bp.lo = 0;
+            bp.q = 0;
+          }
+        }
+        d = t - bp.lo;
       }
-      if (!ok) {
-        ok = descend_one(v, uu[k], t, pol, cur, lo, hi);
-        if (!ok) cur = -1;
-      }
-      ii[k] = ok ? cur : -1;
-      pp[k] = ok ? in_bin_position(t - lo, r, hi - lo) : 0.0f;
+      ii[k] = cur;
+      pp[k] = cur >= 0 ? bp.pos(d, r) : 0.0f;
     }
 #pragma unroll
-    for (int c = 0; c < V; ++c) {
-      __stcs(i4 + q * V + c, make_int4(ii[4 * c], ii[4 * c + 1], ii[4 * c + 2], ii[4 * c + 3]));
-      __stcs(p4 + q * V + c, make_float4(pp[4 * c], pp[4 * c + 1], pp[4 * c + 2], pp[4 * c + 3]));
+    for (int k = 0; k < V; ++k) {
+      __stcs(i4 + q0 * V + k, make_int4(ii[4 * k], ii[4 * k + 1], ii[4 * k + 2], ii[4 * k + 3]));
+      __stcs(p4 + q0 * V + k, make_float4(pp[4 * k], pp[4 * k + 1], pp[4 * k + 2], pp[4 * k + 3]));
+    }
+    // restart the window at the bin of the batch's last sample once it ran ahead
+    const int32_t cl = __shfl_sync(0xffffffffu, cur, 31);
+    const uint64_t ll = __shfl_sync(0xffffffffu, (unsigned long long)bp.lo, 31);
+    __syncwarp();
+    if (cl < 0) {
+      c = -1;
+    } else if (c < 0 || cl < c || cl - c >= kWinBounds / 2) {
+      c = cl;
+      Cc = ll;
+      window_fill(win, v, c, lane, pol);
     }
   }
-  for (int64_t s = runs * R + gtid; s < count; s += stride) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = batches * 32 * R + gtid; s < count; s += stride) {
     int32_t ii;
     float pp;
     sample_one<false, false>(v, nullptr, u[s], pol, ii, pp);
@@ -701,19 +823,19 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
     return;
   }
   if (coherent && !BS) {
-    // one wave of resident blocks (grid-stride over the runs)
+    // one wave of resident blocks; each warp maps a contiguous stretch
     static int resident = 0;
     if (resident == 0) {
-      int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sample_runs_kernel<kRunSamples>,
-                                                        kSampleThreads, 0) != cudaSuccess ||
-          b <= 0)
-        b = RTF_RUN_MINB;
-      resident = b;
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &nb, sample_wrun_kernel<RTF_WRUN_SAMPLES>, kSampleThreads, 0) != cudaSuccess ||
+          nb <= 0)
+        nb = 4;
+      resident = nb;
     }
-    const int64_t per = (int64_t)kSampleThreads * kRunSamples;
+    const int64_t per = (int64_t)kSampleThreads * RTF_WRUN_SAMPLES;
     const int64_t blocks = min((int64_t)sms * resident, (count + per - 1) / per);
-    sample_runs_kernel<kRunSamples><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
+    sample_wrun_kernel<RTF_WRUN_SAMPLES><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
         f->nodes, f->guide_recs, f->dists, u, count, idx_out, pos_out);
     return;
   }

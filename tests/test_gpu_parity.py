@@ -638,10 +638,10 @@ def test_coherent_hint_changes_nothing_but_the_grid(big):
 
 @pytest.mark.parametrize("m", [0, 4, 14])
 def test_coherent_runs_match_oracle_all_weight_kinds(m):
-    """The run sampler (RTF_SAMPLE_COHERENT): a sample in the previous
+    """The coherent sampler (RTF_SAMPLE_COHERENT): a sample in the previous
     sample's bin, a step forward over zero-width bins, a step backward and a
     jump all give the oracle's bin and position.  Counts leave a ragged tail
-    (not a multiple of the 16-sample run)."""
+    (not a multiple of the 256-sample batch of a warp)."""
     rng = np.random.default_rng(50 + m)
     for n, kind, w in weight_cases():
         f = api.rtf_build(to_dev(w), m)
@@ -676,3 +676,39 @@ def test_coherent_runs_tiny_counts():
         idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV), mode=api.SAMPLE_1D | api.SAMPLE_COHERENT)
         ridx, rpos = orc.sample(ref.C, u)
         check_samples(idx, pos, ridx, rpos)
+
+
+@pytest.mark.parametrize("kind", ["lognormal2", "zeros", "dups"])
+def test_coherent_window_orders_many_batches(kind):
+    """The coherent sampler over many batches per warp (its window carried from
+    batch to batch): sorted, descending, sorted runs of random lengths, sorted
+    with outliers, sorted and so sparse that the window slides far, one value
+    repeated.  Every sample equals the per-sample descent's."""
+    rng = np.random.default_rng({"lognormal2": 61, "zeros": 62, "dups": 63}[kind])
+    n = 1 << 20
+    if kind == "lognormal2":
+        w = np.exp(rng.normal(0, 2, n))
+    elif kind == "zeros":
+        w = rng.uniform(0, 1, n) * (rng.random(n) < 0.3)
+    else:
+        w = np.repeat(rng.uniform(0.01, 1, n // 8), 8) * (rng.random(n) < 0.8)
+    f = api.rtf_build(to_dev(w.astype(np.float32)), 16)
+    ns = 1 << 23
+    base = np.sort(rng.integers(0, 1 << 32, ns, dtype=np.uint64)).astype(np.uint32)
+    cuts = np.sort(rng.choice(np.arange(1, ns), 63, replace=False))
+    saw = np.concatenate([np.sort(c) for c in np.split(rng.integers(0, 1 << 32, ns, dtype=np.uint64)
+                                                       .astype(np.uint32), cuts)])
+    outl = base.copy()
+    outl[::1000] = rng.integers(0, 1 << 32, outl[::1000].size, dtype=np.uint64).astype(np.uint32)
+    sparse = (np.arange(ns, dtype=np.uint64) * 509).astype(np.uint32)  # wraps: sorted pieces
+    same = np.full(ns, 0x9E3779B9, np.uint32)
+    for name, u in (("sorted", base), ("descending", base[::-1].copy()), ("sawtooth", saw),
+                    ("outliers", outl), ("sparse", sparse), ("same", same)):
+        ud = api.u32_tensor(u, DEV)
+        i1, p1 = api.rtf_sample(f, ud, mode=api.SAMPLE_1D | api.SAMPLE_COHERENT)
+        i2, p2 = api.rtf_sample(f, ud)
+        torch.cuda.synchronize()
+        f.check_status()
+        assert torch.equal(i1, i2), f"{kind}/{name}: indices"
+        assert torch.equal(p1.view(torch.int32), p2.view(torch.int32)), f"{kind}/{name}: positions"
+        assert int(i1.min()) >= 0
