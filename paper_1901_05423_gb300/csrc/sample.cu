@@ -27,6 +27,19 @@ namespace rtf {
 
 constexpr int kSmemGuideMaxBits = 10;  // 32 KB of guide records in shared memory
 
+// Pairs per thread of the 2-D sampler (1: one pair at a time; 2 or 4: their
+// descents in lockstep).  GB300, 4096 x 2048 map, 2^26 pairs: 1.54 ms with 2,
+// 1.64 ms with 1, 2.36 ms with 4 (120 registers, two blocks per SM).
+#ifndef RTF_2D_PAIRS
+#define RTF_2D_PAIRS 2
+#endif
+// Samples per thread of the sampler with a distribution id per sample (their
+// descents in lockstep).  GB300, 16384 ragged distributions, 2^27 samples:
+// 5.83 ms with 4, 6.24 ms with 2.
+#ifndef RTF_TAGGED_K
+#define RTF_TAGGED_K 4
+#endif
+
 // Tunables of the single-distribution sampler (compile-time): samples per
 // thread descending in lockstep, the minimum resident blocks per SM given to
 // the register allocator (0 = none), and the L2 fetch size requested with each
@@ -704,22 +717,36 @@ __global__ void __launch_bounds__(kSampleThreads)
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if constexpr (!BS) {
     bool bad_id = false;
-    const int64_t groups = count >> 2;
-    const uint4* u4 = reinterpret_cast<const uint4*>(u);
-    int4* i4 = reinterpret_cast<int4*>(idx_out);
-    float4* p4 = reinterpret_cast<float4*>(pos_out);
+    constexpr int K = RTF_TAGGED_K;
+    static_assert(K == 2 || K == 4, "2 or 4 samples per thread");
+    const int64_t groups = count / K;
     for (int64_t q = gtid; q < groups; q += stride) {
-      const uint4 x = __ldcs(u4 + q);
-      const uint32_t uu[4] = {x.x, x.y, x.z, x.w};
-      const int32_t dd[4] = {__ldcs(dist_id + 4 * q), __ldcs(dist_id + 4 * q + 1),
-                             __ldcs(dist_id + 4 * q + 2), __ldcs(dist_id + 4 * q + 3)};
-      int32_t ii[4];
-      float pp[4];
-      sample_group_tagged<4>(nodes, guide, dists, D, uu, dd, pol, ii, pp, bad_id);
-      __stcs(i4 + q, make_int4(ii[0], ii[1], ii[2], ii[3]));
-      __stcs(p4 + q, make_float4(pp[0], pp[1], pp[2], pp[3]));
+      uint32_t uu[K];
+      int32_t dd[K], ii[K];
+      float pp[K];
+      if constexpr (K == 4) {
+        const uint4 x = __ldcs(reinterpret_cast<const uint4*>(u) + q);
+        uu[0] = x.x;
+        uu[1] = x.y;
+        uu[2] = x.z;
+        uu[3] = x.w;
+      } else {
+        const uint2 x = __ldcs(reinterpret_cast<const uint2*>(u) + q);
+        uu[0] = x.x;
+        uu[1] = x.y;
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) dd[k] = __ldcs(dist_id + K * q + k);
+      sample_group_tagged<K>(nodes, guide, dists, D, uu, dd, pol, ii, pp, bad_id);
+      if constexpr (K == 4) {
+        __stcs(reinterpret_cast<int4*>(idx_out) + q, make_int4(ii[0], ii[1], ii[2], ii[3]));
+        __stcs(reinterpret_cast<float4*>(pos_out) + q, make_float4(pp[0], pp[1], pp[2], pp[3]));
+      } else {
+        __stcs(reinterpret_cast<int2*>(idx_out) + q, make_int2(ii[0], ii[1]));
+        __stcs(reinterpret_cast<float2*>(pos_out) + q, make_float2(pp[0], pp[1]));
+      }
     }
-    for (int64_t s = 4 * groups + gtid; s < count; s += stride) {
+    for (int64_t s = K * groups + gtid; s < count; s += stride) {
       const uint32_t uu[1] = {__ldcs(u + s)};
       const int32_t dd[1] = {__ldcs(dist_id + s)};
       int32_t ii[1];
@@ -784,8 +811,44 @@ __global__ void __launch_bounds__(kSampleThreads)
                      int64_t count, int2* __restrict__ idx_out, float2* __restrict__ pos_out) {
   const uint64_t pol = l2_evict_last_policy();
   const DistView marg = dist_view(dists, D - 1, nodes, guide);
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < count;
-       s += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t done = 0;
+  if constexpr (!BS && RTF_2D_PAIRS > 1) {
+    // RTF_2D_PAIRS pairs per thread: their rows through the marginal in
+    // lockstep, then their columns in lockstep, each through its own row (a
+    // pair whose row was not found gets column -1)
+    constexpr int P = RTF_2D_PAIRS;
+    const int64_t groups = count / P;
+    const uint4* u4 = reinterpret_cast<const uint4*>(u);
+    int4* i4 = reinterpret_cast<int4*>(idx_out);
+    float4* p4 = reinterpret_cast<float4*>(pos_out);
+    for (int64_t q = gtid; q < groups; q += stride) {
+      uint32_t u1[P], u2[P];
+#pragma unroll
+      for (int h = 0; h < P / 2; ++h) {
+        const uint4 a = __ldcs(u4 + (P / 2) * q + h);
+        u1[2 * h] = a.x;
+        u2[2 * h] = a.y;
+        u1[2 * h + 1] = a.z;
+        u2[2 * h + 1] = a.w;
+      }
+      int32_t r[P], c[P], nl[P], dd[P];
+      float pr[P], pc[P];
+      sample_group<P, false>(marg, nullptr, u1, pol, r, pr, nl);
+#pragma unroll
+      for (int k = 0; k < P; ++k) dd[k] = (r[k] >= 0 && r[k] < D - 1) ? r[k] : -1;
+      bool no_row = false;
+      sample_group_tagged<P>(nodes, guide, dists, D, u2, dd, pol, c, pc, no_row);
+#pragma unroll
+      for (int h = 0; h < P / 2; ++h) {
+        __stcs(i4 + (P / 2) * q + h, make_int4(r[2 * h], c[2 * h], r[2 * h + 1], c[2 * h + 1]));
+        __stcs(p4 + (P / 2) * q + h, make_float4(pr[2 * h], pc[2 * h], pr[2 * h + 1], pc[2 * h + 1]));
+      }
+    }
+    done = P * groups;
+  }
+  for (int64_t s = done + gtid; s < count; s += stride) {
     uint2 uu = __ldcs(u + s);
     int32_t r, c;
     float pr, pc;
@@ -808,14 +871,15 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
                             float* pos_out, cudaStream_t st) {
   const int sms = num_sms();
   if (mode == RTF_SAMPLE_2D) {
-    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads - 1) / kSampleThreads);
+    const int64_t per = BS ? 1 : RTF_2D_PAIRS;  // pairs per thread and step
+    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads * per - 1) / (kSampleThreads * per));
     sample_2d_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
         f->nodes, f->guide_recs, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
         reinterpret_cast<int2*>(idx_out), reinterpret_cast<float2*>(pos_out));
     return;
   }
   if (dist_id != nullptr) {
-    const int64_t per = BS ? 1 : 4;  // samples per thread and step
+    const int64_t per = BS ? 1 : RTF_TAGGED_K;  // samples per thread and step
     int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads * per - 1) / (kSampleThreads * per));
     sample_tagged_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
         f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,

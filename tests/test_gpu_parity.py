@@ -338,6 +338,7 @@ def env_check(H, Wd, m_row, m_col, n_s, seed=0):
 
 def test_env_map_small():
     env_check(64, 128, 6, 7, 1 << 16)
+    env_check(48, 96, 5, 6, (1 << 12) + 3, seed=3)  # pairs left over after groups of four
 
 
 def test_env_map_full_config():
