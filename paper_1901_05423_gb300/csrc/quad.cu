@@ -70,12 +70,12 @@ __global__ void __launch_bounds__(kQuadThreads)
                                   ((uint64_t)(uint16_t)code[2] << 32) |
                                   ((uint64_t)(uint16_t)code[3] << 48))
                                : 0;
-    ulonglong4 rec;
+    ulonglong4_32a rec;
     rec.x = split[0];
     rec.y = nj.cdf | (near ? 0 : RTF_QUAD_FAR);
     rec.z = split[1];
     rec.w = refs;
-    *reinterpret_cast<ulonglong4*>(quad + e) = rec;
+    *reinterpret_cast<ulonglong4_32a*>(quad + e) = rec;
   }
 }
 

@@ -888,14 +888,14 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
   }
   if (coherent && !BS) {
     // one wave of resident blocks; each warp maps a contiguous stretch
-    static int resident = 0;
+    static std::atomic<int> resident_cache{0};  // same kernel and architecture on every device
+    int resident = resident_cache.load(std::memory_order_relaxed);
     if (resident == 0) {
-      int nb = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &nb, sample_wrun_kernel<RTF_WRUN_SAMPLES>, kSampleThreads, 0) != cudaSuccess ||
-          nb <= 0)
-        nb = 4;
-      resident = nb;
+              &resident, sample_wrun_kernel<RTF_WRUN_SAMPLES>, kSampleThreads, 0) != cudaSuccess ||
+          resident <= 0)
+        resident = 4;
+      resident_cache.store(resident, std::memory_order_relaxed);
     }
     const int64_t per = (int64_t)kSampleThreads * RTF_WRUN_SAMPLES;
     const int64_t blocks = min((int64_t)sms * resident, (count + per - 1) / per);

@@ -4,6 +4,7 @@
 // CDF domain and the in-bin position of Sec. 5.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 
 #include "rtf_device.cuh"
@@ -116,27 +117,32 @@ __device__ __forceinline__ DistView dist_view(const rtf_dist* dists, int d, cons
   return v;
 }
 
-// Device properties the launchers size their grids by (cached per process).
-inline int64_t l2_bytes() {
-  static int64_t v = 0;
+// Device properties the launchers size their grids by, cached per device
+// (host threads may race to fill an entry; they all store the same value).
+constexpr int kCachedDevices = 64;
+
+inline int device_attr_cached(std::atomic<int>* cache, cudaDeviceAttr attr, int fallback) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const bool cacheable = dev >= 0 && dev < kCachedDevices;
+  int v = cacheable ? cache[dev].load(std::memory_order_relaxed) : 0;
   if (v == 0) {
-    int dev = 0, b = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, dev);
-    v = b > 0 ? b : (int64_t)126 << 20;
+    int b = 0;
+    if (cudaDeviceGetAttribute(&b, attr, dev) != cudaSuccess || b <= 0) b = fallback;
+    v = b;
+    if (cacheable) cache[dev].store(v, std::memory_order_relaxed);
   }
   return v;
 }
 
+inline int64_t l2_bytes() {
+  static std::atomic<int> cache[kCachedDevices];
+  return device_attr_cached(cache, cudaDevAttrL2CacheSize, 126 << 20);
+}
+
 inline int num_sms() {
-  static int v = 0;
-  if (v == 0) {
-    int dev = 0, b = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&b, cudaDevAttrMultiProcessorCount, dev);
-    v = b > 0 ? b : 148;
-  }
-  return v;
+  static std::atomic<int> cache[kCachedDevices];
+  return device_attr_cached(cache, cudaDevAttrMultiProcessorCount, 148);
 }
 
 }  // namespace rtf
