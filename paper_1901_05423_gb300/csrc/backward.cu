@@ -422,6 +422,161 @@ __global__ void __launch_bounds__(kBwThreads)
   }
 }
 
+// One distribution (no segment ends inside the array but its last element):
+// the same reverse decoupled-lookback scan and the same per-element
+// arithmetic as suffix_kernel, with the tile scanned by warp shuffles instead
+// of a segmented shared-memory scan and the inputs read as 16-byte vectors.
+__global__ void __launch_bounds__(kBwThreads)
+    suffix_single_kernel(const float2* __restrict__ acc, const float* __restrict__ w, int64_t N,
+                         const double* __restrict__ G, uint32_t* flags, double* carry,
+                         double* incl, uint32_t* ticket, float* grad_w, uint32_t* status) {
+  __shared__ uint32_t tick_s;
+  __shared__ float wtot_s[kBwThreads / 32];
+  __shared__ int first_prefix_s, first_invalid_s;
+  __shared__ double part_s[kBwThreads / 32];
+  __shared__ double E_s;
+  if (threadIdx.x == 0) tick_s = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t ntiles = (N + kBwTile - 1) / kBwTile;
+  const int64_t tile = ntiles - 1 - (int64_t)tick_s;
+  const int64_t t0 = tile * kBwTile, t1 = min(t0 + (int64_t)kBwTile, N);
+  const int64_t e0 = t0 + (int64_t)threadIdx.x * kBwPer;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+  float a[kBwPer], b[kBwPer];
+  if (e0 + kBwPer <= t1) {
+    const float4* av = reinterpret_cast<const float4*>(acc + e0);
+    const float4* wv = reinterpret_cast<const float4*>(w + e0);
+#pragma unroll
+    for (int h = 0; h < kBwPer / 4; ++h) {
+      const float4 x0 = av[2 * h], x1 = av[2 * h + 1], ww = wv[h];
+      const float ax[4] = {x0.x, x0.z, x1.x, x1.z}, bx[4] = {x0.y, x0.w, x1.y, x1.w};
+      const float wk[4] = {ww.x, ww.y, ww.z, ww.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        a[4 * h + k] = 0.f;
+        b[4 * h + k] = 0.f;
+        if (ax[k] != 0.0f || bx[k] != 0.0f) {
+          const float inv = 1.0f / wk[k];
+          a[4 * h + k] = ax[k] * inv;
+          b[4 * h + k] = bx[k] * inv;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kBwPer; ++k) {
+      a[k] = 0.f;
+      b[k] = 0.f;
+      const int64_t e = e0 + k;
+      if (e < t1) {
+        const float2 v = acc[e];
+        if (v.x != 0.0f || v.y != 0.0f) {
+          const float inv = 1.0f / w[e];
+          a[k] = v.x * inv;
+          b[k] = v.y * inv;
+        }
+      }
+    }
+  }
+  float tot = 0.f;
+#pragma unroll
+  for (int k = kBwPer - 1; k >= 0; --k) tot += a[k];
+  // sum of the thread totals after this thread: within the warp by shuffles,
+  // then over the warps after this one
+  float v = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v += y;
+  }
+  if (lane == 0) wtot_s[wid] = v;
+  __syncthreads();
+  float exv = v - tot;
+  float tile_tot = 0.f;
+#pragma unroll
+  for (int k = kBwThreads / 32 - 1; k >= 0; --k) {
+    if (k > wid) exv += wtot_s[k];
+    tile_tot += wtot_s[k];
+  }
+  const bool last_tile = t1 == N;  // the distribution's last element lies here
+  if (threadIdx.x == 0) {
+    carry[tile] = (double)tile_tot;
+    incl[tile] = (double)tile_tot;
+    __threadfence();
+    atomicExch(flags + tile, last_tile ? 2u : 1u);
+  }
+  // block-wide lookback for the sum beyond t1 (as in suffix_kernel)
+  double E = 0.0;
+  if (!last_tile) {
+    int64_t look = tile + 1;
+    long long spins = 0;
+    while (look < ntiles) {
+      if (threadIdx.x == 0) {
+        first_prefix_s = kBwThreads;
+        first_invalid_s = kBwThreads;
+      }
+      __syncthreads();
+      const int64_t idx = look + threadIdx.x;
+      const uint32_t fl = idx < ntiles ? *((volatile uint32_t*)(flags + idx)) : 2u;
+      if (fl == 2) atomicMin(&first_prefix_s, (int)threadIdx.x);
+      if (fl == 0) atomicMin(&first_invalid_s, (int)threadIdx.x);
+      __syncthreads();
+      const int pfx = first_prefix_s, inv = first_invalid_s;
+      if (inv < pfx) {
+        if (++spins > kSpinLimit) {
+          if (threadIdx.x == 0) raise_status(status, RTF_STATUS_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+        __syncthreads();
+        continue;
+      }
+      __threadfence();
+      double x = 0.0;
+      if ((int)threadIdx.x < pfx && idx < ntiles) x = *((volatile double*)(carry + idx));
+      if ((int)threadIdx.x == pfx && idx < ntiles) x = *((volatile double*)(incl + idx));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) part_s[wid] = x;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kBwThreads / 32; ++k) t += part_s[k];
+        E_s = t;
+      }
+      __syncthreads();
+      E += E_s;
+      if (pfx < kBwThreads) break;
+      look += kBwThreads;
+    }
+    if (threadIdx.x == 0) {
+      incl[tile] = (double)tile_tot + E;
+      __threadfence();
+      atomicExch(flags + tile, 2u);
+    }
+  }
+  if (e0 >= t1) return;
+  const float base = (float)(G[0] - ((double)exv + E));
+  float inrun = 0.f;
+  float gk[kBwPer];
+#pragma unroll
+  for (int k = kBwPer - 1; k >= 0; --k) {
+    gk[k] = base - inrun - b[k];
+    inrun += a[k];
+  }
+  if (e0 + kBwPer <= t1) {
+    float4* gv = reinterpret_cast<float4*>(grad_w + e0);
+#pragma unroll
+    for (int h = 0; h < kBwPer / 4; ++h)
+      gv[h] = make_float4(gk[4 * h], gk[4 * h + 1], gk[4 * h + 2], gk[4 * h + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kBwPer; ++k)
+      if (e0 + k < t1) grad_w[e0 + k] = gk[k];
+  }
+}
+
 __global__ void add_row_kernel(float* grad_w, const rtf_dist* __restrict__ dists, int H,
                                const float* __restrict__ gradR) {
   for (int r = blockIdx.x; r < H; r += gridDim.x) {
@@ -502,9 +657,15 @@ cudaError_t launch_backward_finish(const rtf_forest* f, const float* w, int mode
   const int64_t tiles = (N + kBwTile - 1) / kBwTile;
   bin_total_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, f->nodes, w, R, f->dists, D, N,
                                                            Nw, G);
-  suffix_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, w, R, f->dists, D, N, Nw, G, flags,
-                                                        carry, incl, ticket, grad_w, gradR,
-                                                        f->status);
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(w) & 15) == 0 &&
+                      (reinterpret_cast<uintptr_t>(grad_w) & 15) == 0;
+  if (D == 1 && !two_d && vec_ok)
+    suffix_single_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, w, N, G, flags, carry,
+                                                                 incl, ticket, grad_w, f->status);
+  else
+    suffix_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, w, R, f->dists, D, N, Nw, G,
+                                                          flags, carry, incl, ticket, grad_w,
+                                                          gradR, f->status);
   if (two_d)
     add_row_kernel<<<(unsigned)std::min<int64_t>(sms * 4, D - 1), 256, 0, st>>>(
         grad_w, f->dists, D - 1, gradR);
