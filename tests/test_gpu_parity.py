@@ -508,21 +508,28 @@ def test_bsearch_load_counts_bounded():
 # host-streamed sampling (rtf_sample_pipelined)
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("coherent", [False, True])
 @pytest.mark.parametrize("chunk", [4, 4096, 1 << 20])
-def test_pipelined_equals_device_sampling(chunk):
+def test_pipelined_equals_device_sampling(chunk, coherent):
     """Host samples in, device and host results out, chunked with overlap; a
-    count that is not a multiple of the chunk."""
+    count that is not a multiple of the chunk; i.i.d. samples, and sorted
+    samples with the coherence hint (the coherent sampler per chunk)."""
     w = W.lognormal_weights(100000, seed=70, sigma=2.0)
     f = api.rtf_build(to_dev(w), 14)
     n_s = 50001 if chunk > 4 else 999
     u = W.iid_u32(n_s, seed=71)
+    mode = api.SAMPLE_1D
+    if coherent:
+        u = np.sort(u)
+        mode |= api.SAMPLE_COHERENT
     u_host = torch.from_numpy(u.view(np.int32)).pin_memory()
     u_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
     idx_dev = torch.empty(n_s, dtype=torch.int32, device=DEV)
     pos_dev = torch.empty(n_s, dtype=torch.float32, device=DEV)
     idx_host = torch.empty(n_s, dtype=torch.int32).pin_memory()
     pos_host = torch.empty(n_s, dtype=torch.float32).pin_memory()
-    api.rtf_sample_pipelined(f, u_host, u_dev, idx_dev, pos_dev, idx_host, pos_host, chunk=chunk)
+    api.rtf_sample_pipelined(f, u_host, u_dev, idx_dev, pos_dev, idx_host, pos_host, chunk=chunk,
+                             mode=mode)
     torch.cuda.synchronize()
     ridx, rpos = orc.sample(orc.build(w, 1 << 14).C, u)
     check_samples(idx_host.numpy(), pos_host.numpy(), ridx, rpos)
