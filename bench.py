@@ -488,6 +488,9 @@ def gpu_arm(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "traffic_GBps": traffic / (avg[dom] * 1e-3) / 1e9 if traffic else None,
+                     # the DRAM bytes ncu measured for this kernel (random node and guide
+                     # lines included) against the same peak
+                     "traffic_frac": traffic / (avg[dom] * 1e-3) / 1e9 / peak if traffic else None,
                      "peak_kind": peak_kind},
         "alone_ms": alone_ms,
         "fractions_of_hbm": {k: alg[k] / (alone_ms[k] * 1e-3) / 1e9 / peak for k in alone_ms},
