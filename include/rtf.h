@@ -371,6 +371,17 @@ rtf_status rtf_sample_quad(const rtf_forest *f, const rtf_quad_rec *quad,
                            int32_t mode, int32_t *idx_out, float *pos_out,
                            int32_t *loads_out, void *stream);
 
+/*
+ * Check of the failure path of the library's bounded waits, without any
+ * fault: one block runs the decoupled-lookback wait of the scans on a
+ * predecessor status word that nothing publishes (scratch: two 64-bit words
+ * of device memory, cleared by the call).  After its iteration limit (about
+ * a second) the wait gives up, sets RTF_STATUS_TIMEOUT in *status (device
+ * memory, not cleared) and the kernel returns; the context stays usable.
+ * Stream-ordered.
+ */
+rtf_status rtf_check_bounded_wait(uint32_t *status, uint64_t *scratch, void *stream);
+
 /* Bytes of workspace rtf_sample_backward needs. */
 size_t rtf_backward_workspace_size(int64_t num_elems, int32_t num_dists);
 

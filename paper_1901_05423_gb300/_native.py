@@ -130,6 +130,7 @@ EXPORTS = {
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "rtf_check_bounded_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rtf_backward_begin": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                           ctypes.c_size_t, ctypes.c_void_p]),
     "rtf_backward_accumulate": (ctypes.c_int, [ctypes.POINTER(RtfForestC)] + [ctypes.c_void_p] * 4

@@ -327,6 +327,19 @@ def rtf_sample_quad(forest: Forest, quad: torch.Tensor, u: torch.Tensor,
     return idx_out, pos_out
 
 
+def check_bounded_wait(device=None) -> int:
+    """Run the library's bounded wait on a status word nothing publishes
+    (``rtf_check_bounded_wait``); returns the status bits it raised (the
+    wait gives up after about a second and sets STATUS_TIMEOUT)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    scratch = torch.zeros(2, dtype=torch.int64, device=dev)
+    lib = _native.load()
+    _check(lib.rtf_check_bounded_wait(_ptr(status), _ptr(scratch), _stream_ptr(dev)),
+           "rtf_check_bounded_wait")
+    return int(status.item())
+
+
 def load_statistics(loads, group: int = 32) -> dict:
     """Maximum, average and average over consecutive groups of `group` samples
     of the group's maximum (the cost of samples that run in lockstep), the

@@ -24,6 +24,7 @@ cudaError_t launch_sample_loads(const rtf_forest* f, const uint32_t* u, const in
                                 int64_t count, int mode, int32_t* loads_out, cudaStream_t st);
 size_t backward_ws_bytes(int64_t N, int32_t D);
 cudaError_t launch_build_quad(const rtf_forest* f, rtf_quad_rec* quad, cudaStream_t st);
+cudaError_t launch_wait_probe(uint32_t* status, uint64_t* scratch, cudaStream_t st);
 cudaError_t launch_sample_quad(const rtf_forest* f, const rtf_quad_rec* quad, const uint32_t* u,
                                const int32_t* dist_id, int64_t count, int mode, int32_t* idx_out,
                                float* pos_out, int32_t* loads_out, cudaStream_t st);
@@ -186,6 +187,11 @@ rtf_status rtf_sample_quad(const rtf_forest* f, const rtf_quad_rec* quad, const 
   if (loads_out && !aligned(loads_out, 8)) return RTF_EINVAL;
   return cuda_status(rtf::launch_sample_quad(f, quad, u, dist_id, count, mode, idx_out, pos_out,
                                              loads_out, static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_check_bounded_wait(uint32_t* status, uint64_t* scratch, void* stream) {
+  if (!status || !scratch || !aligned(status, 4) || !aligned(scratch, 8)) return RTF_EINVAL;
+  return cuda_status(rtf::launch_wait_probe(status, scratch, static_cast<cudaStream_t>(stream)));
 }
 
 size_t rtf_backward_workspace_size(int64_t num_elems, int32_t num_dists) {

@@ -880,6 +880,23 @@ __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t
 }
 
 // ---------------------------------------------------------------------------
+// check of the bounded waits: a lookback on a predecessor nobody publishes
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) wait_probe_kernel(const uint64_t* st,
+                                                                  uint32_t* status) {
+  __shared__ LookbackShared lb;
+  // tile 1 waits for tile 0, whose status word stays 0 (not published)
+  (void)block_lookback(st, 1, true, &lb, status);
+}
+
+cudaError_t launch_wait_probe(uint32_t* status, uint64_t* scratch, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * sizeof(uint64_t), st);
+  if (e != cudaSuccess) return e;
+  wait_probe_kernel<<<1, kScanThreads, 0, st>>>(scratch, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // guide: cells without keys take the interval of the last key before them
 // ---------------------------------------------------------------------------
 constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 4

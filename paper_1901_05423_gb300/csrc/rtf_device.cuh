@@ -224,7 +224,6 @@ __device__ __forceinline__ uint32_t key_distance(uint64_t a, uint64_t b) {
 __device__ __forceinline__ float u64_to_f32(uint64_t x) { return __ull2float_rn(x); }
 
 // ---------------------------------------------------------------------------
-// memory ordering helpers// ---------------------------------------------------------------------------
 // memory ordering helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
@@ -503,7 +502,7 @@ __device__ __forceinline__ uint64_t block_lookback(const uint64_t* st, int64_t t
   return E;
 }
 
-// Index of the distribution that owns element `e`// Index of the distribution that owns element `e`: the largest d with
+// Index of the distribution that owns element `e`: the largest d with
 // dists[d].elem_off <= e (binary search over [lo, hi]).
 __device__ inline int find_dist(const rtf_dist* dists, int lo, int hi, int64_t e) {
   // galloping from lo (callers pass the first distribution of a tile, and an

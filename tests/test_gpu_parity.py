@@ -720,3 +720,23 @@ def test_coherent_window_orders_many_batches(kind):
         assert torch.equal(i1, i2), f"{kind}/{name}: indices"
         assert torch.equal(p1.view(torch.int32), p2.view(torch.int32)), f"{kind}/{name}: positions"
         assert int(i1.min()) >= 0
+
+
+# ---------------------------------------------------------------------------
+# failure path of the bounded waits (no fault: a flag that nothing sets)
+# ---------------------------------------------------------------------------
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    import time
+    t0 = time.time()
+    st = api.check_bounded_wait(DEV)
+    dt = time.time() - t0
+    assert st & api.STATUS_TIMEOUT, st
+    assert dt < 60, f"the wait took {dt:.1f} s"
+    # the same context builds and samples correctly afterwards
+    w = W.lognormal_weights(5000, seed=81, sigma=2.0)
+    f, ref = build_and_check(w, 9)
+    u = W.iid_u32(1 << 14, seed=82)
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
+    ridx, rpos = orc.sample(ref.C, u)
+    check_samples(idx, pos, ridx, rpos)

@@ -108,6 +108,8 @@ def test_bad_arguments_rejected_without_gpu_work(lib):
                                None, None) == EINVAL  # samples needed
     assert lib.rtf_sample_quad(ctypes.byref(f), P0(32), None, None, 0, 0, None, None,
                                None, None) == 0  # nothing to do
+    assert lib.rtf_check_bounded_wait(None, P0(16), None) == EINVAL
+    assert lib.rtf_check_bounded_wait(P0(16), P0(12), None) == EINVAL  # scratch 8-byte aligned
     P = ctypes.c_void_p
     for chunk in (0, 3, 6):  # chunks are positive multiples of 4
         assert lib.rtf_sample_pipelined(ctypes.byref(f), None, P(16), None, None, 8, 0, P(16),
