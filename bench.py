@@ -584,8 +584,11 @@ def extra_ragged(dev, reps=3):
     b.record()
     torch.cuda.synchronize()
     looped_ms = a.elapsed_time(b)
-    # build + tagged sampling captured once, replayed
+    # the tagged sampler's launch shape from the autotuner (timed on the first
+    # 2^24 samples), then build + tagged sampling captured once and replayed
     f = api.rtf_build_batched(w, sizes, ms, forest=f, plan_dev=f._plan_dev)
+    kind, shape, shape_ms = autotune.tune_launch_shape(f, u[:1 << 24], dist[:1 << 24],
+                                                       use_cache=False)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     st = torch.cuda.Stream(dev)
@@ -605,10 +608,14 @@ def extra_ragged(dev, reps=3):
     torch.cuda.synchronize()
     f.check_status()
     graph_ms = a.elapsed_time(b) / reps
+    api.reset_launch_shape()
     N = int(off[-1])
     return {
         "workload": "16384 ragged distributions, n_d log-uniform in [8,65536] (sum %d), "
-                    "lognormal(0,1.5), autotuned guide bits, 2^27 tagged iid samples" % N,
+                    "lognormal(0,1.5), autotuned guide bits and launch shape, "
+                    "2^27 tagged iid samples" % N,
+        "launch_shape": {"kind": kind, "blocks_per_sm": shape,
+                         "ms_per_2^24_samples": {str(k): v for k, v in shape_ms.items()}},
         "batched_build_ms": batched_ms, "looped_build_ms": looped_ms,
         "batched_over_looped": looped_ms / batched_ms,
         "build_elem_per_s": N / (batched_ms * 1e-3),

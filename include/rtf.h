@@ -276,6 +276,30 @@ rtf_status rtf_sample(const rtf_forest *f, const uint32_t *u,
                       int32_t *idx_out, float *pos_out, void *stream);
 
 /*
+ * Launch shape of the samplers: the resident blocks of 256 threads per SM
+ * that each kind of sampling launch is given (its grid is that times the SM
+ * count, capped by the work).  0 keeps the built-in choice, measured on
+ * GB300: 3 for one distribution with scattered samples over records larger
+ * than L2 (fewer resident descents keep more of the structure in L2), 8 for
+ * one distribution otherwise, 8 with a distribution id per sample, 8 in 2-D.
+ * (The coherent sampler always runs one wave of resident blocks.)  The
+ * setting is process-wide, applies to launches issued after the call and
+ * never changes a result.  Each value must lie in [0, 64].
+ */
+typedef struct rtf_launch_shape {
+  int32_t single_large; /* one distribution, records larger than L2, scattered samples */
+  int32_t single;       /* one distribution otherwise (without the coherence hint) */
+  int32_t tagged;       /* a distribution id per sample */
+  int32_t pairs;        /* RTF_SAMPLE_2D */
+} rtf_launch_shape;
+
+/* Sets the launch shape; NULL restores the built-in choices. */
+rtf_status rtf_set_launch_shape(const rtf_launch_shape *shape);
+
+/* The shape in effect, built-in choices filled in. */
+rtf_status rtf_get_launch_shape(rtf_launch_shape *shape);
+
+/*
  * rtf_sample for samples that live in host memory: the samples are copied to
  * the device, mapped and the results copied back in chunks of `chunk` samples
  * (a multiple of 4), with the copies of one chunk overlapping the sampling of

@@ -102,6 +102,12 @@ class RtfForestC(ctypes.Structure):
     ]
 
 
+class RtfLaunchShapeC(ctypes.Structure):
+    """Mirror of ``rtf_launch_shape`` in include/rtf.h (16 bytes)."""
+    _fields_ = [("single_large", ctypes.c_int32), ("single", ctypes.c_int32),
+                ("tagged", ctypes.c_int32), ("pairs", ctypes.c_int32)]
+
+
 EXPORTS = {
     # name: (restype, argtypes)
     "rtf_version": (ctypes.c_char_p, []),
@@ -131,6 +137,8 @@ EXPORTS = {
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "rtf_check_bounded_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "rtf_set_launch_shape": (ctypes.c_int, [ctypes.POINTER(RtfLaunchShapeC)]),
+    "rtf_get_launch_shape": (ctypes.c_int, [ctypes.POINTER(RtfLaunchShapeC)]),
     "rtf_backward_begin": (ctypes.c_int, [ctypes.POINTER(RtfForestC), ctypes.c_void_p,
                                           ctypes.c_size_t, ctypes.c_void_p]),
     "rtf_backward_accumulate": (ctypes.c_int, [ctypes.POINTER(RtfForestC)] + [ctypes.c_void_p] * 4

@@ -327,6 +327,38 @@ def rtf_sample_quad(forest: Forest, quad: torch.Tensor, u: torch.Tensor,
     return idx_out, pos_out
 
 
+LAUNCH_KINDS = ("single_large", "single", "tagged", "pairs")
+
+
+def get_launch_shape() -> dict:
+    """Blocks per SM of each kind of sampling launch (``rtf_get_launch_shape``)."""
+    lib = _native.load()
+    c = _native.RtfLaunchShapeC()
+    _check(lib.rtf_get_launch_shape(ctypes.byref(c)), "rtf_get_launch_shape")
+    return {k: int(getattr(c, k)) for k in LAUNCH_KINDS}
+
+
+def set_launch_shape(**kinds) -> dict:
+    """Set blocks per SM for some kinds (others keep their current value);
+    returns the shape in effect (``rtf_set_launch_shape``)."""
+    unknown = set(kinds) - set(LAUNCH_KINDS)
+    if unknown:
+        raise RtfError(f"unknown launch kinds {sorted(unknown)}")
+    cur = get_launch_shape()
+    cur.update({k: int(v) for k, v in kinds.items()})
+    lib = _native.load()
+    c = _native.RtfLaunchShapeC(**cur)
+    _check(lib.rtf_set_launch_shape(ctypes.byref(c)), "rtf_set_launch_shape")
+    return get_launch_shape()
+
+
+def reset_launch_shape() -> dict:
+    """Back to the built-in launch shape."""
+    lib = _native.load()
+    _check(lib.rtf_set_launch_shape(None), "rtf_set_launch_shape")
+    return get_launch_shape()
+
+
 def check_bounded_wait(device=None) -> int:
     """Run the library's bounded wait on a status word nothing publishes
     (``rtf_check_bounded_wait``); returns the status bits it raised (the

@@ -1,4 +1,5 @@
-"""Autotuner of the guide size for ragged batches.
+"""Autotuner of the guide size for ragged batches and of the samplers'
+launch shape.
 
 The paper leaves the guide table size to the application: as large as memory
 allows, or proportional to the size of the distribution (Sec. 3).  For a
@@ -7,8 +8,16 @@ measured here on the GPU: for every power-of-two size bucket a batch of
 synthetic lognormal distributions of that size is built and sampled (one
 tagged sample per weight, the ratio of the ragged workload) for each candidate
 number of guide bits m around log2(n), and the m with the smallest build +
-sampling time wins.  Results are cached per GPU model in a JSON file
-(``$RTF_CACHE_DIR`` or ``~/.cache/rtf``).
+sampling time wins.
+
+The launch shape (resident blocks per SM of each kind of sampling launch,
+``rtf_set_launch_shape``) is tuned on the caller's own structure and samples:
+each candidate is timed on them and the fastest is set.  It matters most where
+the structure does not fit L2 and the samples are scattered: fewer resident
+descents then keep more of the structure in L2.
+
+Results are cached per GPU model in JSON files (``$RTF_CACHE_DIR`` or
+``~/.cache/rtf``).
 """
 
 from __future__ import annotations
@@ -25,10 +34,10 @@ from . import workloads as W
 DEFAULT_OFFSETS = (-2, -1, 0, 1, 2)
 
 
-def _cache_path(device: torch.device) -> str:
+def _cache_path(device: torch.device, what: str = "guide_bits") -> str:
     root = os.environ.get("RTF_CACHE_DIR") or os.path.join(os.path.expanduser("~"), ".cache", "rtf")
     name = torch.cuda.get_device_name(device).replace(" ", "_")
-    return os.path.join(root, f"guide_bits_{name}.json")
+    return os.path.join(root, f"{what}_{name}.json")
 
 
 def _time_bucket(n: int, m: int, device, total: int, reps: int, seed: int) -> float:
@@ -88,3 +97,63 @@ def guide_bits_for(sizes, table: dict) -> np.ndarray:
     b = np.clip(np.round(np.log2(np.maximum(sizes, 1))).astype(int), min(table), max(table))
     lut = np.array([table.get(int(k), int(k)) for k in range(0, max(table) + 1)])
     return lut[b].astype(np.int32)
+
+
+DEFAULT_SHAPES = (2, 3, 4, 6, 8, 12, 16)
+
+
+def _launch_kind(forest, u, dist_id, mode) -> str:
+    if (mode & 0xFF) == api.SAMPLE_2D:
+        return "pairs"
+    if dist_id is not None:
+        return "tagged"
+    records = forest.num_elems * api.NODE_BYTES + forest.num_cells * api.GUIDE_REC_BYTES
+    l2 = torch.cuda.get_device_properties(u.device).L2_cache_size
+    return "single_large" if records > l2 else "single"
+
+
+def tune_launch_shape(forest, u: torch.Tensor, dist_id: torch.Tensor | None = None,
+                      mode: int = api.SAMPLE_1D, candidates=DEFAULT_SHAPES, reps: int = 3,
+                      key: str | None = None, use_cache: bool = True) -> tuple[str, int, dict]:
+    """Time rtf_sample on (forest, u, dist_id, mode) with each candidate number
+    of blocks per SM for the kind of launch it makes, set the fastest and
+    return (kind, blocks per SM, {candidate: ms}).  With `key`, the choice is
+    cached under it (per GPU model) and reused without timing."""
+    if mode & api.SAMPLE_COHERENT:
+        raise api.RtfError("the coherent sampler runs one wave of resident blocks; nothing to tune")
+    kind = _launch_kind(forest, u, dist_id, mode)
+    path = _cache_path(u.device, "launch_shape")
+    cache = {}
+    if use_cache and key is not None and os.path.exists(path):
+        with open(path) as fh:
+            cache = json.load(fh)
+        if f"{kind}/{key}" in cache:
+            best = int(cache[f"{kind}/{key}"])
+            api.set_launch_shape(**{kind: best})
+            return kind, best, {}
+    two_d = (mode & 0xFF) == api.SAMPLE_2D
+    count = u.numel() // (2 if two_d else 1)
+    shape = (count, 2) if two_d else (count,)
+    idx = torch.empty(shape, dtype=torch.int32, device=u.device)
+    pos = torch.empty(shape, dtype=torch.float32, device=u.device)
+    times = {}
+    for c in candidates:
+        api.set_launch_shape(**{kind: int(c)})
+        api.rtf_sample(forest, u, dist_id=dist_id, mode=mode, idx_out=idx, pos_out=pos)
+        torch.cuda.synchronize(u.device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            api.rtf_sample(forest, u, dist_id=dist_id, mode=mode, idx_out=idx, pos_out=pos)
+        e1.record()
+        torch.cuda.synchronize(u.device)
+        times[int(c)] = e0.elapsed_time(e1) / reps
+    best = min(times, key=times.get)
+    api.set_launch_shape(**{kind: best})
+    if use_cache and key is not None:
+        cache[f"{kind}/{key}"] = best
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as fh:
+            json.dump(cache, fh)
+    return kind, best, times

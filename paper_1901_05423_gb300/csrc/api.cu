@@ -25,6 +25,8 @@ cudaError_t launch_sample_loads(const rtf_forest* f, const uint32_t* u, const in
 size_t backward_ws_bytes(int64_t N, int32_t D);
 cudaError_t launch_build_quad(const rtf_forest* f, rtf_quad_rec* quad, cudaStream_t st);
 cudaError_t launch_wait_probe(uint32_t* status, uint64_t* scratch, cudaStream_t st);
+void set_launch_shape(const int32_t* v);
+void get_launch_shape(int32_t* v);
 cudaError_t launch_sample_quad(const rtf_forest* f, const rtf_quad_rec* quad, const uint32_t* u,
                                const int32_t* dist_id, int64_t count, int mode, int32_t* idx_out,
                                float* pos_out, int32_t* loads_out, cudaStream_t st);
@@ -187,6 +189,29 @@ rtf_status rtf_sample_quad(const rtf_forest* f, const rtf_quad_rec* quad, const 
   if (loads_out && !aligned(loads_out, 8)) return RTF_EINVAL;
   return cuda_status(rtf::launch_sample_quad(f, quad, u, dist_id, count, mode, idx_out, pos_out,
                                              loads_out, static_cast<cudaStream_t>(stream)));
+}
+
+rtf_status rtf_set_launch_shape(const rtf_launch_shape* shape) {
+  if (!shape) {
+    rtf::set_launch_shape(nullptr);
+    return RTF_OK;
+  }
+  const int32_t v[4] = {shape->single_large, shape->single, shape->tagged, shape->pairs};
+  for (int k = 0; k < 4; ++k)
+    if (v[k] < 0 || v[k] > 64) return RTF_EINVAL;
+  rtf::set_launch_shape(v);
+  return RTF_OK;
+}
+
+rtf_status rtf_get_launch_shape(rtf_launch_shape* shape) {
+  if (!shape) return RTF_EINVAL;
+  int32_t v[4];
+  rtf::get_launch_shape(v);
+  shape->single_large = v[0];
+  shape->single = v[1];
+  shape->tagged = v[2];
+  shape->pairs = v[3];
+  return RTF_OK;
 }
 
 rtf_status rtf_check_bounded_wait(uint32_t* status, uint64_t* scratch, void* stream) {

@@ -865,6 +865,24 @@ __global__ void __launch_bounds__(kSampleThreads)
 }
 
 
+// The launch shape (rtf_set_launch_shape): blocks per SM per kind of launch,
+// 0 for the built-in choice.
+static std::atomic<int> g_shape[4];  // single_large, single, tagged, pairs
+constexpr int kShapeBuiltin[4] = {RTF_SAMPLE_BLOCKS_PER_SM_BIG, RTF_SAMPLE_BLOCKS_PER_SM, 8, 8};
+
+static int shape_of(int kind) {
+  const int v = g_shape[kind].load(std::memory_order_relaxed);
+  return v > 0 ? v : kShapeBuiltin[kind];
+}
+
+void set_launch_shape(const int32_t* v) {
+  for (int k = 0; k < 4; ++k) g_shape[k].store(v ? v[k] : 0, std::memory_order_relaxed);
+}
+
+void get_launch_shape(int32_t* v) {
+  for (int k = 0; k < 4; ++k) v[k] = shape_of(k);
+}
+
 template <bool BS>
 static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_t* dist_id,
                             int64_t count, int mode, bool coherent, int32_t* idx_out,
@@ -872,7 +890,8 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
   const int sms = num_sms();
   if (mode == RTF_SAMPLE_2D) {
     const int64_t per = BS ? 1 : RTF_2D_PAIRS;  // pairs per thread and step
-    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads * per - 1) / (kSampleThreads * per));
+    int64_t blocks = min((int64_t)sms * shape_of(3),
+                         (count + kSampleThreads * per - 1) / (kSampleThreads * per));
     sample_2d_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
         f->nodes, f->guide_recs, f->dists, f->num_dists, reinterpret_cast<const uint2*>(u), count,
         reinterpret_cast<int2*>(idx_out), reinterpret_cast<float2*>(pos_out));
@@ -880,7 +899,8 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
   }
   if (dist_id != nullptr) {
     const int64_t per = BS ? 1 : RTF_TAGGED_K;  // samples per thread and step
-    int64_t blocks = min((int64_t)sms * 8, (count + kSampleThreads * per - 1) / (kSampleThreads * per));
+    int64_t blocks = min((int64_t)sms * shape_of(2),
+                         (count + kSampleThreads * per - 1) / (kSampleThreads * per));
     sample_tagged_kernel<BS><<<(unsigned)blocks, kSampleThreads, 0, st>>>(
         f->nodes, f->guide_recs, f->dists, f->num_dists, u, dist_id, count, idx_out, pos_out,
         f->status);
@@ -906,8 +926,7 @@ static void launch_sample_t(const rtf_forest* f, const uint32_t* u, const int32_
   const int64_t per_block = (int64_t)kSampleThreads * 4;
   const int64_t records = (int64_t)sizeof(rtf_node) * f->num_elems +
                           (int64_t)sizeof(rtf_guide_rec) * f->num_cells;
-  const int per_sm = !coherent && records > l2_bytes() ? RTF_SAMPLE_BLOCKS_PER_SM_BIG
-                                                       : RTF_SAMPLE_BLOCKS_PER_SM;
+  const int per_sm = !coherent && records > l2_bytes() ? shape_of(0) : shape_of(1);
   int64_t blocks = min((int64_t)sms * per_sm, (count + per_block - 1) / per_block);
   if (f->max_m <= kSmemGuideMaxBits) {
     size_t smem = sizeof(rtf_guide_rec) << f->max_m;

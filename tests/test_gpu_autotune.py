@@ -25,3 +25,49 @@ def test_small_tuning_run(tmp_path, monkeypatch):
     assert again == table  # served from the cache file
     ms = autotune.guide_bits_for(np.array([8, 9, 100, 256, 10 ** 6]), table)
     assert ms.dtype == np.int32 and ms[0] == table[3] and ms[-1] == table[8]
+
+
+def test_launch_shape_changes_no_result_and_is_tuned(tmp_path, monkeypatch):
+    """Every launch shape gives the same bits (tagged samples over a ragged
+    batch, and scattered samples over one structure larger than L2); the
+    launch-shape autotuner picks one of its candidates, sets it and caches it."""
+    from paper_1901_05423_gb300 import api, autotune
+    from paper_1901_05423_gb300 import workloads as W
+    monkeypatch.setenv("RTF_CACHE_DIR", str(tmp_path))
+    dev = torch.device("cuda:0")
+    try:
+        w_h, off = W.ragged_batch(512, seed=5)
+        sizes = np.diff(off)
+        f = api.rtf_build_batched(torch.from_numpy(w_h).to(dev), sizes,
+                                  np.clip(np.round(np.log2(sizes)).astype(int), 3, 16))
+        u = api.u32_tensor(W.iid_u32(1 << 20, seed=6), dev)
+        d = torch.from_numpy(W.dist_ids(1 << 20, len(sizes), seed=7)).to(dev)
+        i0, p0 = api.rtf_sample(f, u, dist_id=d)
+        for c in (1, 2, 5, 16):
+            api.set_launch_shape(tagged=c)
+            i1, p1 = api.rtf_sample(f, u, dist_id=d)
+            assert torch.equal(i0, i1) and torch.equal(p0.view(torch.int32), p1.view(torch.int32))
+        kind, best, times = autotune.tune_launch_shape(f, u, d, candidates=(2, 8), reps=1,
+                                                       key="ragged512")
+        assert kind == "tagged" and best in (2, 8) and sorted(times) == [2, 8]
+        assert api.get_launch_shape()["tagged"] == best
+        api.reset_launch_shape()
+        kind2, best2, times2 = autotune.tune_launch_shape(f, u, d, candidates=(2, 8), reps=1,
+                                                         key="ragged512")
+        assert (kind2, best2, times2) == ("tagged", best, {})  # from the cache
+        assert api.get_launch_shape()["tagged"] == best
+
+        wb = W.lognormal_weights(1 << 23, seed=8, sigma=2.0)  # 128 MB of node records
+        fb = api.rtf_build(torch.from_numpy(wb).to(dev), 20)
+        ub = api.u32_tensor(W.iid_u32(1 << 22, seed=9), dev)
+        i0, p0 = api.rtf_sample(fb, ub)
+        for c in (1, 3, 8):
+            api.set_launch_shape(single_large=c)
+            i1, p1 = api.rtf_sample(fb, ub)
+            assert torch.equal(i0, i1) and torch.equal(p0.view(torch.int32), p1.view(torch.int32))
+        kind, best, _ = autotune.tune_launch_shape(fb, ub, candidates=(3, 8), reps=1)
+        assert kind == "single_large" and api.get_launch_shape()["single_large"] == best
+        fb.check_status()
+        f.check_status()
+    finally:
+        api.reset_launch_shape()

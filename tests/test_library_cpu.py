@@ -165,3 +165,28 @@ def test_load_statistics_columns():
     assert st["average32"] == (7 + 3) / 2
     with pytest.raises(ValueError):
         load_statistics(np.array([1, -1]))
+
+
+def test_launch_shape_host_logic(lib):
+    """rtf_set_launch_shape / rtf_get_launch_shape: values in [0, 64], 0 for the
+    built-in choice, NULL restores all; no GPU work."""
+    from paper_1901_05423_gb300 import _native
+    EINVAL = 1
+    s = _native.RtfLaunchShapeC()
+    try:
+        assert lib.rtf_set_launch_shape(None) == 0
+        assert lib.rtf_get_launch_shape(ctypes.byref(s)) == 0
+        builtin = (s.single_large, s.single, s.tagged, s.pairs)
+        assert builtin == (3, 8, 8, 8)
+        assert lib.rtf_set_launch_shape(ctypes.byref(_native.RtfLaunchShapeC(5, 0, 12, 0))) == 0
+        lib.rtf_get_launch_shape(ctypes.byref(s))
+        assert (s.single_large, s.single, s.tagged, s.pairs) == (5, 8, 12, 8)
+        for bad in ((65, 0, 0, 0), (0, -1, 0, 0), (0, 0, 0, 1000)):
+            assert lib.rtf_set_launch_shape(ctypes.byref(_native.RtfLaunchShapeC(*bad))) == EINVAL
+        lib.rtf_get_launch_shape(ctypes.byref(s))
+        assert (s.single_large, s.tagged) == (5, 12)  # a rejected call changes nothing
+        assert lib.rtf_get_launch_shape(None) == EINVAL
+    finally:
+        lib.rtf_set_launch_shape(None)
+    lib.rtf_get_launch_shape(ctypes.byref(s))
+    assert (s.single_large, s.single, s.tagged, s.pairs) == builtin
