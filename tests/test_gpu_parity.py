@@ -740,3 +740,49 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable():
     idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
     ridx, rpos = orc.sample(ref.C, u)
     check_samples(idx, pos, ridx, rpos)
+
+
+# ---------------------------------------------------------------------------
+# sizes past 32-bit indexing, and guide tables much larger than n
+# ---------------------------------------------------------------------------
+
+def test_sample_counts_past_2_31():
+    """2^31 + 1029 samples in one call (i.i.d. and, ascending, through the
+    coherent sampler): the kernels' 64-bit sample indexing and their tails;
+    the oracle checks the first and last 1024 samples and 2048 in between."""
+    w = W.lognormal_weights(1 << 20, seed=91, sigma=2.0)
+    f = api.rtf_build(to_dev(w), 16)
+    ref = orc.build(w, 1 << 16)
+    ns = (1 << 31) + 1029
+    gen = torch.Generator(device=DEV).manual_seed(92)
+    sel = np.concatenate([np.arange(1024), ns - 1024 + np.arange(1024),
+                          np.random.default_rng(93).integers(1024, ns - 1024, 2048)])
+    sel_t = torch.from_numpy(sel).to(DEV)
+    for name in ("iid", "ascending"):
+        if name == "iid":
+            u = torch.randint(-(1 << 31), 1 << 31, (ns,), dtype=torch.int32, device=DEV,
+                              generator=gen)
+            mode = api.SAMPLE_1D
+        else:
+            u = torch.arange(ns, dtype=torch.int64, device=DEV).to(torch.int32)  # 0, 1, 2, ...
+            mode = api.SAMPLE_1D | api.SAMPLE_COHERENT
+        idx, pos = api.rtf_sample(f, u, mode=mode)
+        torch.cuda.synchronize()
+        f.check_status()
+        us = u[sel_t].cpu().numpy().view(np.uint32)
+        ridx, rpos = orc.sample(ref.C, us)
+        check_samples(idx[sel_t], pos[sel_t], ridx, rpos)
+        del u, idx, pos
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [1, 777, 40000])
+def test_guide_tables_much_larger_than_n(n):
+    """2^22 cells over few weights: long runs of cells without keys take the
+    interval of the last key before them (the carry-forward over many tiles)."""
+    w = W.lognormal_weights(n, seed=94 + n, sigma=3.0)
+    f, ref = build_and_check(w, 22)
+    u = W.iid_u32(1 << 16, seed=95)
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
+    ridx, rpos = orc.sample(ref.C, u)
+    check_samples(idx, pos, ridx, rpos)
