@@ -453,7 +453,7 @@ struct BinPos {
   }
   __device__ __forceinline__ float pos(uint64_t d, uint32_t r) const {
     const bool small = (d >> 32) == 0;
-    const float num = small ? u64_to_f32((d << 32) | r) : u64_to_f32(d);
+    const float num = u64_to_f32(small ? ((d << 32) | r) : d);
     const float den = small ? den_a : den_b;
     const float rcp = small ? rcp_a : rcp_b;
     float p = num * rcp;

@@ -81,14 +81,11 @@ __device__ __forceinline__ void scale_sample(uint32_t u, uint64_t T, uint64_t& t
 // reciprocal estimate refined by one fused residual step: within about 1.5 ulp
 // of the exact value.  The result is clamped below 1.
 __device__ __forceinline__ float in_bin_position(uint64_t d, uint32_t r, uint64_t q) {
-  float num, den;
-  if ((d >> 32) == 0) {
-    num = u64_to_f32((d << 32) | r);
-    den = u64_to_f32(q) * 4294967296.0f;
-  } else {
-    num = u64_to_f32(d);
-    den = u64_to_f32(q);
-  }
+  // the integer is chosen before its one conversion (the same value either way)
+  const bool small = (d >> 32) == 0;
+  const float num = u64_to_f32(small ? ((d << 32) | r) : d);
+  const float qf = u64_to_f32(q);
+  const float den = small ? qf * 4294967296.0f : qf;
   float rcp;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rcp) : "f"(den));
   float p = num * rcp;
