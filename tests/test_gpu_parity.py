@@ -786,3 +786,28 @@ def test_guide_tables_much_larger_than_n(n):
     idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
     ridx, rpos = orc.sample(ref.C, u)
     check_samples(idx, pos, ridx, rpos)
+
+
+def test_build_past_4gb_of_records():
+    """n = 2^29 + 3 weights, 2^24 cells (8 GB of node records, 512 MB of
+    guide records): the CDF at sampled elements, T, and 2^16 sampled indices
+    and positions against the oracle's exact CDF."""
+    n = (1 << 29) + 3
+    rng = np.random.default_rng(96)
+    w = np.exp(rng.standard_normal(n, dtype=np.float32) * np.float32(2.0)).astype(np.float32)
+    f = api.rtf_build(to_dev(w), 24)
+    torch.cuda.synchronize()
+    f.check_status()
+    C = orc.cdf(orc.quantize(w, orc.scale(w)))
+    sel = np.concatenate([np.arange(2048), n - 2048 + np.arange(2048),
+                          rng.integers(2048, n - 2048, 4096)])
+    got = f.cdf()[torch.from_numpy(sel).to(DEV)].cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, C[sel]), "CDF"
+    assert int(f.dist_table()[0, 3].item()) & ((1 << 64) - 1) == int(C[-1]), "T"
+    u = W.iid_u32(1 << 16, seed=97)
+    u[:2] = [0, 0xFFFFFFFF]
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
+    ridx, rpos = orc.sample(C, u)
+    check_samples(idx, pos, ridx, rpos)
+    del f
+    torch.cuda.empty_cache()

@@ -154,3 +154,39 @@ def test_quad_full_size_equals_binary():
         idx, pos = api.rtf_sample_quad(f, quad, ud, mode=mode)
         i2, p2 = api.rtf_sample(f, ud)
         assert torch.equal(idx, i2) and torch.equal(pos.view(torch.int32), p2.view(torch.int32))
+
+
+def test_quad_coherent_hint_and_2d_load_counts():
+    """The coherence hint only widens the 4-ary sampler's grid (same bits);
+    in 2-D the load counts come as (row, column) pairs, each at least the
+    guide record, and equal the 1-D counts of the marginal and of each row."""
+    w = W.lognormal_weights(300000, seed=41, sigma=2.0)
+    f = api.rtf_build(to_dev(w), 16)
+    quad = api.rtf_build_quad(f)
+    u = np.sort(W.iid_u32(1 << 20, seed=42))
+    ud = api.u32_tensor(u, DEV)
+    i1, p1 = api.rtf_sample_quad(f, quad, ud)
+    i2, p2 = api.rtf_sample_quad(f, quad, ud, mode=api.SAMPLE_1D | api.SAMPLE_COHERENT)
+    assert torch.equal(i1, i2) and torch.equal(p1.view(torch.int32), p2.view(torch.int32))
+
+    H, Wd = 64, 96
+    lum = W.env_map(H, Wd, seed=43)
+    f2 = api.rtf_build_batched(to_dev(lum.reshape(-1)), [Wd] * H + [H], [5] * H + [4], marginal=True)
+    q2 = api.rtf_build_quad(f2)
+    ns = 4099
+    uu = W.iid_u32(2 * ns, seed=44)
+    loads = torch.empty((ns, 2), dtype=torch.int32, device=DEV)
+    idx, pos = api.rtf_sample_quad(f2, q2, api.u32_tensor(uu, DEV), mode=api.SAMPLE_2D,
+                                   loads_out=loads)
+    torch.cuda.synchronize()
+    f2.check_status()
+    i_ref, p_ref = api.rtf_sample(f2, api.u32_tensor(uu, DEV), mode=api.SAMPLE_2D)
+    assert torch.equal(idx, i_ref) and torch.equal(pos.view(torch.int32), p_ref.view(torch.int32))
+    lg = loads.cpu().numpy()
+    assert (lg >= 1).all()
+    # the row counts equal those of a 1-D descent through the marginal alone
+    rows = np.full(ns, H, np.int32)  # the marginal is the last distribution
+    lrow = torch.empty(ns, dtype=torch.int32, device=DEV)
+    api.rtf_sample_quad(f2, q2, api.u32_tensor(uu[0::2].copy(), DEV), dist_id=to_dev(rows),
+                        loads_out=lrow)
+    assert np.array_equal(lrow.cpu().numpy(), lg[:, 0])
