@@ -207,23 +207,33 @@ __global__ void __launch_bounds__(kScanThreads)
 
   const int64_t tile = blockIdx.x;
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, Nw);
-  if (threadIdx.x == 0) {
-    dfirst_s = SEG ? find_dist(dists, 0, Dw - 1, t0) : 0;
-    meta_s = 0;
-  }
-  const int wo = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
-  const int dfirst = dfirst_s;
 
   if (!SEG) {
-    // one distribution: the tile's sum of q; the last tile also holds the
-    // distribution's end (finished here when the tile is also the first)
+    // one distribution: the tile's sum of q (weights read straight from
+    // global memory, 16-byte vectors where aligned); the last tile also
+    // holds the distribution's end (finished here when the tile is also the
+    // first)
     const int S = dist_scale(dists[0], dmax, 0, n_shared);
-    const int l0 = threadIdx.x * kScanPer;
+    const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
+    float wv[kScanPer];
+    if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w + e0) & 15) == 0) {
+#pragma unroll
+      for (int h = 0; h < kScanPer / 4; ++h) {
+        const float4 x = __ldcs(reinterpret_cast<const float4*>(w + e0) + h);
+        wv[4 * h] = x.x;
+        wv[4 * h + 1] = x.y;
+        wv[4 * h + 2] = x.z;
+        wv[4 * h + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < t1 ? w[e0 + k] : 0.0f;
+    }
     uint64_t run = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-      if (t0 + l0 + k < t1) {
-        const uint32_t b = weight_bits(wsm[wo + l0 + k]);
+      if (e0 + k < t1) {
+        const uint32_t b = weight_bits(wv[k]);
         run += weight_bad(b) ? 0ull : quantize_bits(b, S);
       }
     }
@@ -250,6 +260,13 @@ __global__ void __launch_bounds__(kScanThreads)
     }
     return;
   }
+
+  if (threadIdx.x == 0) {
+    dfirst_s = find_dist(dists, 0, Dw - 1, t0);
+    meta_s = 0;
+  }
+  const int wo = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
+  const int dfirst = dfirst_s;
 
   // per-thread run of kScanPer consecutive weights
   const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
