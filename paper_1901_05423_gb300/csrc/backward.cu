@@ -105,7 +105,19 @@ __device__ __forceinline__ void scatter_merge(float2* acc, int64_t j, float va, 
     }
   }
   const bool tail = (lane == 31) || (((heads >> (lane + 1)) & 1u) != 0);
-  if (tail && valid) atomicAdd(acc + j, make_float2(va, vb));
+  if (tail && valid) {
+    // the per-bin sums (8 bytes per bin, about the size of L2 at 2^24 bins)
+    // are added with an L2 evict-last policy while the sample stream passes
+    // through with evict-first loads, so that the sums stay resident: 2^28
+    // samples into 2^24 bins, backward 3.71 -> 3.14 ms on GB300 (a plain
+    // vector atomic, with or without the default policy: 3.71 ms; fractions
+    // 0.5-1.0 of the policy alike)
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(acc + j), "f"(va),
+                 "f"(vb), "l"(pol)
+                 : "memory");
+  }
 }
 
 // 1-D samples (dist_id NULL -> distribution 0)
