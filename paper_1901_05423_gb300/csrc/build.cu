@@ -27,6 +27,11 @@
 
 namespace rtf {
 
+// The passes before the forest kernel read the weights with plain loads, not
+// streaming ones, so that the forest kernel's third read of them (64 MB at
+// n = 2^24) finds them in L2: the build 0.419 -> 0.403 ms on GB300.
+__device__ __forceinline__ float4 ld_weights4(const float4* p) { return __ldg(p); }
+
 // ---------------------------------------------------------------------------
 // init
 // ---------------------------------------------------------------------------
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(kScaleThreads)
       const float4* p = reinterpret_cast<const float4*>(w + e0);
 #pragma unroll
       for (int k = 0; k < kScalePer / 4; ++k) {
-        float4 v = __ldcs(p + k);
+        float4 v = ld_weights4(p + k);
         uint32_t b0 = weight_bits(v.x), b1 = weight_bits(v.y), b2 = weight_bits(v.z),
                  b3 = weight_bits(v.w);
         bad |= weight_bad(b0) | weight_bad(b1) | weight_bad(b2) | weight_bad(b3);
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kScanThreads)
     if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w + e0) & 15) == 0) {
 #pragma unroll
       for (int h = 0; h < kScanPer / 4; ++h) {
-        const float4 x = __ldcs(reinterpret_cast<const float4*>(w + e0) + h);
+        const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
         wv[4 * h] = x.x;
         wv[4 * h + 1] = x.y;
         wv[4 * h + 2] = x.z;
