@@ -34,9 +34,12 @@ N_W = 1 << 24
 M_BITS = 20
 N_S = 1 << 28
 # kernels of this library per step: build 7 (init_dists, scale, tile_sum,
-# tile_scan, forest, forest_merge, guide), sampling 2, backward 3 (scatter,
-# bin_total, suffix)
-LAUNCHES_PER_STEP = 12
+# tile_scan, forest, forest_merge, guide), sampling 2, backward 4 (scatter in
+# two passes over the halves of the 2^24 bins, bin_total, suffix)
+LAUNCHES_PER_STEP = 13
+# with --streams 3 the i.i.d. set is sampled in ACC_CHUNKS chunks and each
+# chunk's terms added by one scatter pass (2^25 samples: under 4 per bin)
+LAUNCHES_PER_STEP_ACC = 7 + 1 + 8 + 8 + 2
 
 
 # DRAM bytes per unit measured by ncu at full size (dram__bytes_read.sum +
@@ -497,7 +500,7 @@ def gpu_arm(args):
         "e2e": {"value": job_throughput(world, 2 * N_S, max_over_ranks(e2e_ms, dist, dev)),
                 "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": (LAUNCHES_PER_STEP + (2 * (ACC_CHUNKS - 1) if args.streams == 3 else 0))
+        "gpu_launches": (LAUNCHES_PER_STEP_ACC if args.streams == 3 else LAUNCHES_PER_STEP)
                         * args.steps,
         "clocks": clk.summary(),
     }

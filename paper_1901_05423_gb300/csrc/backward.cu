@@ -120,11 +120,13 @@ __device__ __forceinline__ void scatter_merge(float2* acc, int64_t j, float va, 
   }
 }
 
-// 1-D samples (dist_id NULL -> distribution 0)
+// 1-D samples (dist_id NULL -> distribution 0); bins outside [jlo, jhi) are
+// left to another pass.
 __global__ void __launch_bounds__(kBwThreads)
     scatter_1d_kernel(const rtf_dist* __restrict__ dists, int D, const int32_t* __restrict__ dist_id,
                       const int32_t* __restrict__ idx, const float* __restrict__ pos,
-                      const float* __restrict__ gpos, int64_t count, float2* acc) {
+                      const float* __restrict__ gpos, int64_t count, float2* acc,
+                      int64_t jlo, int64_t jhi) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t iters = (count + stride - 1) / stride;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(kBwThreads)
           n = dists[d].n;
         }
       }
-      valid = valid && i >= 0 && (int64_t)i < n;
+      valid = valid && i >= 0 && (int64_t)i < n && off + i >= jlo && off + i < jhi;
       if (valid) {
         j = off + i;
         const float g = __ldcs(gpos + s);
@@ -607,6 +609,27 @@ static int bw_sms() {
 
 size_t backward_ws_bytes(int64_t N, int32_t D) { return bw_layout(N, D).total; }
 
+static int64_t bw_l2_bytes() {
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  return l2 > 0 ? l2 : (int64_t(126) << 20);
+}
+
+// Passes of the 1-D scatter over the samples, each adding into one half of
+// the bins.  When the per-bin sums (8 bytes per bin) exceed 3/4 of L2 the
+// passing sample stream evicts them; two passes keep each half resident at the
+// price of reading the samples twice, which pays with at least 4 samples per
+// bin.  2^28 samples on GB300 (L2 135.5 MB), one pass -> two passes:
+// 2^23 bins 1.90 -> 2.33 ms (so one pass there), 2^24 bins 3.17 -> 2.54 ms,
+// 2^25 bins 6.11 -> 4.01 ms; 2^27 tagged samples into 1.19e8 bins (about one
+// per bin) 6.97 -> 7.03 ms (so one pass there); three passes at 2^24 bins
+// 3.48 ms.
+static int scatter_passes(int64_t N, int64_t count) {
+  const int64_t sums = N * (int64_t)sizeof(float2);
+  return (4 * sums > 3 * bw_l2_bytes() && count >= 4 * N) ? 2 : 1;
+}
+
 // The backward in three steps: clear the per-bin sums, add the samples' terms
 // (any number of times), turn the sums into the gradient.
 struct BwPtrs {
@@ -640,9 +663,13 @@ cudaError_t launch_backward_accumulate(const rtf_forest* f, const int32_t* dist_
     scatter_2d_kernel<<<(unsigned)blocks, kBwThreads, 0, st>>>(
         f->dists, D, reinterpret_cast<const int2*>(idx), reinterpret_cast<const float2*>(pos),
         reinterpret_cast<const float2*>(gpos), count, p.acc);
-  else
-    scatter_1d_kernel<<<(unsigned)blocks, kBwThreads, 0, st>>>(f->dists, D, dist_id, idx, pos,
-                                                               gpos, count, p.acc);
+  else {
+    const int64_t N = f->num_elems;
+    const int passes = scatter_passes(N, count);
+    for (int k = 0; k < passes; ++k)
+      scatter_1d_kernel<<<(unsigned)blocks, kBwThreads, 0, st>>>(
+          f->dists, D, dist_id, idx, pos, gpos, count, p.acc, N * k / passes, N * (k + 1) / passes);
+  }
   return cudaGetLastError();
 }
 

@@ -84,6 +84,34 @@ def test_backward_config_full():
     assert rel_err(gw, gref) <= TOL
 
 
+def test_backward_two_pass_scatter():
+    """2^26 samples into 2^24 bins, lognormal(0, 2): the per-bin sums (128 MiB)
+    exceed 3/4 of the L2 with 4 samples per bin, so the scatter adds them in
+    two passes over the halves of the bins, as in the benchmark's backward."""
+    n, n_s, m = 1 << 24, 1 << 26, 20
+    w = W.lognormal_weights(n, seed=30, sigma=2.0)
+    u = W.iid_u32(n_s, seed=31)
+    g = W.normal_f32(n_s, seed=32)
+    wd = to_dev(w)
+    f = api.rtf_build(wd, m)
+    ud = api.u32_tensor(u, DEV)
+    idx, pos = api.rtf_sample(f, ud)
+    gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, to_dev(g))
+    torch.cuda.synchronize()
+    f.check_status()
+    # the oracle takes the same samples in ascending order (the gradient is a
+    # sum over the samples; sorted, its searches stay in cache)
+    key = (u.astype(np.uint64) << np.uint64(32)) | np.arange(n_s, dtype=np.uint64)
+    key.sort()
+    order = (key & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    us, gs = u[order], g[order]
+    ref = orc.build(w, 1 << m)
+    ridx, _ = orc.sample(ref.C, us)
+    assert np.array_equal(idx.cpu().numpy()[order], ridx)
+    gref = orc.grad(w, us, ridx, gs)
+    assert rel_err(gw.cpu().numpy(), gref) <= TOL
+
+
 def test_backward_sorted_samples_merge_runs():
     """Sorted samples put long runs of equal bins inside a warp."""
     n, n_s, m = 5000, 1 << 20, 10
