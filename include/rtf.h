@@ -453,6 +453,12 @@ rtf_status rtf_sample_backward(const rtf_forest *f, const float *w,
  * The calls on one workspace must be ordered (one stream, or events); the
  * workspace holds the sums between them.  Summation order differs between
  * splits, so results agree to float rounding, not bit for bit.
+ *
+ * Speed: for 1-D samples whose per-bin sums (8 bytes per bin) exceed 3/4 of
+ * the L2 cache, an accumulate call that brings at least 4 samples per bin
+ * reads its samples twice, adding into one half of the bins per pass so that
+ * the sums stay in L2 (2^28 samples into 2^24 bins on GB300: 2.54 ms against
+ * 3.17 ms in one pass); smaller calls take one pass.
  */
 rtf_status rtf_backward_begin(const rtf_forest *f, void *ws, size_t ws_bytes,
                               void *stream);
