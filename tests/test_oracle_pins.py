@@ -514,6 +514,43 @@ def test_env_map_marginal_is_row_totals_and_stratified():
     assert np.all((pc >= 0) & (pc <= 1)) and np.all((pr >= 0) & (pr <= 1))
 
 
+def test_env_sampling_equals_definition_brute_force():
+    """Component-wise 2-D sampling (Sec. 5) against its definition in Python
+    integers: the shared scale from the largest exponent of the whole map, the
+    row as the largest index whose marginal prefix sum is at most
+    floor(u1 T / 2^32), the column likewise in that row with u2 and the row's
+    total, and both positions as exact rationals."""
+    rng = np.random.default_rng(21)
+    H, W = 5, 7
+    lum = np.exp(rng.normal(0, 1.5, (H, W))).astype(np.float32)
+    lum[1, 3] = 0.0  # a zero-width bin inside a row
+    lum[3, 0] = 0.0  # and one at a row's start
+    rows, marg = o.build_env(lum, 2, 3)
+    B = 62 - math.ceil(math.log2(H * W))
+    e_max = max(math.frexp(float(x))[1] - 1 for x in lum.reshape(-1) if x > 0)
+    S = B - 1 - e_max
+    q = [[math.floor(Fraction(float(x)) * 2 ** S) for x in lum[r]] for r in range(H)]
+    R = [sum(row) for row in q]
+    T = sum(R)
+    u1 = rng.integers(0, TWO32, 3000, dtype=np.uint64).astype(np.uint32)
+    u2 = rng.integers(0, TWO32, 3000, dtype=np.uint64).astype(np.uint32)
+    u1[:4] = [0, TWO32 - 1, 0, TWO32 - 1]
+    u2[:4] = [0, 0, TWO32 - 1, TWO32 - 1]
+    r, c, pr, pc = o.sample_env(rows, marg, u1, u2)
+    for k in range(u1.size):
+        a, b = int(u1[k]), int(u2[k])
+        t1 = (a * T) >> 32
+        rr = max(i for i in range(H) if sum(R[:i]) <= t1)
+        assert r[k] == rr
+        t2 = (b * R[rr]) >> 32
+        cc = max(j for j in range(W) if sum(q[rr][:j]) <= t2)
+        assert c[k] == cc
+        xr = Fraction(a * T - sum(R[:rr]) * TWO32, R[rr] * TWO32)
+        xc = Fraction(b * R[rr] - sum(q[rr][:cc]) * TWO32, q[rr][cc] * TWO32)
+        assert 0 <= xr < 1 and 0 <= xc < 1
+        assert abs(pr[k] - float(xr)) <= 1e-15 and abs(pc[k] - float(xc)) <= 1e-15
+
+
 def test_batched_equals_independent_builds():
     rng = np.random.default_rng(13)
     sizes = [1, 7, 64, 300]
