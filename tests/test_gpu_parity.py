@@ -788,6 +788,37 @@ def test_guide_tables_much_larger_than_n(n):
     check_samples(idx, pos, ridx, rpos)
 
 
+def test_maximum_guide_bits():
+    """m = 30, the largest table the interface accepts (2^30 cells of 4 u-units:
+    36 GB of guide entries and records) over 40000 lognormal(0, 3) weights:
+    samples through the whole path against the oracle's inverse CDF, and
+    sampled guide entries against their definition: negative exactly when one
+    interval covers the cell (the same bin at its first and last u), and then
+    that interval."""
+    n, m = 40000, 30
+    w = W.lognormal_weights(n, seed=98, sigma=3.0)
+    f = api.rtf_build(to_dev(w), m)
+    torch.cuda.synchronize()
+    f.check_status()
+    C = orc.cdf(orc.quantize(w, orc.scale(w)))
+    u = W.iid_u32(1 << 18, seed=99)
+    u[:2] = [0, 0xFFFFFFFF]
+    idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV))
+    ridx, rpos = orc.sample(C, u)
+    check_samples(idx, pos, ridx, rpos)
+    rng = np.random.default_rng(100)
+    cells = np.concatenate([np.arange(64), (1 << m) - 64 + np.arange(64),
+                            rng.integers(0, 1 << m, 1 << 16)]).astype(np.int64)
+    got = f.guide[torch.from_numpy(cells).to(DEV)].cpu().numpy()
+    first, _ = orc.sample(C, (cells << (32 - m)).astype(np.uint32))
+    last, _ = orc.sample(C, ((cells << (32 - m)) + (1 << (32 - m)) - 1).astype(np.uint32))
+    covered = first == last
+    assert np.array_equal(got < 0, covered)
+    assert np.array_equal(~got[covered], first[covered])
+    del f
+    torch.cuda.empty_cache()
+
+
 def test_build_past_4gb_of_records():
     """n = 2^29 + 3 weights, 2^24 cells (8 GB of node records, 512 MB of
     guide records): the CDF at sampled elements, T, and 2^16 sampled indices
