@@ -78,6 +78,35 @@ def test_backward_single_bin_is_zero():
     assert abs(float(gw.item())) <= 1e-5 * float(np.abs(g).sum())
 
 
+def test_backward_without_samples_is_zero():
+    """No samples: every per-bin sum is zero and so is every element of the
+    gradient (output buffers pre-filled with NaN), for 1-D, 2-D and an
+    accumulator that received no batch; sampling no samples is a no-op."""
+    w = W.lognormal_weights(3000, seed=40, sigma=1.0)
+    wd = to_dev(w)
+    f = api.rtf_build(wd, 8)
+    eu = api.u32_tensor(np.zeros(0, np.uint32), DEV)
+    idx, pos = api.rtf_sample(f, eu)
+    assert idx.numel() == 0 and pos.numel() == 0
+    ef = torch.empty(0, dtype=torch.float32, device=DEV)
+    gw = torch.full_like(wd, float("nan"))
+    api.rtf_sample_backward(f, wd, eu, None, idx, pos, ef, grad_w=gw)
+    acc = api.GradientAccumulator(f).begin()
+    gw2 = acc.finish(wd, torch.full_like(wd, float("nan")))
+    H, Wd = 8, 16
+    lum = to_dev(W.env_map(H, Wd, seed=41).reshape(-1))
+    fe = api.rtf_build_batched(lum, [Wd] * H + [H], [4] * (H + 1), marginal=True)
+    e2 = torch.empty((0, 2), dtype=torch.int32, device=DEV)
+    gw3 = torch.full_like(lum, float("nan"))
+    api.rtf_sample_backward(fe, lum, eu, None, e2, e2.float(), e2.float(), mode=api.SAMPLE_2D,
+                            grad_w=gw3)
+    torch.cuda.synchronize()
+    f.check_status()
+    fe.check_status()
+    for g in (gw, gw2, gw3):
+        assert torch.equal(g, torch.zeros_like(g))
+
+
 def test_backward_config_full():
     """n = 2^20 lognormal(0, 1), 2^24 uniform samples, dL/dx ~ N(0, 1)."""
     gw, gref = run_1d(1 << 20, 1 << 24, 18, seed=10)
