@@ -423,6 +423,52 @@ def test_guide_single_interval_brute_force():
                 assert st.guide[g] == first[0]
 
 
+def topdown_visits(K, cell, M, u):
+    """Node visits of Algorithm 2 for sample u, from the top-down definition
+    of the cell's tree: none when one interval covers the sample's cell (no key
+    in it, or all its keys at the cell's start), else the cell's root (whose
+    left child is the interval before the cell's first key) and one inner node
+    per bisection that isolates the sample's interval."""
+    g = (u * M) >> 32
+    idx = [j for j in range(len(cell)) if int(cell[j]) == g]
+    start = -((-g * TWO32) // M)  # smallest u of cell g
+    if not idx or all(int(K[j]) == start for j in idx):
+        return 0
+    a, b = idx[0], idx[-1]
+    if u < int(K[a]):
+        return 1
+    lo, hi, visits = a, b, 1
+    while lo < hi:
+        best, kb = -1, None
+        for k in range(lo, hi):
+            d = bitlen(int(K[k]) ^ int(K[k + 1]))
+            if d >= best:
+                best, kb = d, k
+        visits += 1
+        if u < int(K[kb + 1]):
+            hi = kb
+        else:
+            lo = kb + 1
+    return visits
+
+
+def test_descent_steps_equal_topdown_depth():
+    """The load counts behind Table 1: visits of Algorithm 2 on the oracle's
+    structure equal the depth of the sample's interval in the top-down tree of
+    its cell (0 for a covered cell, 1 for the interval left of the cell's first
+    key), at every key, key - 1 and grid point."""
+    for w, M, st in forest_cases(17, 150):
+        K, cell = o.keys(st.C, M)
+        us = set(grid_samples(6))
+        for k in K[:-1] if len(K) > len(cell) else K:
+            for d in (-1, 0, 1):
+                if 0 <= int(k) + d < TWO32:
+                    us.add(int(k) + d)
+        for u in sorted(us):
+            assert o.descend_steps(st.guide, st.nodes, K, M, u) == topdown_visits(K, cell, M, u), \
+                (w.tolist(), M, u)
+
+
 def test_descent_depth_bound_power_of_two_cells():
     """With 2^m cells, in-cell keys differ only in their low 32-m bits, so a
     reachable path visits at most 1 + (32 - m) nodes."""
