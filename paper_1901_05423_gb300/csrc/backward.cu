@@ -620,11 +620,11 @@ static int64_t bw_l2_bytes() {
 // the bins.  When the per-bin sums (8 bytes per bin) exceed 3/4 of L2 the
 // passing sample stream evicts them; two passes keep each half resident at the
 // price of reading the samples twice, which pays with at least 4 samples per
-// bin.  2^28 samples on GB300 (L2 135.5 MB), one pass -> two passes:
-// 2^23 bins 1.90 -> 2.33 ms (so one pass there), 2^24 bins 3.17 -> 2.54 ms,
-// 2^25 bins 6.11 -> 4.01 ms; 2^27 tagged samples into 1.19e8 bins (about one
-// per bin) 6.97 -> 7.03 ms (so one pass there); three passes at 2^24 bins
-// 3.48 ms.
+// bin.  The whole backward of 2^28 samples on GB300 (L2 135.5 MB), one pass ->
+// two passes: 2^23 bins 1.90 -> 2.33 ms (so one pass there), 2^24 bins 3.17 ->
+// 2.54 ms, 2^25 bins 6.11 -> 4.01 ms; of 2^27 tagged samples into 1.19e8 bins
+// (about one per bin) 6.97 -> 7.03 ms (so one pass there); three passes at
+// 2^24 bins 3.48 ms.
 static int scatter_passes(int64_t N, int64_t count) {
   const int64_t sums = N * (int64_t)sizeof(float2);
   return (4 * sums > 3 * bw_l2_bytes() && count >= 4 * N) ? 2 : 1;
