@@ -35,8 +35,19 @@
 //   orc_quad / orc_descend_quad          - the 4-ary descent equals orc_index
 //       for every u of a grid; its record count is ceil((v - 1) / 2) for v
 //       binary visits of Algorithm 2; record splits ascend in key order.
-//   orc_grad                             - central finite differences of an
+//   orc_descend / orc_descend_steps      - Algorithm 2 equals orc_index for
+//       every u of a grid; its visit count equals the depth of the sample's
+//       interval in the top-down tree of its cell; at most 1 + (32 - m)
+//       visits with 2^m cells.
+//   orc_grad / orc_grad64                - central finite differences of an
 //       independent fp64 relaxed forward; n = 1 gives zero; two-bin closed form.
+//   orc_relaxed_position                 - equals an independent fp64
+//       restatement of x = (xi W - C_i) / w_i, and the exact position to 1e-6.
+//   The 2-D composition (oracle.py: build_env, sample_env) - marginal equal to
+//       the exact row totals; rows, columns and positions equal their
+//       definition recomputed in Python integers.
+//   Table 1's printed statistics         - parity unpinned: the paper gives
+//       neither n, the table size nor the "4 spikes" density.
 
 #include <algorithm>
 #include <cmath>
