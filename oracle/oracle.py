@@ -16,7 +16,11 @@ Sampling of Discrete or Piecewise Constant Probability Distributions":
 * Algorithm 2 (``descend``), and over 4-ary records that collapse two binary
   levels (``quad``, ``descend_quad``; the section on k-ary trees);
 * the 2-D component-wise scheme of Sec. 5 (``build_env``, ``sample_env``);
-* the fp64 gradient of the in-bin position (``grad``; not in the paper).
+* the fp64 gradient of the in-bin position (``grad``, ``grad_env``; not in the
+  paper): the gradient of the computed forward x = (xi T - C_i) / q_i with the
+  floor of the quantisation passed straight through, i.e. the relaxation
+  x = (xi W' - C'_i) / w'_i differentiated at the quantised weights
+  w' = floor(w 2^S) 2^-S.
 
 Each wrapper names the C function it calls; the citations are in the C file.
 """
@@ -80,7 +84,8 @@ def _load():
             "orc_descend_quad": (i64, [P, P, P, P, P, i64, ctypes.c_uint32, P]),
             "orc_build": (ctypes.c_int, [P, i64, i64, i64, P, P, P, P]),
             "orc_build_int": (ctypes.c_int, [P, i64, i64, P, P, P]),
-            "orc_grad": (None, [P, i64, P, P, P, i64, P]),
+            "orc_grad_q": (None, [P, i64, i32, P, P, P, i64, P]),
+            "orc_quantized_weights": (None, [P, i64, i32, P]),
             "orc_grad64": (None, [P, i64, P, P, P, i64, P]),
             "orc_relaxed_position": (None, [P, i64, P, P, i64, P]),
         }
@@ -151,14 +156,41 @@ def position(C, u: int, i: int) -> float:
     return float(_load().orc_position(_p(C), C.size - 1, int(u), int(i)))
 
 
-def sample(C, u):
-    """``orc_sample``: (idx int32, pos fp64) for each uint32 sample."""
+def sample(C, u, threads: int = 1):
+    """``orc_sample``: (idx int32, pos fp64) for each uint32 sample.
+
+    With ``threads`` > 1 the samples are cut into that many contiguous chunks,
+    each mapped by one ``orc_sample`` call on its own thread (the samples are
+    independent; ctypes releases the interpreter lock during the call)."""
     C = np.ascontiguousarray(C, dtype=np.uint64)
     u = np.ascontiguousarray(u, dtype=np.uint32)
     idx = np.zeros(u.size, np.int32)
     pos = np.zeros(u.size, np.float64)
-    _load().orc_sample(_p(C), C.size - 1, _p(u), u.size, _p(idx), _p(pos))
+    lib = _load()
+    threads = max(1, min(int(threads), u.size // 4096 or 1))
+    if threads == 1:
+        lib.orc_sample(_p(C), C.size - 1, _p(u), u.size, _p(idx), _p(pos))
+        return idx, pos
+    cuts = np.linspace(0, u.size, threads + 1).astype(np.int64)
+
+    def run(k):
+        a, b = int(cuts[k]), int(cuts[k + 1])
+        lib.orc_sample(_p(C), C.size - 1, _p(u[a:b]), b - a, _p(idx[a:b]), _p(pos[a:b]))
+
+    pool = [threading.Thread(target=run, args=(k,)) for k in range(threads)]
+    for t in pool:
+        t.start()
+    for t in pool:
+        t.join()
     return idx, pos
+
+
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def forest(K, cell) -> np.ndarray:
@@ -312,45 +344,56 @@ def sample_env(rows, marg, u1, u2):
     return r, c, pr, pc
 
 
-def grad(w, u, idx, gx) -> np.ndarray:
-    """``orc_grad``: fp64 dL/dw of the in-bin positions (chain rule)."""
+def quantized_weights(w, S: int) -> np.ndarray:
+    """``orc_quantized_weights``: w' = floor(w 2^S) 2^-S in fp64 (exact)."""
     w = _f32(w)
-    u = np.ascontiguousarray(u, dtype=np.uint32)
-    idx = np.ascontiguousarray(idx, dtype=np.int32)
-    gx = np.ascontiguousarray(gx, dtype=np.float32)
     out = np.zeros(w.size, np.float64)
-    _load().orc_grad(_p(w), w.size, _p(u), _p(idx), _p(gx), u.size, _p(out))
+    _load().orc_quantized_weights(_p(w), w.size, int(S), _p(out))
     return out
 
 
-def grad64(w64, u, idx, gx) -> np.ndarray:
-    """``orc_grad64``: the same gradient for fp64 weights."""
-    w64 = np.ascontiguousarray(w64, dtype=np.float64)
+def grad_q(C, S: int, u, idx, gx) -> np.ndarray:
+    """``orc_grad_q``: fp64 dL/dw of the positions of one distribution given by
+    its integer CDF C[0..n] and scale S (the relaxation at w' = q 2^-S, with x
+    from the exact integers)."""
+    C = np.ascontiguousarray(C, dtype=np.uint64)
     u = np.ascontiguousarray(u, dtype=np.uint32)
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     gx = np.ascontiguousarray(gx, dtype=np.float32)
-    out = np.zeros(w64.size, np.float64)
-    _load().orc_grad64(_p(w64), w64.size, _p(u), _p(idx), _p(gx), u.size, _p(out))
+    n = C.size - 1
+    out = np.zeros(n, np.float64)
+    _load().orc_grad_q(_p(C), n, int(S), _p(u), _p(idx), _p(gx), u.size, _p(out))
     return out
+
+
+def grad(w, u, idx, gx, n_group: int | None = None) -> np.ndarray:
+    """fp64 dL/dw of the in-bin positions of one distribution (``orc_scale``,
+    ``orc_quantize``, ``orc_cdf``, then ``orc_grad_q``)."""
+    w = _f32(w)
+    S = scale(w, n_group)
+    return grad_q(cdf(quantize(w, S)), S, u, idx, gx)
 
 
 def grad_env(lum, u1, u2, r, c, g_row, g_col) -> np.ndarray:
     """Gradient of the 2-D positions (Sec. 5, component-wise) with respect to
     the map: each row's column positions differentiate through that row's
-    weights; the row positions through the marginal, whose relaxed weights are
-    the real row sums R_r, so dL/dR_r is added to every weight of row r."""
+    quantised weights; the row positions through the marginal, whose weights
+    are the exact row totals T_r (in real units T_r 2^-S = sum_c w'(r, c)), so
+    dL/dR_r is added to every weight of row r.  All pixels share one scale."""
     lum = np.ascontiguousarray(lum, dtype=np.float32)
     H, Wd = lum.shape
+    S = scale(lum.reshape(-1), n_group=H * Wd)
     out = np.zeros((H, Wd), np.float64)
-    R = lum.astype(np.float64).sum(axis=1)
-    gR = grad64(R, u1, r, g_row)
+    Crows = [cdf(quantize(lum[r_], S)) for r_ in range(H)]
+    totals = np.array([int(Cr[-1]) for Cr in Crows], np.uint64)
+    gR = grad_q(cdf(totals), S, u1, r, g_row)
     out += gR[:, None]
     order = np.argsort(r, kind="stable")
     rs = r[order]
     bounds = np.searchsorted(rs, np.arange(H + 1))
     for row in np.unique(rs):
         sel = order[bounds[row]:bounds[row + 1]]
-        out[row] += grad(lum[row], u2[sel], c[sel], g_col[sel])
+        out[row] += grad_q(Crows[row], S, u2[sel], c[sel], g_col[sel])
     return out
 
 

@@ -39,10 +39,14 @@
 //       every u of a grid; its visit count equals the depth of the sample's
 //       interval in the top-down tree of its cell; at most 1 + (32 - m)
 //       visits with 2^m cells.
-//   orc_grad / orc_grad64                - central finite differences of an
-//       independent fp64 relaxed forward; n = 1 gives zero; two-bin closed form.
+//   orc_grad_q / orc_grad64              - central finite differences of an
+//       independent fp64 relaxed forward at the quantised weights w' (1-D and
+//       2-D); the relaxation at w' equals the exact position (it is the
+//       function the GPU computes), at the unquantised weights it does not;
+//       n = 1 gives zero; two-bin closed form.
+//   orc_quantized_weights                - exact rationals: w' = floor(w 2^S) 2^-S.
 //   orc_relaxed_position                 - equals an independent fp64
-//       restatement of x = (xi W - C_i) / w_i, and the exact position to 1e-6.
+//       restatement of x = (xi W - C_i) / w_i.
 //   The 2-D composition (oracle.py: build_env, sample_env) - marginal equal to
 //       the exact row totals; rows, columns and positions equal their
 //       definition recomputed in Python integers.
@@ -380,40 +384,58 @@ int orc_build_int(const uint64_t* q, int64_t n, int64_t M, uint64_t* C,
 }
 
 // Gradient of the in-bin position with respect to the weights (not in the
-// paper; the chain rule through the relaxed, real-valued forward
-//   x = (xi W - C_i) / w_i,   W = sum_k w_k,   C_i = sum_{k<i} w_k,
-// with the bin i held fixed at the one the exact pipeline selected).
-// Reverse mode, in fp64: per sample
-//   dL/dW   += g xi / w_i,   dL/dC_i += -g / w_i,   dL/dw_i += -g x / w_i,
-// then W = sum w and C_i = sum_{k<i} w_k give
-//   dL/dw_k = dL/dW + sum_{i>k} dL/dC_i + dL/dw_k(direct).
-void orc_grad(const float* w, int64_t n, const uint32_t* u,
-              const int32_t* idx, const float* gx, int64_t ns, double* grad) {
-  std::vector<double> Creal(n + 1);
-  Creal[0] = 0.0;
-  for (int64_t k = 0; k < n; ++k) Creal[k + 1] = Creal[k] + (double)w[k];
-  double W = Creal[n];
+// paper).  Reading: the gradient of the forward that is actually computed,
+//   x = (xi T - C_i) / q_i,   q_i = floor(w_i 2^S),
+// with the floor of the quantisation passed straight through and the scale S
+// held fixed.  In real units this is the relaxation
+//   x = (xi W' - C'_i) / w'_i,   w'_k = q_k 2^-S,  W' = sum_k w'_k,
+//   C'_i = sum_{k<i} w'_k,
+// differentiated at the quantised weights w' (it equals the computed forward
+// there), with the bin i held fixed at the one the exact pipeline selected.
+// Reverse mode, in fp64, per sample
+//   dL/dW'   += g xi / w'_i,   dL/dC'_i += -g / w'_i,   dL/dw'_i += -g x / w'_i,
+// then W' = sum w' and C'_i = sum_{k<i} w'_k give
+//   dL/dw_k = dL/dW' + sum_{i>k} dL/dC'_i + dL/dw'_k(direct).
+// x is taken from the exact integers (orc_position), not recomputed from real
+// prefix sums: for bins far narrower than the total that recomputation loses
+// most of its digits to cancellation.
+//
+// Input: the integer CDF C[0..n] of the distribution and its scale S (for the
+// marginal of a 2-D map: the CDF of the exact row totals and the map's shared
+// scale, so that w'_r = T_r 2^-S is the real total of row r).
+void orc_grad_q(const uint64_t* C, int64_t n, int32_t S, const uint32_t* u,
+                const int32_t* idx, const float* gx, int64_t ns, double* grad) {
   double dW = 0.0;
   std::vector<double> dC(n, 0.0), dwd(n, 0.0);
   for (int64_t s = 0; s < ns; ++s) {
     int64_t i = idx[s];
+    double wq = std::ldexp((double)(C[i + 1] - C[i]), -S);
     double xi = std::ldexp((double)u[s], -32);
-    double wi = (double)w[i];
-    double x = (xi * W - Creal[i]) / wi;
+    double x = orc_position(C, n, u[s], i);
     double g = (double)gx[s];
-    dW += g * xi / wi;
-    dC[i] += -g / wi;
-    dwd[i] += -g * x / wi;
+    dW += g * xi / wq;
+    dC[i] += -g / wq;
+    dwd[i] += -g * x / wq;
   }
-  double suffix = 0.0;  // sum_{i>k} dL/dC_i
+  double suffix = 0.0;  // sum_{i>k} dL/dC'_i
   for (int64_t k = n - 1; k >= 0; --k) {
     grad[k] = dW + suffix + dwd[k];
     suffix += dC[k];
   }
 }
 
-// Same gradient for fp64 weights (the marginal of a 2-D map, whose relaxed
-// weights are the real row sums R_r = sum_c w(r, c)).
+// The quantised weights in real units, w'_k = floor(w_k 2^S) 2^-S (exact in
+// fp64: q_k has at most 24 significant bits).
+void orc_quantized_weights(const float* w, int64_t n, int32_t S, double* wq) {
+  for (int64_t k = 0; k < n; ++k) {
+    double v = std::ldexp((double)w[k], S);
+    wq[k] = std::ldexp(std::floor(v), -S);
+  }
+}
+
+// The chain rule of orc_grad_q at arbitrary real weights, with x recomputed
+// from them: x = (xi W - C_i) / w_i, W = sum w, C_i = sum_{k<i} w_k.  A
+// statement of the relaxation on its own, for the finite-difference pins.
 void orc_grad64(const double* w, int64_t n, const uint32_t* u, const int32_t* idx,
                 const float* gx, int64_t ns, double* grad) {
   std::vector<double> Creal(n + 1);

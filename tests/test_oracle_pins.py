@@ -622,19 +622,72 @@ def relaxed_forward(w64, u, idx):
     return (xi * C[-1] - C[idx]) / w64[idx]
 
 
-def test_relaxed_forward_matches_exact_position():
+def exact_quantized(w, S):
+    """floor(w 2^S) 2^-S as an exact rational, from the float's own value."""
+    v = Fraction(float(w)) * Fraction(2) ** S
+    return Fraction(math.floor(v)) / Fraction(2) ** S
+
+
+def test_quantized_weights_exact_rational():
+    rng = np.random.default_rng(17)
+    for _ in range(20):
+        n = int(rng.integers(1, 300))
+        w = random_weights(rng, n)
+        S = o.scale(w)
+        wq = o.quantized_weights(w, S)
+        for k in range(n):
+            assert Fraction(float(wq[k])) == exact_quantized(w[k], S)
+
+
+def test_relaxation_at_quantised_weights_is_the_computed_forward():
+    """The gradient's reading: the function differentiated is the relaxation
+    at w' = floor(w 2^S) 2^-S, which equals the exact position the pipeline
+    computes; at the unquantised weights it does not (here a weight whose
+    low bits fall below the grid 2^-S of a distribution with a large
+    weight)."""
     rng = np.random.default_rng(14)
     w = np.exp(rng.normal(0, 1, 200)).astype(np.float32)
     st = o.build(w, 64)
     u = rng.integers(0, TWO32, 2000, dtype=np.uint64).astype(np.uint32)
     idx, pos = o.sample(st.C, u)
-    x = relaxed_forward(w.astype(np.float64), u, idx)
-    x2 = o.relaxed_position(w.astype(np.float64), u, idx)
-    assert np.abs(x - pos).max() < 1e-6
-    assert np.abs(x2 - x).max() < 1e-12
+    wq = o.quantized_weights(w, st.S)
+    assert np.abs(relaxed_forward(wq, u, idx) - pos).max() < 1e-12
+    x2 = o.relaxed_position(wq, u, idx)
+    assert np.abs(x2 - relaxed_forward(wq, u, idx)).max() < 1e-12
+    # n = 2 in a group of 2^30 weights (B = 32), w = (1, 1.75 2^-30): S = 31,
+    # q = (2^31, floor(3.5) = 3), T = 2^31 + 3; the top samples land in bin 1
+    w2 = np.array([1.0, 1.75 * 2.0 ** -30], np.float32)
+    st2 = o.build(w2, 4, n_group=1 << 30)
+    assert st2.S == 31 and int(st2.C[2] - st2.C[1]) == 3
+    u2 = np.array([TWO32 - 1, TWO32 - 3], np.uint32)
+    i2, p2 = o.sample(st2.C, u2)
+    assert (i2 == 1).all()
+    wq2 = o.quantized_weights(w2, st2.S)
+    # the exact position, in rationals, equals the relaxation at w'
+    Tq = int(st2.C[2])
+    for k in range(2):
+        exact = Fraction(int(u2[k]) * Tq - int(st2.C[1]) * TWO32, 3 * TWO32)
+        assert abs(float(exact) - p2[k]) < 1e-15
+    assert np.abs(relaxed_forward(wq2, u2, i2) - p2).max() < 1e-6
+    assert np.abs(relaxed_forward(w2.astype(np.float64), u2, i2) - p2).max() > 0.05
+
+
+def fd_gradient(w64, u, idx, g, h_rel=1e-3):
+    """Central differences of the relaxed forward, weight by weight."""
+    fd = np.zeros(w64.size)
+    for k in range(w64.size):
+        h = h_rel * w64[k]
+        wp, wm = w64.copy(), w64.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd[k] = np.dot(g.astype(np.float64),
+                       (relaxed_forward(wp, u, idx) - relaxed_forward(wm, u, idx)) / (2 * h))
+    return fd
 
 
 def test_gradient_central_differences():
+    """Element by element against central differences of the relaxation at
+    the quantised weights, on samples away from the bin edges."""
     rng = np.random.default_rng(15)
     n = 24
     w = np.exp(rng.normal(0, 1, n)).astype(np.float32)
@@ -645,17 +698,32 @@ def test_gradient_central_differences():
     u, idx = u[keep], idx[keep]
     g = rng.normal(0, 1, u.size).astype(np.float32)
     grad = o.grad(w, u, idx, g)
-    w64 = w.astype(np.float64)
-    fd = np.zeros(n)
-    for k in range(n):
-        h = 1e-3 * w64[k]
-        wp, wm = w64.copy(), w64.copy()
-        wp[k] += h
-        wm[k] -= h
-        xp = relaxed_forward(wp, u, idx)
-        xm = relaxed_forward(wm, u, idx)
-        fd[k] = np.dot(g.astype(np.float64), (xp - xm) / (2 * h))
-    assert np.linalg.norm(grad - fd) <= 1e-5 * np.linalg.norm(fd)
+    fd = fd_gradient(o.quantized_weights(w, st.S), u, idx, g)
+    assert np.all(np.abs(grad - fd) <= 1e-5 * (np.abs(fd) + np.abs(fd).max() * 1e-3))
+
+
+def test_gradient_is_taken_at_the_quantised_weights():
+    """A group of 2^54 weights (B = 8: about 7 significant bits per weight
+    survive the quantisation): the gradient agrees with the differences of the
+    relaxation at w' and not with those at the unquantised weights, so
+    dividing by w instead of w' fails."""
+    rng = np.random.default_rng(18)
+    n, ng = 40, 1 << 54
+    w = np.exp(rng.normal(0, 1, n)).astype(np.float32)
+    st = o.build(w, 16, n_group=ng)
+    wq = o.quantized_weights(w, st.S)
+    assert (wq > 0).all()
+    assert np.abs(wq / w - 1.0).max() > 1e-3
+    u = rng.integers(0, TWO32, 4000, dtype=np.uint64).astype(np.uint32)
+    idx, pos = o.sample(st.C, u)
+    keep = (pos > 0.01) & (pos < 0.99)
+    u, idx = u[keep], idx[keep]
+    g = rng.normal(0, 1, u.size).astype(np.float32)
+    grad = o.grad(w, u, idx, g, n_group=ng)
+    fd_q = fd_gradient(wq, u, idx, g)
+    fd_w = fd_gradient(w.astype(np.float64), u, idx, g)
+    assert np.all(np.abs(grad - fd_q) <= 1e-5 * (np.abs(fd_q) + np.abs(fd_q).max() * 1e-3))
+    assert np.abs(grad - fd_w).max() > 1e-3 * np.abs(fd_w).max()
 
 
 def test_gradient_single_bin_is_zero():
@@ -667,7 +735,8 @@ def test_gradient_single_bin_is_zero():
 
 def test_gradient_two_bins_closed_form():
     """Two bins, one sample in bin 1: x = (xi (w0 + w1) - w0) / w1, so
-    dx/dw0 = (xi - 1) / w1 and dx/dw1 = (xi - x) / w1."""
+    dx/dw0 = (xi - 1) / w1 and dx/dw1 = (xi - x) / w1 (1 and 3 lie on the
+    quantisation grid, so w' = w)."""
     w = np.array([1.0, 3.0], np.float32)
     u = np.array([3 << 30], np.uint32)   # xi = 0.75 -> bin 1 (P_1 = 0.25)
     xi = 0.75
@@ -691,6 +760,9 @@ def relaxed_forward_2d(lum64, u1, u2, r, c):
 
 
 def test_env_gradient_central_differences():
+    """2-D: element by element against central differences of the relaxation
+    at the quantised map (shared scale), whose row sums are the marginal's
+    exact row totals; the relaxation there equals the exact positions."""
     rng = np.random.default_rng(16)
     H, Wd = 5, 7
     lum = np.exp(rng.normal(0, 1, (H, Wd))).astype(np.float32)
@@ -700,19 +772,22 @@ def test_env_gradient_central_differences():
     r, c, pr, pc = o.sample_env(rows, marg, u1, u2)
     keep = (pr > 0.01) & (pr < 0.99) & (pc > 0.01) & (pc < 0.99)
     u1, u2, r, c = u1[keep], u2[keep], r[keep], c[keep]
+    pr, pc = pr[keep], pc[keep]
     gy = rng.normal(0, 1, u1.size).astype(np.float32)
     gx = rng.normal(0, 1, u1.size).astype(np.float32)
     grad = o.grad_env(lum, u1, u2, r, c, gy, gx)
-    lum64 = lum.astype(np.float64)
+    lq = o.quantized_weights(lum.reshape(-1), marg.S).reshape(H, Wd)
+    y0, x0 = relaxed_forward_2d(lq, u1, u2, r, c)
+    assert np.abs(y0 - pr).max() < 1e-12 and np.abs(x0 - pc).max() < 1e-12
     fd = np.zeros((H, Wd))
     for k in range(H):
         for j in range(Wd):
-            h = 1e-3 * lum64[k, j]
-            lp, lm = lum64.copy(), lum64.copy()
+            h = 1e-3 * lq[k, j]
+            lp, lm = lq.copy(), lq.copy()
             lp[k, j] += h
             lm[k, j] -= h
             yp, xp = relaxed_forward_2d(lp, u1, u2, r, c)
             ym, xm = relaxed_forward_2d(lm, u1, u2, r, c)
             fd[k, j] = (np.dot(gy.astype(np.float64), yp - ym) +
                         np.dot(gx.astype(np.float64), xp - xm)) / (2 * h)
-    assert np.linalg.norm(grad - fd) <= 1e-5 * np.linalg.norm(fd)
+    assert np.all(np.abs(grad - fd) <= 1e-5 * (np.abs(fd) + np.abs(fd).max() * 1e-3))
