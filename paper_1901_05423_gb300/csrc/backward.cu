@@ -1,8 +1,11 @@
 // Gradient of the in-bin sample positions with respect to the weights (not in
-// the paper; the adjoint of the relaxed forward x = (xi W - C_i) / w_i with the
-// bin i of each sample held fixed).
+// the paper).  The forward computes x = (xi T - C_i) / q_i on the quantised
+// weights q_i = floor(w_i 2^S); its gradient is taken with the floor passed
+// straight through and the scale S held fixed, i.e. the relaxation
+// x = (xi W' - C'_i) / w'_i at the quantised weights w'_k = q_k 2^-S
+// (W' = sum w', C'_i = sum_{k<i} w'_k), with the bin i of each sample fixed:
 //
-//   dL/dw_k = sum_{i in d} Xi_i / w_i  -  sum_{i > k, i in d} A_i / w_i  -  X_k / w_k
+//   dL/dw_k = sum_{i in d} Xi_i / w'_i  -  sum_{i > k, i in d} A_i / w'_i  -  X_k / w'_k
 //   A_i = sum_{s -> i} g_s,  X_i = sum_{s -> i} g_s x_s,  Xi_i = sum_{s -> i} g_s xi_s.
 //
 // The sample's own xi need not be carried: the position is defined through
@@ -11,14 +14,14 @@
 // Only two sums per bin are accumulated.
 //
 // Kernels:
-//   row_sum_kernel       (2-D) real row totals R_r = sum_c w(r, c), the
-//                        weights of the marginal
+//   row_total_kernel     (2-D) the marginal's weights in real units,
+//                        R'_r = T_r 2^-S (T_r the exact integer row total)
 //   scatter kernels      one 8-byte vector atomic {g, g x} per sample into its
 //                        bin, runs of equal bins inside a warp merged first
-//   bin_total_kernel     G_d = sum_{i in d} Xi_i / w_i per distribution
-//   suffix_kernel        reverse decoupled-lookback scan of A_i / w_i per
+//   bin_total_kernel     G_d = sum_{i in d} Xi_i / w'_i per distribution
+//   suffix_kernel        reverse decoupled-lookback scan of A_i / w'_i per
 //                        distribution (fp32 in the tile, fp64 carry), then
-//                        dL/dw_k = G_d - S_k - X_k / w_k
+//                        dL/dw_k = G_d - S_k - X_k / w'_k
 //   add_row_kernel       (2-D) the marginal's gradient dL/dR_r added to every
 //                        weight of row r
 #include <algorithm>
@@ -40,7 +43,7 @@ struct BwLayout {
   size_t incl;   // double [tiles]   that sum plus everything after it
   size_t ticket; // u32
   size_t zero_end;
-  size_t R;      // float [D]   (2-D: row totals)
+  size_t R;      // float2 [D]  (2-D: row totals as double-floats)
   size_t gradR;  // float [D]   (2-D: gradient of the marginal's weights)
   size_t total;
 };
@@ -56,29 +59,127 @@ __host__ __device__ inline BwLayout bw_layout(int64_t N, int32_t D) {
   L.incl = o; o = align256(o + 8 * (size_t)tiles);
   L.ticket = o; o = align256(o + 256);
   L.zero_end = o;
-  L.R = o; o = align256(o + 4 * (size_t)D);
+  L.R = o; o = align256(o + 8 * (size_t)D);
   L.gradR = o; o = align256(o + 4 * (size_t)D);
   L.total = o;
   return L;
 }
 
-// weight of element e: a row weight, or (2-D) the real total of marginal row e - Nw
-__device__ __forceinline__ float weight_at(const float* w, const float* R, int64_t Nw, int64_t e) {
-  return e < Nw ? w[e] : R[e - Nw];
+// The quantised weight in real units, w' = floor(w 2^S) 2^-S: w with the bits
+// of its significand below 2^-S cleared (exact; 0 when w 2^S < 1).  w >= 0.
+__device__ __forceinline__ float quantized_weight(float w, int S) {
+  const uint32_t b = __float_as_uint(w) & 0x7FFFFFFFu;
+  const uint32_t E = b >> 23;
+  const int lsb = (E ? (int)E : 1) - 150;  // exponent of the significand's last bit
+  const int sh = -S - lsb;                 // significand bits below 2^-S
+  if (sh <= 0) return __uint_as_float(b);
+  if (sh >= 24) return 0.0f;
+  return __uint_as_float(b & ~((1u << sh) - 1u));
 }
 
 // ---------------------------------------------------------------------------
-__global__ void row_sum_kernel(const float* __restrict__ w, const rtf_dist* __restrict__ dists,
-                               int H, float* R) {
-  const int lane = threadIdx.x & 31;
-  const int warps = blockDim.x >> 5;
-  for (int r = blockIdx.x * warps + (threadIdx.x >> 5); r < H; r += gridDim.x * warps) {
-    const int64_t off = dists[r].elem_off, n = dists[r].n;
-    float s = 0.0f;
-    for (int64_t k = lane; k < n; k += 32) s += w[off + k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) R[r] = s;
+// double-float arithmetic
+// ---------------------------------------------------------------------------
+// A value held as the unevaluated sum hi + lo of two floats (about 48
+// significant bits), built from error-free transformations: the sum of two
+// floats together with its exact rounding error (Knuth's TwoSum, The Art of
+// Computer Programming vol. 2, Sec. 4.2.2), and the exact residual of a
+// product or a quotient by one fused multiply-add.  Every step rounds
+// explicitly (__fadd_rn, __fmul_rn, __fmaf_rn) so that the compiler cannot
+// contract it.  Why: the per-bin terms A_i / w'_i span many orders of
+// magnitude (those of the narrowest bins reach 1e5 and more at n = 2^24); in
+// float32 their rounding errors, which the suffix carries to every element
+// left of them, exceed the gradient's relative error bound wherever
+// G - S_k nearly cancels.  fp64 is kept to per-thread and per-tile values (its
+// throughput on this part is low).
+struct dflt {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dflt df_zero() { return dflt{0.0f, 0.0f}; }
+
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return dflt{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ dflt df_sub(dflt a, dflt b) { return df_add(a, dflt{-b.hi, -b.lo}); }
+
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float h = __fadd_rn(p, e);
+  return dflt{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+// x / (yh + yl) with inv ~ 1 / yh: the quotient estimate q, the residual
+// x - q yh (exact) - q yl, and its correction.
+__device__ __forceinline__ dflt df_div(float x, float yh, float yl, float inv) {
+  const float q = __fmul_rn(x, inv);
+  float r = __fmaf_rn(-q, yh, x);
+  r = __fmaf_rn(-q, yl, r);
+  const float c = __fmul_rn(r, inv);
+  const float h = __fadd_rn(q, c);
+  return dflt{h, __fsub_rn(c, __fsub_rn(h, q))};
+}
+
+__device__ __forceinline__ double df_to_double(dflt a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ dflt df_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return dflt{h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ float df_to_float(dflt a) { return __fadd_rn(a.hi, a.lo); }
+
+// An integer below 2^63 as a double-float: the nearest float and the float of
+// the exact remainder.
+__device__ __forceinline__ dflt df_from_u64(uint64_t x) {
+  const float h = __ull2float_rn(x);
+  return dflt{h, __ll2float_rn((int64_t)(x - __float2ull_rn(h)))};
+}
+
+__device__ __forceinline__ dflt df_shfl_down(dflt a, int d) {
+  return dflt{__shfl_down_sync(0xffffffffu, a.hi, d), __shfl_down_sync(0xffffffffu, a.lo, d)};
+}
+
+__device__ __forceinline__ dflt df_shfl_xor(dflt a, int d) {
+  return dflt{__shfl_xor_sync(0xffffffffu, a.hi, d), __shfl_xor_sync(0xffffffffu, a.lo, d)};
+}
+
+// The quantised weight q 2^-S of an integer weight q (a row weight, exact in
+// the high part, or the marginal's row total) as a double-float.
+__device__ __forceinline__ dflt qweight_df(uint64_t q, int S) {
+  const dflt v = df_from_u64(q);
+  return dflt{scalbnf(v.hi, -S), scalbnf(v.lo, -S)};
+}
+
+// {a, b} = {A / w', X / w'} for the per-bin sums {A, X} and the quantised
+// weight w' = wh + wl (zero for an empty bin or a zero weight).
+__device__ __forceinline__ void bin_terms(float2 ax, float wh, float wl, dflt* a, dflt* b) {
+  if ((ax.x != 0.0f || ax.y != 0.0f) && wh != 0.0f) {
+    const float inv = __frcp_rn(wh);
+    *a = df_div(ax.x, wh, wl, inv);
+    *b = df_div(ax.y, wh, wl, inv);
+  } else {
+    *a = df_zero();
+    *b = df_zero();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// R'_r = T_r 2^-S: the marginal's weights in the units of the map's weights,
+// as double-floats {hi, lo}.
+__global__ void row_total_kernel(const rtf_dist* __restrict__ dists, int H, float2* R) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < H; r += gridDim.x * blockDim.x) {
+    const dflt v = qweight_df(dists[r].total, dists[r].scale);
+    R[r] = make_float2(v.hi, v.lo);
   }
 }
 
@@ -192,16 +293,16 @@ __global__ void __launch_bounds__(kBwThreads)
   }
 }
 
-// G_d = sum_{i in d} Xi_i / w_i with Xi_i = (A_i C_i + X_i q_i) / T.
-// Per-thread fp32 runs, then one fp64 atomic per distribution piece (a block
-// inside one distribution reduces first and adds once).
+// G_d = sum_{i in d} Xi_i / w'_i.  With Xi_i = (A_i C_i + X_i q_i) / T and
+// q_i / w'_i = 2^S, each term is a_i c_i + X_i 2^S / T with a_i = A_i / w'_i
+// and c_i = C_i / T, so G_d = sum_i a_i c_i + (2^S / T) sum_i X_i: both sums
+// in double-float per thread, fp64 per distribution piece (one atomic per
+// piece; a block inside one distribution reduces first and adds once).
 __global__ void __launch_bounds__(kBwThreads)
     bin_total_kernel(const float2* __restrict__ acc, const rtf_node* __restrict__ nodes,
-                     const float* __restrict__ w, const float* __restrict__ R,
-                     const rtf_dist* __restrict__ dists, int D, int64_t N, int64_t Nw,
-                     double* G) {
+                     const rtf_dist* __restrict__ dists, int D, int64_t N, double* G) {
   __shared__ int dfirst_s, dlast_s;
-  __shared__ float part[kBwThreads / 32];
+  __shared__ double part[kBwThreads / 32];
   const int64_t t0 = (int64_t)blockIdx.x * kBwTile;
   const int64_t t1 = min(t0 + (int64_t)kBwTile, N);
   if (threadIdx.x == 0) {
@@ -213,63 +314,75 @@ __global__ void __launch_bounds__(kBwThreads)
   const int64_t e0 = t0 + (int64_t)threadIdx.x * kBwPer;
   int d = dfirst;
   if (e0 < t1 && dlast != dfirst) d = find_dist(dists, dfirst, dlast, e0);
-  float run = 0.f;
+  double contrib = 0.0;
   if (e0 < t1) {
     rtf_dist P = dists[d];
     int64_t end = P.elem_off + P.n;
-    float invT = 1.0f / u64_to_f32(P.total);
+    dflt invT = df_from_double(1.0 / (double)P.total);
+    double K = ldexp(1.0, P.scale) / (double)P.total;
+    dflt sac = df_zero(), sx = df_zero();
     uint64_t cnext = nodes[e0].cdf;
     const int64_t e1 = min(e0 + (int64_t)kBwPer, t1);
     for (int64_t e = e0; e < e1; ++e) {
       if (e >= end) {
-        if (dlast != dfirst) atomicAdd(G + d, (double)run);
-        run = 0.f;
+        const double v = df_to_double(sac) + K * df_to_double(sx);
+        if (dlast != dfirst) atomicAdd(G + d, v);
+        sac = df_zero();
+        sx = df_zero();
         ++d;
         P = dists[d];
         end = P.elem_off + P.n;
-        invT = 1.0f / u64_to_f32(P.total);
+        invT = df_from_double(1.0 / (double)P.total);
+        K = ldexp(1.0, P.scale) / (double)P.total;
       }
       const uint64_t c = cnext;
       cnext = (e + 1 < N) ? nodes[e + 1].cdf : 0ull;
       const uint64_t cup = (e + 1 < end) ? cnext : P.total;
       const float2 ax = acc[e];
-      if (ax.x != 0.0f || ax.y != 0.0f) {
-        const float cf = u64_to_f32(c) * invT;
-        const float qf = u64_to_f32(cup - c) * invT;
-        run += (ax.x * cf + ax.y * qf) / weight_at(w, R, Nw, e);
+      const uint64_t q = cup - c;
+      if ((ax.x != 0.0f || ax.y != 0.0f) && q != 0) {
+        const dflt wq = qweight_df(q, P.scale);
+        dflt av, bv;
+        bin_terms(ax, wq.hi, wq.lo, &av, &bv);
+        sac = df_add(sac, df_mul(av, df_mul(df_from_u64(c), invT)));
+        sx = df_add(sx, dflt{ax.y, 0.0f});
       }
     }
+    contrib = df_to_double(sac) + K * df_to_double(sx);
   }
   if (dlast != dfirst) {
-    if (e0 < t1) atomicAdd(G + d, (double)run);
+    if (e0 < t1) atomicAdd(G + d, contrib);
     return;
   }
-  // the whole block lies in one distribution
+  // the whole block lies in one distribution: the warp's sum in double-float,
+  // the block's in fp64
+  dflt v = df_from_double(contrib);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = run;
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = df_to_double(v);
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int k = 0; k < kBwThreads / 32; ++k) t += (double)part[k];
+    for (int k = 0; k < kBwThreads / 32; ++k) t += part[k];
     atomicAdd(G + dfirst, t);
   }
 }
 
-// Reverse segmented scan: S_k = sum_{i > k, same distribution} A_i / w_i, then
+// Reverse segmented scan: S_k = sum_{i > k, same distribution} A_i / w'_i, then
 // the gradient.  Tiles are taken from the end by ticket; each tile publishes
 // the sum of a over its first piece (the part of dist(t0) inside the tile)
 // and, once known, that sum plus everything after it.  The lookback is
-// block-wide: every thread reads one successor's flag per round.
+// block-wide: every thread reads one successor's flag per round.  Terms and
+// sums inside the tile are double-floats, carries fp64.
 __global__ void __launch_bounds__(kBwThreads)
     suffix_kernel(const float2* __restrict__ acc, const float* __restrict__ w,
-                  const float* __restrict__ R, const rtf_dist* __restrict__ dists, int D,
+                  const float2* __restrict__ R, const rtf_dist* __restrict__ dists, int D,
                   int64_t N, int64_t Nw, const double* __restrict__ G, uint32_t* flags,
                   double* carry, double* incl, uint32_t* ticket, float* grad_w, float* gradR,
                   uint32_t* status) {
   __shared__ uint32_t tick_s;
   __shared__ int dfirst_s;
-  __shared__ float ex_s[kBwThreads];
+  __shared__ float exh_s[kBwThreads], exl_s[kBwThreads];
   __shared__ int exf_s[kBwThreads];
   __shared__ int first_prefix_s, first_invalid_s;
   __shared__ double part_s[kBwThreads / 32];
@@ -285,7 +398,7 @@ __global__ void __launch_bounds__(kBwThreads)
   const int64_t e0 = t0 + (int64_t)threadIdx.x * kBwPer;
 
   // per-thread values; tails mark the last element of a distribution
-  float a[kBwPer], b[kBwPer];
+  dflt a[kBwPer], b[kBwPer];
   int dk[kBwPer];
   uint32_t tailmask = 0;
   {
@@ -294,17 +407,23 @@ __global__ void __launch_bounds__(kBwThreads)
 #pragma unroll
     for (int k = 0; k < kBwPer; ++k) {
       const int64_t e = e0 + k;
-      a[k] = 0.f;
-      b[k] = 0.f;
+      a[k] = df_zero();
+      b[k] = df_zero();
       dk[k] = d;
       if (e < t1) {
         while (d + 1 < D && e >= dists[d + 1].elem_off) ++d;
         dk[k] = d;
         const float2 v = acc[e];
         if (v.x != 0.0f || v.y != 0.0f) {
-          const float inv = 1.0f / weight_at(w, R, Nw, e);
-          a[k] = v.x * inv;
-          b[k] = v.y * inv;
+          float wh, wl = 0.0f;
+          if (e < Nw) {
+            wh = quantized_weight(w[e], dists[d].scale);
+          } else {
+            const float2 r2 = R[e - Nw];
+            wh = r2.x;
+            wl = r2.y;
+          }
+          bin_terms(v, wh, wl, &a[k], &b[k]);
         }
         const int64_t end = dists[d].elem_off + dists[d].n;
         if (e + 1 == end) tailmask |= 1u << k;
@@ -313,56 +432,59 @@ __global__ void __launch_bounds__(kBwThreads)
   }
   // thread aggregate continuing leftwards: sum of a from the first element up
   // to the first tail (or the whole run)
-  float tot = 0.f;
+  dflt tot = df_zero();
 #pragma unroll
   for (int k = kBwPer - 1; k >= 0; --k) {
-    if (tailmask & (1u << k)) tot = 0.f;
-    tot += a[k];
+    if (tailmask & (1u << k)) tot = df_zero();
+    tot = df_add(tot, a[k]);
   }
   // segmented inclusive scan over reversed thread order: slot i holds thread
   // n-1-i, so slots run from the right end of the tile to the left
   const int myslot = kBwThreads - 1 - threadIdx.x;
-  ex_s[myslot] = tot;
+  exh_s[myslot] = tot.hi;
+  exl_s[myslot] = tot.lo;
   exf_s[myslot] = tailmask ? 1 : 0;
   __syncthreads();
   {
     const int slot = threadIdx.x;
-    float v = ex_s[slot];
+    dflt v{exh_s[slot], exl_s[slot]};
     int f = exf_s[slot];
     for (int dlt = 1; dlt < kBwThreads; dlt <<= 1) {
-      float pv = 0.f;
+      dflt pv = df_zero();
       int pf = 0;
       if (slot >= dlt) {
-        pv = ex_s[slot - dlt];
+        pv = dflt{exh_s[slot - dlt], exl_s[slot - dlt]};
         pf = exf_s[slot - dlt];
       }
       __syncthreads();
       if (slot >= dlt && !f) {
-        v = pv + v;
+        v = df_add(pv, v);
         f = pf;
       }
-      ex_s[slot] = v;
+      exh_s[slot] = v.hi;
+      exl_s[slot] = v.lo;
       exf_s[slot] = f;
       __syncthreads();
     }
   }
-  float exv = 0.f;
+  dflt exv = df_zero();
   int exf = 0;
   if (myslot > 0) {
-    exv = ex_s[myslot - 1];
+    exv = dflt{exh_s[myslot - 1], exl_s[myslot - 1]};
     exf = exf_s[myslot - 1];
   }
-  const float first_piece = ex_s[kBwThreads - 1];
+  const double first_piece =
+      df_to_double(dflt{exh_s[kBwThreads - 1], exl_s[kBwThreads - 1]});
   const bool first_piece_closed = exf_s[kBwThreads - 1] != 0;  // dist(t0) ends in this tile
   const int dlast_tile = find_dist(dists, dfirst, min(D - 1, dfirst + kBwTile), t1 - 1);
   const bool continues = (dists[dlast_tile].elem_off + dists[dlast_tile].n) > t1;
   if (threadIdx.x == 0) {
-    carry[tile] = (double)first_piece;
-    incl[tile] = (double)first_piece;
+    carry[tile] = first_piece;
+    incl[tile] = first_piece;
     __threadfence();
     atomicExch(flags + tile, first_piece_closed ? 2u : 1u);
   }
-  // block-wide lookback for the incoming carry: sum of a beyond t1 in dist(t1-1)
+  // block-wide lookback for the sum beyond t1 in the distribution of t1 - 1
   double E = 0.0;
   if (continues) {
     int64_t look = tile + 1;
@@ -378,8 +500,8 @@ __global__ void __launch_bounds__(kBwThreads)
       if (fl == 2) atomicMin(&first_prefix_s, (int)threadIdx.x);
       if (fl == 0) atomicMin(&first_invalid_s, (int)threadIdx.x);
       __syncthreads();
-      const int p = first_prefix_s, q = first_invalid_s;
-      if (q < p) {
+      const int pfx = first_prefix_s, inv = first_invalid_s;
+      if (inv < pfx) {
         if (++spins > kSpinLimit) {
           if (threadIdx.x == 0) raise_status(status, RTF_STATUS_TIMEOUT);
           break;
@@ -389,12 +511,12 @@ __global__ void __launch_bounds__(kBwThreads)
         continue;
       }
       __threadfence();
-      double v = 0.0;
-      if ((int)threadIdx.x < p && idx < ntiles) v = *((volatile double*)(carry + idx));
-      if ((int)threadIdx.x == p && idx < ntiles) v = *((volatile double*)(incl + idx));
+      double x = 0.0;
+      if ((int)threadIdx.x < pfx && idx < ntiles) x = *((volatile double*)(carry + idx));
+      if ((int)threadIdx.x == pfx && idx < ntiles) x = *((volatile double*)(incl + idx));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) part_s[threadIdx.x >> 5] = v;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) == 0) part_s[threadIdx.x >> 5] = x;
       __syncthreads();
       if (threadIdx.x == 0) {
         double t = 0.0;
@@ -403,12 +525,12 @@ __global__ void __launch_bounds__(kBwThreads)
       }
       __syncthreads();
       E += E_s;
-      if (p < kBwThreads) break;
+      if (pfx < kBwThreads) break;
       look += kBwThreads;
     }
   }
   if (threadIdx.x == 0 && !first_piece_closed) {
-    incl[tile] = (double)first_piece + E;
+    incl[tile] = first_piece + E;
     __threadfence();
     atomicExch(flags + tile, 2u);
   }
@@ -416,23 +538,23 @@ __global__ void __launch_bounds__(kBwThreads)
   // element results, walking the thread's run from the right: until the first
   // tail the suffix continues past the thread (exclusive value, plus the
   // incoming carry when no tail lies to the right inside the tile)
-  const double after = exf ? (double)exv : (double)exv + E;
-  float inrun = 0.f;
-  float base = (float)(G[dk[kBwPer - 1]] - after);
+  const double after = exf ? df_to_double(exv) : df_to_double(exv) + E;
+  dflt inrun = df_zero();
+  dflt base = df_from_double(G[dk[kBwPer - 1]] - after);
 #pragma unroll
   for (int k = kBwPer - 1; k >= 0; --k) {
     const int64_t e = e0 + k;
     if (e >= t1) continue;
     if (tailmask & (1u << k)) {
-      inrun = 0.f;
-      base = (float)G[dk[k]];
+      inrun = df_zero();
+      base = df_from_double(G[dk[k]]);
     }
-    const float gk = base - inrun - b[k];
+    const float gk = df_to_float(df_sub(df_sub(base, inrun), b[k]));
     if (e < Nw)
       grad_w[e] = gk;
     else
       gradR[e - Nw] = gk;
-    inrun += a[k];
+    inrun = df_add(inrun, a[k]);
   }
 }
 
@@ -441,11 +563,12 @@ __global__ void __launch_bounds__(kBwThreads)
 // arithmetic as suffix_kernel, with the tile scanned by warp shuffles instead
 // of a segmented shared-memory scan and the inputs read as 16-byte vectors.
 __global__ void __launch_bounds__(kBwThreads)
-    suffix_single_kernel(const float2* __restrict__ acc, const float* __restrict__ w, int64_t N,
+    suffix_single_kernel(const float2* __restrict__ acc, const float* __restrict__ w,
+                         const rtf_dist* __restrict__ dists, int64_t N,
                          const double* __restrict__ G, uint32_t* flags, double* carry,
                          double* incl, uint32_t* ticket, float* grad_w, uint32_t* status) {
   __shared__ uint32_t tick_s;
-  __shared__ float wtot_s[kBwThreads / 32];
+  __shared__ dflt wtot_s[kBwThreads / 32];
   __shared__ int first_prefix_s, first_invalid_s;
   __shared__ double part_s[kBwThreads / 32];
   __shared__ double E_s;
@@ -456,71 +579,62 @@ __global__ void __launch_bounds__(kBwThreads)
   const int64_t t0 = tile * kBwTile, t1 = min(t0 + (int64_t)kBwTile, N);
   const int64_t e0 = t0 + (int64_t)threadIdx.x * kBwPer;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int S = dists[0].scale;
 
-  float a[kBwPer], b[kBwPer];
+  dflt a[kBwPer], b[kBwPer];
   if (e0 + kBwPer <= t1) {
     const float4* av = reinterpret_cast<const float4*>(acc + e0);
     const float4* wv = reinterpret_cast<const float4*>(w + e0);
 #pragma unroll
     for (int h = 0; h < kBwPer / 4; ++h) {
       const float4 x0 = av[2 * h], x1 = av[2 * h + 1], ww = wv[h];
-      const float ax[4] = {x0.x, x0.z, x1.x, x1.z}, bx[4] = {x0.y, x0.w, x1.y, x1.w};
+      const float2 ax[4] = {make_float2(x0.x, x0.y), make_float2(x0.z, x0.w),
+                            make_float2(x1.x, x1.y), make_float2(x1.z, x1.w)};
       const float wk[4] = {ww.x, ww.y, ww.z, ww.w};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        a[4 * h + k] = 0.f;
-        b[4 * h + k] = 0.f;
-        if (ax[k] != 0.0f || bx[k] != 0.0f) {
-          const float inv = 1.0f / wk[k];
-          a[4 * h + k] = ax[k] * inv;
-          b[4 * h + k] = bx[k] * inv;
-        }
-      }
+      for (int k = 0; k < 4; ++k)
+        bin_terms(ax[k], quantized_weight(wk[k], S), 0.0f, &a[4 * h + k], &b[4 * h + k]);
     }
   } else {
 #pragma unroll
     for (int k = 0; k < kBwPer; ++k) {
-      a[k] = 0.f;
-      b[k] = 0.f;
+      a[k] = df_zero();
+      b[k] = df_zero();
       const int64_t e = e0 + k;
-      if (e < t1) {
-        const float2 v = acc[e];
-        if (v.x != 0.0f || v.y != 0.0f) {
-          const float inv = 1.0f / w[e];
-          a[k] = v.x * inv;
-          b[k] = v.y * inv;
-        }
-      }
+      if (e < t1) bin_terms(acc[e], quantized_weight(w[e], S), 0.0f, &a[k], &b[k]);
     }
   }
-  float tot = 0.f;
+  dflt tot = df_zero();
 #pragma unroll
-  for (int k = kBwPer - 1; k >= 0; --k) tot += a[k];
-  // sum of the thread totals after this thread: within the warp by shuffles,
-  // then over the warps after this one
-  float v = tot;
+  for (int k = kBwPer - 1; k >= 0; --k) tot = df_add(tot, a[k]);
+  // sum of the thread totals after this thread: within the warp by shuffles
+  // (inclusive from the right, then shifted by one lane), then over the warps
+  // after this one
+  dflt v = tot;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const float y = __shfl_down_sync(0xffffffffu, v, o);
-    if (lane + o < 32) v += y;
+    const dflt y = df_shfl_down(v, o);
+    if (lane + o < 32) v = df_add(v, y);
   }
+  dflt exv = df_shfl_down(v, 1);
+  if (lane == 31) exv = df_zero();
   if (lane == 0) wtot_s[wid] = v;
   __syncthreads();
-  float exv = v - tot;
-  float tile_tot = 0.f;
+  dflt tile_tot = df_zero();
 #pragma unroll
   for (int k = kBwThreads / 32 - 1; k >= 0; --k) {
-    if (k > wid) exv += wtot_s[k];
-    tile_tot += wtot_s[k];
+    if (k > wid) exv = df_add(exv, wtot_s[k]);
+    tile_tot = df_add(tile_tot, wtot_s[k]);
   }
+  const double tile_tot_d = df_to_double(tile_tot);
   const bool last_tile = t1 == N;  // the distribution's last element lies here
   if (threadIdx.x == 0) {
-    carry[tile] = (double)tile_tot;
-    incl[tile] = (double)tile_tot;
+    carry[tile] = tile_tot_d;
+    incl[tile] = tile_tot_d;
     __threadfence();
     atomicExch(flags + tile, last_tile ? 2u : 1u);
   }
-  // block-wide lookback for the sum beyond t1 (as in suffix_kernel)
+  // block-wide lookback for the sum beyond t1 in the distribution of t1 - 1
   double E = 0.0;
   if (!last_tile) {
     int64_t look = tile + 1;
@@ -552,7 +666,7 @@ __global__ void __launch_bounds__(kBwThreads)
       if ((int)threadIdx.x == pfx && idx < ntiles) x = *((volatile double*)(incl + idx));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) part_s[wid] = x;
+      if ((threadIdx.x & 31) == 0) part_s[threadIdx.x >> 5] = x;
       __syncthreads();
       if (threadIdx.x == 0) {
         double t = 0.0;
@@ -564,20 +678,20 @@ __global__ void __launch_bounds__(kBwThreads)
       if (pfx < kBwThreads) break;
       look += kBwThreads;
     }
-    if (threadIdx.x == 0) {
-      incl[tile] = (double)tile_tot + E;
-      __threadfence();
-      atomicExch(flags + tile, 2u);
-    }
+  }
+  if (!last_tile && threadIdx.x == 0) {
+    incl[tile] = tile_tot_d + E;
+    __threadfence();
+    atomicExch(flags + tile, 2u);
   }
   if (e0 >= t1) return;
-  const float base = (float)(G[0] - ((double)exv + E));
-  float inrun = 0.f;
+  const dflt base = df_from_double(G[0] - (df_to_double(exv) + E));
+  dflt inrun = df_zero();
   float gk[kBwPer];
 #pragma unroll
   for (int k = kBwPer - 1; k >= 0; --k) {
-    gk[k] = base - inrun - b[k];
-    inrun += a[k];
+    gk[k] = df_to_float(df_sub(df_sub(base, inrun), b[k]));
+    inrun = df_add(inrun, a[k]);
   }
   if (e0 + kBwPer <= t1) {
     float4* gv = reinterpret_cast<float4*>(grad_w + e0);
@@ -685,22 +799,22 @@ cudaError_t launch_backward_finish(const rtf_forest* f, const float* w, int mode
   double* carry = reinterpret_cast<double*>(p.base + L.carry);
   double* incl = reinterpret_cast<double*>(p.base + L.incl);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(p.base + L.ticket);
-  float* R = reinterpret_cast<float*>(p.base + L.R);
+  float2* R = reinterpret_cast<float2*>(p.base + L.R);
   float* gradR = reinterpret_cast<float*>(p.base + L.gradR);
   const int64_t Nw = two_d ? N - (D - 1) : N;
   const int sms = bw_sms();
   if (two_d) {
-    row_sum_kernel<<<(unsigned)std::min<int64_t>(sms * 4, (D + 7) / 8), 256, 0, st>>>(
-        w, f->dists, D - 1, R);
+    row_total_kernel<<<(unsigned)std::min<int64_t>(sms * 4, (D - 1 + 255) / 256), 256, 0, st>>>(
+        f->dists, D - 1, R);
   }
   const int64_t tiles = (N + kBwTile - 1) / kBwTile;
-  bin_total_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, f->nodes, w, R, f->dists, D, N,
-                                                           Nw, G);
+  bin_total_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, f->nodes, f->dists, D, N, G);
   const bool vec_ok = (reinterpret_cast<uintptr_t>(w) & 15) == 0 &&
                       (reinterpret_cast<uintptr_t>(grad_w) & 15) == 0;
   if (D == 1 && !two_d && vec_ok)
-    suffix_single_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, w, N, G, flags, carry,
-                                                                 incl, ticket, grad_w, f->status);
+    suffix_single_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, w, f->dists, N, G, flags,
+                                                                 carry, incl, ticket, grad_w,
+                                                                 f->status);
   else
     suffix_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, w, R, f->dists, D, N, Nw, G,
                                                           flags, carry, incl, ticket, grad_w,

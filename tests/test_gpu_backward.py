@@ -1,6 +1,17 @@
 """Gradient of the in-bin positions on the GPU against the oracle's fp64
-chain-rule gradient (relative error in the 2-norm at most 1e-4) and against
-central differences of the GPU forward itself."""
+chain-rule gradient and against central differences of the GPU forward itself.
+
+Both sides differentiate the forward that is computed, x = (xi T - C_i) / q_i,
+with the floor of the quantisation passed straight through: the relaxation at
+the quantised weights w' = floor(w 2^S) 2^-S.
+
+Tolerance, element by element: |g - g_ref| <= 1e-4 (|g_ref| + 1e-3 max|g_ref|).
+The 1e-4 is the relative gradient error the path is held to; the absolute
+floor 1e-7 max|g_ref| covers the float32 rounding of the partial sums that
+enter one element (the per-bin sums, the tile's suffix sums and the final
+G - S_k - X_k / w'_k are float32; each rounding is 2^-24 of a sum no larger
+than the largest element in these workloads).  The relative error in the
+2-norm is checked against 1e-4 as well."""
 
 import numpy as np
 import pytest
@@ -30,6 +41,21 @@ def rel_err(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+def check_grad(gw, gref, rel=TOL, floor=1e-3):
+    """Element-wise mixed bound and the 2-norm bound; returns the worst ratio
+    of an element's error to its bound."""
+    gw = np.asarray(gw, np.float64).reshape(-1)
+    gref = np.asarray(gref, np.float64).reshape(-1)
+    assert np.isfinite(gw).all()
+    err = np.abs(gw - gref)
+    bound = rel * (np.abs(gref) + floor * np.abs(gref).max())
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, (f"{bad.size} of {gref.size} gradient elements off; worst "
+                           f"{(err / bound).max():.3g} x the bound, first at {bad[:5]}")
+    assert rel_err(gw, gref) <= rel
+    return float((err / bound).max())
+
+
 def run_1d(n, n_s, m, seed, sigma=1.0):
     w = W.lognormal_weights(n, seed=seed, sigma=sigma)
     u = W.iid_u32(n_s, seed=seed + 1)
@@ -50,19 +76,19 @@ def run_1d(n, n_s, m, seed, sigma=1.0):
 
 def test_backward_small():
     gw, gref = run_1d(1000, 100000, 8, seed=0)
-    assert rel_err(gw, gref) <= TOL
+    check_grad(gw, gref)
 
 
 def test_backward_few_samples_per_bin():
     """Far fewer samples than bins: most bins get no sample."""
     gw, gref = run_1d(1 << 16, 5000, 12, seed=5)
-    assert rel_err(gw, gref) <= TOL
+    check_grad(gw, gref)
 
 
 def test_backward_ragged_tail():
     """n not a multiple of the 2048-element tiles of the suffix scan."""
     gw, gref = run_1d(3 * 8192 + 1234, 1 << 18, 12, seed=6)
-    assert rel_err(gw, gref) <= TOL
+    check_grad(gw, gref)
 
 
 def test_backward_single_bin_is_zero():
@@ -110,19 +136,31 @@ def test_backward_without_samples_is_zero():
 def test_backward_config_full():
     """n = 2^20 lognormal(0, 1), 2^24 uniform samples, dL/dx ~ N(0, 1)."""
     gw, gref = run_1d(1 << 20, 1 << 24, 18, seed=10)
-    assert rel_err(gw, gref) <= TOL
+    check_grad(gw, gref)
+
+
+def oracle_grad_sorted(w, m, u, g, idx_gpu):
+    """The oracle's gradient for many samples: the same samples taken in
+    ascending order (the gradient is a sum over the samples; sorted, the
+    oracle's searches stay in cache), indices checked against the GPU's."""
+    n_s = u.size
+    key = (u.astype(np.uint64) << np.uint64(32)) | np.arange(n_s, dtype=np.uint64)
+    key.sort()
+    order = (key & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    del key
+    us, gs = u[order], g[order]
+    ref = orc.build(w, 1 << m)
+    ridx, _ = orc.sample(ref.C, us, threads=orc.host_threads())
+    assert np.array_equal(idx_gpu[order], ridx)
+    return orc.grad_q(ref.C, ref.S, us, ridx, gs)
 
 
 def test_backward_two_pass_scatter():
-    """2^26 samples into 2^24 bins: the per-bin sums (128 MiB) exceed 3/4 of the
-    L2 with 4 samples per bin, so the scatter adds them in two passes over the
-    halves of the bins, as in the benchmark's backward.  Weights lognormal(0, 1)
-    as in the gradient workload: the fixed-point scale resolves the smallest of
-    them to about 5e6 units (at lognormal(0, 2) and this n the smallest get
-    about 70, and the positions' quantisation, against the real relaxation the
-    oracle differentiates, moves the gradient by about 1e-3)."""
+    """2^26 samples into 2^24 lognormal(0, 2) bins (the benchmark's weights):
+    the per-bin sums (128 MiB) exceed 3/4 of the L2 with 4 samples per bin, so
+    the scatter adds them in two passes over the halves of the bins."""
     n, n_s, m = 1 << 24, 1 << 26, 20
-    w = W.lognormal_weights(n, seed=30, sigma=1.0)
+    w = W.lognormal_weights(n, seed=30, sigma=2.0)
     u = W.iid_u32(n_s, seed=31)
     g = W.normal_f32(n_s, seed=32)
     wd = to_dev(w)
@@ -132,17 +170,32 @@ def test_backward_two_pass_scatter():
     gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, to_dev(g))
     torch.cuda.synchronize()
     f.check_status()
-    # the oracle takes the same samples in ascending order (the gradient is a
-    # sum over the samples; sorted, its searches stay in cache)
-    key = (u.astype(np.uint64) << np.uint64(32)) | np.arange(n_s, dtype=np.uint64)
-    key.sort()
-    order = (key & np.uint64(0xFFFFFFFF)).astype(np.int64)
-    us, gs = u[order], g[order]
-    ref = orc.build(w, 1 << m)
-    ridx, _ = orc.sample(ref.C, us)
-    assert np.array_equal(idx.cpu().numpy()[order], ridx)
-    gref = orc.grad(w, us, ridx, gs)
-    assert rel_err(gw.cpu().numpy(), gref) <= TOL
+    gref = oracle_grad_sorted(w, m, u, g, idx.cpu().numpy())
+    check_grad(gw.cpu().numpy(), gref)
+
+
+def test_backward_bench_workload():
+    """The benchmark's backward, input for input: n = 2^24 lognormal(0, 2)
+    weights (seed 0), 2^20 cells, the 2^28 i.i.d. samples (seed 1) and
+    dL/dx ~ N(0, 1) (seed 2), in the launch configuration the benchmark times
+    (one call, two scatter passes)."""
+    n, n_s, m = 1 << 24, 1 << 28, 20
+    w = W.lognormal_weights(n, seed=0, sigma=2.0)
+    u = W.iid_u32(n_s, seed=1)
+    g = W.normal_f32(n_s, seed=2)
+    wd = to_dev(w)
+    f = api.rtf_build(wd, m)
+    ud = api.u32_tensor(u, DEV)
+    idx, pos = api.rtf_sample(f, ud)
+    gd = to_dev(g)
+    gw = api.rtf_sample_backward(f, wd, ud, None, idx, pos, gd)
+    torch.cuda.synchronize()
+    f.check_status()
+    idx_h = idx.cpu().numpy()
+    gw_h = gw.cpu().numpy()
+    del ud, idx, pos, gd, gw
+    gref = oracle_grad_sorted(w, m, u, g, idx_h)
+    check_grad(gw_h, gref)
 
 
 def test_backward_sorted_samples_merge_runs():
@@ -159,7 +212,7 @@ def test_backward_sorted_samples_merge_runs():
     ref = orc.build(w, 1 << m)
     ridx, _ = orc.sample(ref.C, u)
     gref = orc.grad(w, u, ridx, g)
-    assert rel_err(gw.cpu().numpy(), gref) <= TOL
+    check_grad(gw.cpu().numpy(), gref)
 
 
 def test_backward_tagged_batch():
@@ -184,7 +237,7 @@ def test_backward_tagged_batch():
         ref = orc.build(w[off[d]:off[d + 1]], 1 << ms[d])
         ridx, _ = orc.sample(ref.C, u[sel])
         gref[off[d]:off[d + 1]] = orc.grad(w[off[d]:off[d + 1]], u[sel], ridx, g[sel])
-    assert rel_err(gw, gref) <= TOL
+    check_grad(gw, gref)
 
 
 @pytest.mark.parametrize("H,Wd,n_s", [(32, 64, 1 << 16), (512, 1024, 1 << 22)])
@@ -208,7 +261,7 @@ def test_backward_env_map(H, Wd, n_s):
     ii = idx.cpu().numpy()
     assert np.array_equal(ii[:, 0], r) and np.array_equal(ii[:, 1], c)
     gref = orc.grad_env(lum, u[0::2], u[1::2], r, c, g[0::2], g[1::2]).reshape(-1)
-    assert rel_err(gw.cpu().numpy(), gref) <= TOL
+    check_grad(gw.cpu().numpy(), gref)
 
 
 def test_backward_matches_gpu_forward_differences():
@@ -260,7 +313,7 @@ def test_autograd_function_matches_oracle():
     ridx, _ = orc.sample(ref.C, u_h)
     assert np.array_equal(idx.cpu().numpy(), ridx)
     gref = orc.grad(w_h, u_h, ridx, c_h)
-    assert rel_err(w.grad.cpu().numpy(), gref) <= TOL
+    check_grad(w.grad.cpu().numpy(), gref)
 
 
 def test_autograd_function_2d_matches_oracle():
@@ -276,7 +329,7 @@ def test_autograd_function_2d_matches_oracle():
     rows, marg = orc.build_env(lum_h, 1 << 6, 1 << 7)
     r, c, _, _ = orc.sample_env(rows, marg, u_h[0::2], u_h[1::2])
     gref = orc.grad_env(lum_h, u_h[0::2], u_h[1::2], r, c, c_h[:, 0].copy(), c_h[:, 1].copy())
-    assert rel_err(lum.grad.cpu().numpy(), gref) <= TOL
+    check_grad(lum.grad.cpu().numpy(), gref)
 
 
 def test_accumulated_backward_equals_one_call():
@@ -298,7 +351,7 @@ def test_accumulated_backward_equals_one_call():
     assert rel_err(split, one.astype(np.float64)) <= 1e-5
     ref = orc.build(w, 1 << m)
     ridx, _ = orc.sample(ref.C, u)
-    assert rel_err(split, orc.grad(w, u, ridx, g)) <= TOL
+    check_grad(split, orc.grad(w, u, ridx, g))
 
 
 def test_accumulated_backward_2d_and_on_a_second_stream():
