@@ -450,38 +450,54 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 // ---------------------------------------------------------------------------
-// forest: Algorithm 1 per tile in shared memory, cross-tile merges in global
+// forest: the tree links of every node and leaf (Algorithm 1's result)
 // ---------------------------------------------------------------------------
+// Algorithm 1 (Sec. 3.2) grows ranges bottom-up: a range [lo, hi] becomes the
+// child of the split at lo (child 1) or at hi + 1 (child 0), whichever of the
+// bounding distances delta_{lo-1}, delta_hi is smaller (equal distances go to
+// child 1), and the first of two siblings to arrive stops.  The tree this
+// yields is fixed by the distances alone: the node of split k (between leaves
+// k - 1 and k, node index k, Sec. 3.1) covers the leaves from the nearest
+// split on its left with a larger distance to the nearest split on its right
+// with a distance at least as large (ties go right, as the strict comparison
+// sends equal distances to child 1); among those two bounding splits its
+// parent is the one with the smaller distance (the right one's when the left
+// is larger), and it is that parent's child 0 when the parent lies on its
+// right.  A leaf is the one-leaf range between its two neighbouring splits.
+// So every node and every leaf finds its parent from the two nearest larger
+// distances around it, without climbing and without atomics; every child slot
+// has exactly one writer.  Inside a tile the nearest larger distances are
+// found with warp ballots over the bit planes of the tile's distances; a node
+// whose bounding splits lie outside the tile (its range crosses a tile edge)
+// is left to the merge pass, which searches the global distance array.
 constexpr int kForestPer = kTile / kForestThreads;  // 4
-static_assert(kForestPer == 4, "the otherBounds write-out stores one int4 per thread");
+static_assert(kForestPer == 4, "the distance write-out stores one u32 per thread");
 constexpr int32_t kUnset = 0x7FFFFFFF;
+constexpr int kChunks = (kTile + 1 + 31) / 32;      // 32-split chunks of positions 0..tn
+constexpr uint32_t kDeltaTop = 33;                  // kDeltaInf in 6 bits (above any 0..32)
 
 template <bool SEG>
 struct ForestShared {
   alignas(16) uint64_t C[kTile + 2];  // C_{t0-1} .. C_{t1}
   alignas(16) uint64_t K[kTile + 2];  // K_{t0-1} .. K_{t1}
   alignas(16) int32_t child[kTile][2];
-  // the staged weights are dead once q is known; the tile's otherBounds reuse them
-  union alignas(16) WO {
-    float w[kTile + 4];
-    int32_t other[kTile + 4];
-  } wo;
   int32_t dist[SEG ? kTile : 1];
-  uint8_t delta[kTile + 4];  // delta_{t0-1} .. delta_{t1-1}
+  // d[p]: distance of the split at tile position p, between leaves p - 1 and
+  // p (p = 0: delta_{t0-1}; p = tn: delta_{t1-1})
+  uint8_t d[kChunks * 32];
+  uint32_t plane[kChunks][6];  // bit b of min(d, 33) for the 32 positions of a chunk
+  uint32_t valid[kChunks];     // positions <= tn
+  uint32_t cmax[kChunks];      // largest min(d, 33) of the chunk's valid positions
   SegPair wtot[kForestThreads / 32];
   SegPair btot;
-  uint64_t bar;
-  int ok;
+  uint32_t tmax;
   int dfirst;
   int dprev;
-  int ndefer;
+  int nunres;
   float wprev;
   uint64_t prefix;
   rtf_dist P0;  // parameters of the tile's first distribution
-  int32_t defer_parent[kDeferCap];
-  int32_t defer_bound[kDeferCap];
-  int32_t defer_node[kDeferCap];
-  int32_t defer_dist[kDeferCap];
+  int32_t unres[kUnresCap];
 };
 
 struct ForestArgs {
@@ -498,9 +514,10 @@ struct ForestArgs {
   const uint64_t* tile_prefix;
   const uint32_t* dmax;
   uint8_t* delta;
-  int32_t* other;
-  uint4* items;
-  int32_t* item_count;
+  uint8_t* tmax;
+  uint32_t* gmax;
+  int32_t* unres;
+  int32_t* unres_count;
   uint32_t* status;
 };
 
@@ -544,54 +561,23 @@ __device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist&
   a.last_lo[gi] = Chi;
 }
 
-// Continue Algorithm 1 through global memory from range [lo, hi] with node
-// `node` (local reference) of distribution P.  This runs in the merge kernel,
-// after every tile has written its records, distances and otherBounds slice,
-// so the hand-offs are plain atomic exchanges.
-__device__ void climb_global(const ForestArgs& a, const rtf_dist& P, int64_t lo, int64_t hi,
-                             int32_t node) {
-  for (int64_t guard = 0; guard <= a.N; ++guard) {  // each pass grows the range
-    uint32_t dl = lo > 0 ? (uint32_t)a.delta[lo - 1] : kDeltaInf;
-    uint32_t dr = (uint32_t)a.delta[hi];
-    if (dl >= kDeltaInf && dr >= kDeltaInf) {
-      rtf_node* root = a.nodes + lo;
-      int32_t lo_l = (int32_t)(lo - P.elem_off);
-      root->child[0] = ~(lo_l > 0 ? lo_l - 1 : 0);
-      root->child[1] = node;
-      const uint64_t Clo = a.nodes[lo].cdf, Chi = a.nodes[hi].cdf;
-      const uint64_t Clm1 = lo_l > 0 ? a.nodes[lo - 1].cdf : 0ull;
-      const uint64_t Chp1 = hi + 1 < P.elem_off + P.n ? a.nodes[hi + 1].cdf : P.total;
-      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, Chi), Clm1, Clo, Chi, Chp1, node);
-      return;
+// Lanes of a 32-position chunk whose value (bit planes pl[0..5]) exceeds v
+// (*gt) and equals it (*eq, within `valid`).
+__device__ __forceinline__ void compare_planes(const uint32_t* pl, uint32_t v, uint32_t valid,
+                                               uint32_t* gt, uint32_t* eq) {
+  uint32_t g = 0u, e = valid;
+#pragma unroll
+  for (int b = 5; b >= 0; --b) {
+    const uint32_t p = pl[b];
+    if ((v >> b) & 1u) {
+      e &= p;
+    } else {
+      g |= e & p;
+      e &= ~p;
     }
-    int child = dl > dr ? 0 : 1;
-    int64_t parent = child ? lo : hi + 1;
-    a.nodes[parent].child[child] = node;
-    int ob = atomicExch(a.other + parent, (int)(child ? hi : lo));
-    if (ob < 0) return;  // first of the two children
-    if (child)
-      lo = ob;
-    else
-      hi = ob;
-    node = (int32_t)(parent - P.elem_off);
   }
-  raise_status(a.status, RTF_STATUS_TIMEOUT);
-}
-
-// A hand-off deferred by phase A because the sibling lies in the neighbouring
-// tile, packed as uint4 {parent, bound, node, dist}: the arriver's range is
-// [bound, parent-1] when it is the left child (bound < parent) and
-// [parent, bound] when it is the right child.
-__device__ void run_deferred(const ForestArgs& a, uint4 it) {
-  const int64_t parent = (int32_t)it.x, bound = (int32_t)it.y;
-  const int32_t node = (int32_t)it.z;
-  const int child = bound < parent ? 0 : 1;
-  const rtf_dist P = a.dists[it.w];
-  a.nodes[parent].child[child] = node;
-  const int ob = atomicExch(a.other + parent, (int)bound);
-  if (ob < 0) return;
-  const int64_t lo = child ? ob : bound, hi = child ? bound : ob;
-  climb_global(a, P, lo, hi, (int32_t)(parent - P.elem_off));
+  *gt = g;
+  *eq = e;
 }
 
 // Minimum resident forest blocks per SM given to the register allocator.
@@ -607,27 +593,41 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
   const int tn = (int)(t1 - t0);
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
     const int df = SEG ? find_dist(a.dists, 0, a.D - 1, t0) : 0;
     s.dfirst = df;
     s.dprev = (t0 > 0 && SEG) ? (a.dists[df].elem_off == t0 ? df - 1 : df) : df;
-    s.ndefer = 0;
-    // loads needed later, issued while the tile is staged
+    s.nunres = 0;
+    s.tmax = 0;
     s.P0 = a.dists[df];
     s.prefix = t0 > 0 ? a.tile_prefix[tile] : 0ull;
     s.wprev = (t0 > 0 && t0 - 1 < a.Nw) ? a.w[t0 - 1] : 0.0f;
   }
-  int wo = 0;
-  if (t0 < a.Nw) wo = stage_weights(s.wo.w, a.w, t0, min(t1, a.Nw), &s.bar, &s.ok, a.status);
-  else __syncthreads();
+  // the thread's four weights, straight from global memory (16-byte vectors
+  // where aligned); the passes before this one left them in L2
+  const int l0 = tid * kForestPer;  // tile-local index of the thread's first leaf
+  const int64_t e0 = t0 + l0;
+  float wv[kForestPer];
+  if (e0 + kForestPer <= a.Nw && e0 + kForestPer <= t1 &&
+      (reinterpret_cast<uintptr_t>(a.w + e0) & 15) == 0) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(a.w + e0));
+    wv[0] = x.x;
+    wv[1] = x.y;
+    wv[2] = x.z;
+    wv[3] = x.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kForestPer; ++k)
+      wv[k] = (e0 + k < t1 && e0 + k < a.Nw) ? a.w[e0 + k] : 0.0f;
+  }
+  __syncthreads();
   const int dfirst = s.dfirst;
 
   // ---- q, C and keys of the thread's leaves ---------------------------------
   // Each thread owns kForestPer consecutive leaves; the parameters of the
   // distribution it is in stay in registers (reloaded only at a boundary).
-  const int l0 = tid * kForestPer;  // tile-local index of the first leaf
-  const int64_t e0 = t0 + l0;
   uint64_t q[kForestPer], incl[kForestPer];
   int dk[kForestPer];
   uint32_t headmask = 0;
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
         if (SEG && (flags & kDistMarginal)) {
           qq = __ldcg(&a.dists[e - off].total);
         } else {
-          const uint32_t b = weight_bits(s.wo.w[wo + l0 + k]);
+          const uint32_t b = weight_bits(wv[k]);
           qq = weight_bad(b) ? 0ull : quantize_bits(b, S);
         }
         if (SEG) s.dist[l0 + k] = dcur;
@@ -682,9 +682,9 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
       run += qq;
       incl[k] = run;
     }
-    // exclusive prefix of the thread's run within the tile (its barriers also
-    // retire s.wo.w); one distribution has its only head at element 0, where
-    // the running sum is 0 anyway, so a plain scan serves
+    // exclusive prefix of the thread's run within the tile; one distribution
+    // has its only head at element 0, where the running sum is 0 anyway, so a
+    // plain scan serves
     uint64_t base;
     if (SEG) {
       const SegPair ex = block_seg_exclusive(SegPair{run, headmask ? 1u : 0u}, s.wtot, &s.btot);
@@ -719,7 +719,6 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
         s.C[tn + 1] = inc;  // C_{t1} within the distribution of t1-1
         s.K[tn + 1] = key_of(inc, T, R, z);
       }
-      s.wo.other[l] = -1;
       s.child[l][0] = kUnset;
       s.child[l][1] = kUnset;
     }
@@ -743,12 +742,13 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
     }
   }
   __syncthreads();
-  // distances: delta_j for the thread's leaves j, and delta_{t0-1} by thread 0
+  // distances: delta_j for the thread's leaves j (position l + 1), delta_{t0-1}
+  // (position 0) by thread 0; the tile's largest distance
   {
     int dP = -1;
     int m = 0;
     int64_t end = 0;
-    uint32_t packed = 0;
+    uint32_t packed = 0, dmx = 0;
 #pragma unroll
     for (int k = 0; k < kForestPer; ++k) {
       const int l = l0 + k;
@@ -764,7 +764,8 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
           const uint64_t Ka = s.K[l + 1], Kb = s.K[l + 2];
           if (cell_of(Ka, m) == cell_of(Kb, m)) dlt = key_distance(Ka, Kb);
         }
-        s.delta[l + 1] = (uint8_t)dlt;
+        s.d[l + 1] = (uint8_t)dlt;
+        dmx = max(dmx, dlt);
       }
       packed |= dlt << (8 * k);
     }
@@ -774,6 +775,8 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
       for (int k = 0; k < kForestPer && l0 + k < tn; ++k)
         a.delta[e0 + k] = (uint8_t)(packed >> (8 * k));
     }
+    dmx = __reduce_max_sync(0xffffffffu, dmx);
+    if (lane == 0 && dmx) atomicMax(&s.tmax, dmx);
     if (tid == 0) {
       uint32_t d0 = kDeltaInf;
       if (t0 > 0 && s.dprev == dfirst) {
@@ -781,68 +784,137 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
         const uint64_t Ka = s.K[0], Kb = s.K[1];
         if (cell_of(Ka, mm) == cell_of(Kb, mm)) d0 = key_distance(Ka, Kb);
       }
-      s.delta[0] = (uint8_t)d0;
-      if (t0 > 0) a.delta[t0 - 1] = (uint8_t)d0;
+      s.d[0] = (uint8_t)d0;
     }
   }
   __syncthreads();
 
-  // ---- phase A: Algorithm 1 inside the tile (tile-local indices) -----------
-  // delta[l] is the distance left of leaf l, delta[l + 1] the one right of it.
-#pragma unroll 1
-  for (int k = 0; k < kForestPer; ++k) {
-    const int l = l0 + k;
-    if (l >= tn) break;
-    const int d = SEG ? s.dist[l] : 0;
-    const int32_t base_id = (int32_t)(t0 - (SEG ? a.dists[d].elem_off : s.P0.elem_off));
-    int lo = l, hi = l;
-    int32_t node = ~(base_id + l);
-    while (true) {
-      const uint32_t dl = s.delta[lo];
-      const uint32_t dr = s.delta[hi + 1];
+  // ---- bit planes of the distances, per chunk of 32 positions ---------------
+  const int nchunks = (tn + 1 + 31) >> 5;
+  for (int c = warp; c < nchunks; c += kForestThreads / 32) {
+    const int p = 32 * c + lane;
+    const bool ok = p <= tn;
+    const uint32_t v = ok ? min((uint32_t)s.d[p], kDeltaTop) : 0u;
+    const uint32_t vm = __ballot_sync(0xffffffffu, ok);
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      const uint32_t pb = __ballot_sync(0xffffffffu, (v >> b) & 1u);
+      if (lane == b) mine = pb;
+    }
+    const uint32_t mx = __reduce_max_sync(0xffffffffu, v);
+    if (lane < 6) s.plane[c][lane] = mine;
+    if (lane == 0) {
+      s.valid[c] = vm;
+      s.cmax[c] = mx;
+    }
+  }
+  if (tid == 0) {
+    a.tmax[tile] = (uint8_t)s.tmax;
+    if (s.tmax) atomicMax(a.gmax + tile / kTileGroup, s.tmax);
+  }
+  __syncthreads();
+
+  // ---- links: node and leaf at every position p in [0, tn) -------------------
+  for (int c = warp; c < nchunks; c += kForestThreads / 32) {
+    const int p = 32 * c + lane;
+    if (p >= tn) continue;
+    const int dd = SEG ? s.dist[p] : 0;
+    const rtf_dist& P = SEG ? a.dists[dd] : s.P0;
+    const int32_t base_id = (int32_t)(t0 - P.elem_off);
+    const uint32_t v = s.d[p];
+
+    // leaf p, between the splits at positions p and p + 1
+    {
+      const uint32_t dl = v, dr = s.d[p + 1];
+      const int32_t id = base_id + p;
+      if (dl >= kDeltaInf) s.child[p][0] = ~(id > 0 ? id - 1 : 0);  // p starts a cell
       if (dl >= kDeltaInf && dr >= kDeltaInf) {
-        // full cell inside the tile: its root is the node of the first leaf
-        const int32_t lo_id = base_id + lo;
-        s.child[lo][0] = ~(lo_id > 0 ? lo_id - 1 : 0);
-        s.child[lo][1] = node;
-        const rtf_dist& P = SEG ? a.dists[d] : s.P0;
-        // s.C[l + 1] is C of tile leaf l; s.C[0] that of t0 - 1 (same distribution)
-        const uint64_t Clm1 = lo_id > 0 ? s.C[lo] : 0ull;
-        const uint64_t Chp1 = t0 + hi + 1 == P.elem_off + P.n ? P.total : s.C[hi + 2];
-        finish_cell(a, P, t0 + lo, t0 + hi, s.K[lo + 1], s.K[hi + 1], Clm1, s.C[lo + 1],
-                    s.C[hi + 1], Chp1, node);
-        break;
+        // a cell of one leaf: the leaf is its root's tree
+        s.child[p][1] = ~id;
+        const uint64_t Clm1 = id > 0 ? s.C[p] : 0ull;
+        const uint64_t Chp1 = t0 + p + 1 == P.elem_off + P.n ? P.total : s.C[p + 2];
+        finish_cell(a, P, t0 + p, t0 + p, s.K[p + 1], s.K[p + 1], Clm1, s.C[p + 1], s.C[p + 1],
+                    Chp1, ~id);
+      } else if (dl > dr) {
+        if (p + 1 < tn)
+          s.child[p + 1][0] = ~id;
+        else
+          a.nodes[t1].child[0] = ~id;
+      } else {
+        s.child[p][1] = ~id;
       }
-      const int child = dl > dr ? 0 : 1;
-      if ((child == 1 && lo == 0) || (child == 0 && hi == tn - 1)) {
-        // the sibling lies in the neighbouring tile
-        const int slot = atomicAdd(&s.ndefer, 1);
-        if (slot < kDeferCap) {
-          s.defer_parent[slot] = (int32_t)(t0 + (child ? lo : hi + 1));
-          s.defer_bound[slot] = (int32_t)(t0 + (child ? hi : lo));
-          s.defer_node[slot] = node;
-          s.defer_dist[slot] = d;
+    }
+
+    // node p (the split at position p), unless p is a cell boundary
+    if (v >= kDeltaInf) continue;
+    uint32_t gt, eq;
+    compare_planes(s.plane[c], v, s.valid[c], &gt, &eq);
+    // nearest position left of p with a larger distance
+    int pl = -1;
+    {
+      const uint32_t m = gt & ((1u << lane) - 1u);
+      if (m) {
+        pl = 32 * c + 31 - __clz(m);
+      } else {
+        for (int c2 = c - 1; c2 >= 0; --c2) {
+          if (s.cmax[c2] > v) {
+            uint32_t g2, e2;
+            compare_planes(s.plane[c2], v, s.valid[c2], &g2, &e2);
+            pl = 32 * c2 + 31 - __clz(g2);
+            break;
+          }
         }
-        break;
       }
-      const int parent = child ? lo : hi + 1;
-      s.child[parent][child] = node;
-      const int ob = atomicExch(&s.wo.other[parent], child ? hi : lo);
-      if (ob < 0) break;
-      s.wo.other[parent] = -2;
-      if (child)
-        lo = ob;
+    }
+    // nearest position right of p with a distance at least as large
+    int pr = -1;
+    {
+      const uint32_t m = (gt | eq) & ~((2u << lane) - 1u);
+      if (lane < 31 && m) {
+        pr = 32 * c + __ffs(m) - 1;
+      } else {
+        for (int c2 = c + 1; c2 < nchunks; ++c2) {
+          if (s.cmax[c2] >= v) {
+            uint32_t g2, e2;
+            compare_planes(s.plane[c2], v, s.valid[c2], &g2, &e2);
+            pr = 32 * c2 + __ffs(g2 | e2) - 1;
+            break;
+          }
+        }
+      }
+    }
+    const int32_t id = base_id + p;
+    if (pr < 0 || (pl < 0 && s.d[pr] > v)) {
+      // the parent depends on distances outside the tile
+      const int slot = atomicAdd(&s.nunres, 1);
+      if (slot < kUnresCap) s.unres[slot] = p;
+      continue;
+    }
+    const uint32_t dr = s.d[pr];
+    const uint32_t dl = pl >= 0 ? s.d[pl] : kDeltaInf + 1;  // unknown, larger than v = dr
+    if (dl >= kDeltaInf && dr >= kDeltaInf && pl >= 0) {
+      // the top of a cell inside the tile: leaves [pl, pr - 1], root at pl
+      s.child[pl][1] = id;
+      const int32_t lo_id = base_id + pl;
+      const uint64_t Clm1 = lo_id > 0 ? s.C[pl] : 0ull;
+      const uint64_t Chp1 = t0 + pr == P.elem_off + P.n ? P.total : s.C[pr + 1];
+      finish_cell(a, P, t0 + pl, t0 + pr - 1, s.K[pl + 1], s.K[pr], Clm1, s.C[pl + 1], s.C[pr],
+                  Chp1, id);
+    } else if (dl > dr) {
+      if (pr < tn)
+        s.child[pr][0] = id;
       else
-        hi = ob;
-      node = base_id + parent;
+        a.nodes[t1].child[0] = id;
+    } else {
+      s.child[pl][1] = id;
     }
   }
   __syncthreads();
 
-  // ---- node records and the tile's otherBounds slice -------------------------
-  // Records go out with consecutive threads on consecutive records (leaf
-  // l = tid + k * blockDim); otherBounds holds the far bound of every first
-  // arrival still waiting for its sibling, -1 everywhere else.
+  // ---- node records -----------------------------------------------------------
+  // Consecutive threads on consecutive records (leaf l = tid + k * blockDim); a
+  // child slot written by another tile or by the merge pass is left alone.
 #pragma unroll
   for (int k = 0; k < kForestPer; ++k) {
     const int l = tid + k * kForestThreads;
@@ -862,43 +934,132 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
       if (c1 != kUnset) rec->child[1] = c1;
     }
   }
-  int ob4[kForestPer];
-#pragma unroll
-  for (int k = 0; k < kForestPer; ++k) {
-    const int l = l0 + k;
-    const int o = l < tn ? s.wo.other[l] : -1;
-    ob4[k] = o >= 0 ? (int)(t0 + o) : -1;
-  }
-  if (l0 + kForestPer <= tn) {
-    *reinterpret_cast<int4*>(a.other + e0) = make_int4(ob4[0], ob4[1], ob4[2], ob4[3]);
-  } else {
-    for (int k = 0; k < kForestPer && l0 + k < tn; ++k) a.other[e0 + k] = ob4[k];
-  }
-
-  // ---- hand-offs across tile edges -------------------------------------------
-  // A first arrival that no sibling met inside the tile stays in this tile's
-  // slice of the global otherBounds (written above); a range that must merge
-  // with a sibling in the neighbouring tile is deferred to the merge kernel.
-  const int nd = s.ndefer;
+  const int nu = s.nunres;
   if (tid == 0) {
-    if (nd > kDeferCap) raise_status(a.status, RTF_STATUS_TIMEOUT);
-    a.item_count[tile] = min(nd, kDeferCap);
+    if (nu > kUnresCap) raise_status(a.status, RTF_STATUS_INVARIANT);
+    a.unres_count[tile] = min(nu, kUnresCap);
   }
-  if (tid < min(nd, kDeferCap)) {
-    a.items[tile * kDeferCap + tid] =
-        make_uint4((uint32_t)s.defer_parent[tid], (uint32_t)s.defer_bound[tid],
-                   (uint32_t)s.defer_node[tid], (uint32_t)s.defer_dist[tid]);
-  }
+  if (tid < min(nu, kUnresCap)) a.unres[tile * kUnresCap + tid] = (int32_t)(t0 + s.unres[tid]);
 }
 
-// Hand-offs across tile edges, after every tile finished: one thread per
-// deferred range continues Algorithm 1 through the global otherBounds.
+// Nearest split j' < j with delta_{j'} > v, or -1 (the array start counts as
+// infinitely far), searched by one warp: splits 32 at a time inside j's tile,
+// then tiles by their largest distance inside j's group of tiles, then groups.
+__device__ int64_t find_left(const ForestArgs& a, int64_t j, uint32_t v) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  auto scan_splits = [&](int64_t hi, int64_t lo) -> int64_t {  // positions hi down to lo
+    for (int64_t pos = hi; pos >= lo; pos -= 32) {
+      const int64_t x = pos - lane;
+      const unsigned m = __ballot_sync(full, x >= lo && a.delta[x] > v);
+      if (m) return pos - (__ffs(m) - 1);
+    }
+    return -1;
+  };
+  auto scan_tiles = [&](int64_t hi, int64_t lo) -> int64_t {
+    for (int64_t t = hi; t >= lo; t -= 32) {
+      const int64_t x = t - lane;
+      const unsigned m = __ballot_sync(full, x >= lo && a.tmax[x] > v);
+      if (m) return t - (__ffs(m) - 1);
+    }
+    return -1;
+  };
+  const int64_t T = j / kTile;
+  int64_t r = scan_splits(j - 1, T * kTile);
+  if (r >= 0) return r;
+  const int64_t G = T / kTileGroup;
+  int64_t t = scan_tiles(T - 1, G * kTileGroup);
+  if (t < 0) {
+    int64_t g = -1;
+    for (int64_t gg = G - 1; gg >= 0 && g < 0; gg -= 32) {
+      const int64_t x = gg - lane;
+      const unsigned m = __ballot_sync(full, x >= 0 && a.gmax[x] > v);
+      if (m) g = gg - (__ffs(m) - 1);
+    }
+    if (g < 0) return -1;
+    t = scan_tiles(g * kTileGroup + kTileGroup - 1, g * kTileGroup);
+  }
+  return scan_splits(min(t * kTile + kTile, a.N) - 1, t * kTile);
+}
+
+// Nearest split j' > j with delta_{j'} >= v (the last split, delta_{N-1}, is
+// a boundary and ends every search).
+__device__ int64_t find_right(const ForestArgs& a, int64_t j, uint32_t v, int64_t ntiles) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  auto scan_splits = [&](int64_t lo, int64_t hi) -> int64_t {  // positions lo up to hi
+    for (int64_t pos = lo; pos <= hi; pos += 32) {
+      const int64_t x = pos + lane;
+      const unsigned m = __ballot_sync(full, x <= hi && a.delta[x] >= v);
+      if (m) return pos + (__ffs(m) - 1);
+    }
+    return -1;
+  };
+  auto scan_tiles = [&](int64_t lo, int64_t hi) -> int64_t {
+    for (int64_t t = lo; t <= hi; t += 32) {
+      const int64_t x = t + lane;
+      const unsigned m = __ballot_sync(full, x <= hi && a.tmax[x] >= v);
+      if (m) return t + (__ffs(m) - 1);
+    }
+    return -1;
+  };
+  const int64_t T = j / kTile;
+  int64_t r = scan_splits(j + 1, min(T * kTile + kTile, a.N) - 1);
+  if (r >= 0) return r;
+  const int64_t G = T / kTileGroup;
+  const int64_t ngroups = (ntiles + kTileGroup - 1) / kTileGroup;
+  int64_t t = scan_tiles(T + 1, min(G * kTileGroup + kTileGroup, ntiles) - 1);
+  if (t < 0) {
+    int64_t g = -1;
+    for (int64_t gg = G + 1; gg < ngroups && g < 0; gg += 32) {
+      const int64_t x = gg + lane;
+      const unsigned m = __ballot_sync(full, x < ngroups && a.gmax[x] >= v);
+      if (m) g = gg + (__ffs(m) - 1);
+    }
+    if (g < 0) return -1;  // cannot happen: delta_{N-1} is a boundary
+    t = scan_tiles(g * kTileGroup, min(g * kTileGroup + kTileGroup, ntiles) - 1);
+  }
+  return scan_splits(t * kTile, min(t * kTile + kTile, a.N) - 1);
+}
+
+// The nodes whose range crosses a tile edge: one warp per tile, one node at a
+// time; the two bounding splits come from the global distances, then the link
+// (or the cell's root and guide entry) is written as inside a tile.
 __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t ntiles) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t tile = i / kDeferCap;
-  const int k = (int)(i % kDeferCap);
-  if (tile >= ntiles || k >= a.item_count[tile]) return;
-  run_deferred(a, a.items[tile * kDeferCap + k]);
+  const int64_t tile = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (tile >= ntiles) return;
+  const int lane = threadIdx.x & 31;
+  const int cnt = a.unres_count[tile];
+  for (int k = 0; k < cnt; ++k) {
+    const int64_t p = a.unres[tile * kUnresCap + k];  // node p: the split between p-1 and p
+    const int64_t j = p - 1;
+    const uint32_t v = a.delta[j];
+    const int64_t jl = find_left(a, j, v);
+    const int64_t jr = find_right(a, j, v, ntiles);
+    if (lane != 0) continue;
+    if (jr < 0) {
+      raise_status(a.status, RTF_STATUS_INVARIANT);
+      continue;
+    }
+    const rtf_dist P = a.dists[a.D > 1 ? find_dist(a.dists, 0, a.D - 1, p) : 0];
+    const int32_t id = (int32_t)(p - P.elem_off);
+    const uint32_t dl = jl >= 0 ? (uint32_t)a.delta[jl] : kDeltaInf;
+    const uint32_t dr = a.delta[jr];
+    if (dl >= kDeltaInf && dr >= kDeltaInf) {
+      // the top of a cell: leaves [jl + 1, jr], root at jl + 1
+      const int64_t lo = jl + 1, hi = jr;
+      a.nodes[lo].child[1] = id;
+      const int32_t lo_l = (int32_t)(lo - P.elem_off);
+      const uint64_t Clo = a.nodes[lo].cdf, Chi = a.nodes[hi].cdf;
+      const uint64_t Clm1 = lo_l > 0 ? a.nodes[lo - 1].cdf : 0ull;
+      const uint64_t Chp1 = hi + 1 < P.elem_off + P.n ? a.nodes[hi + 1].cdf : P.total;
+      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, Chi), Clm1, Clo, Chi, Chp1, id);
+    } else if (dl > dr) {
+      a.nodes[jr + 1].child[0] = id;
+    } else {
+      a.nodes[jl + 1].child[1] = id;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1035,9 +1196,6 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   int32_t* last = reinterpret_cast<int32_t*>(base + L.last);
   uint64_t* tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
   uint8_t* delta = reinterpret_cast<uint8_t*>(base + L.delta);
-  int32_t* other = reinterpret_cast<int32_t*>(base + L.other);
-  uint4* items = reinterpret_cast<uint4*>(base + L.items);
-  int32_t* item_count = reinterpret_cast<int32_t*>(base + L.item_count);
   const bool seg = D > 1;
   const int Dw = marginal ? D - 1 : D;
   const int64_t n_shared = marginal ? Nw : 0;
@@ -1089,9 +1247,10 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.tile_prefix = tile_prefix;
   fa.dmax = dmax;
   fa.delta = delta;
-  fa.other = other;
-  fa.items = items;
-  fa.item_count = item_count;
+  fa.tmax = reinterpret_cast<uint8_t*>(base + L.tmax);
+  fa.gmax = reinterpret_cast<uint32_t*>(base + L.gmax);
+  fa.unres = reinterpret_cast<int32_t*>(base + L.unres);
+  fa.unres_count = reinterpret_cast<int32_t*>(base + L.unres_count);
   fa.status = f->status;
   if (seg) {
     const size_t fsmem = sizeof(ForestShared<true>);
@@ -1108,7 +1267,7 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   }
   {
     const int64_t nt = num_tiles(N);
-    forest_merge_kernel<<<(unsigned)((nt * kDeferCap + 127) / 128), 128, 0, st>>>(fa, nt);
+    forest_merge_kernel<<<(unsigned)((nt + 3) / 4), 128, 0, st>>>(fa, nt);
   }
   const int64_t gtiles = (G + kGuideTile - 1) / kGuideTile;
   guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, fa.last_lo, f->guide,

@@ -24,7 +24,13 @@ constexpr int kGuideThreads = 256;    // 4 cells per thread
 constexpr int kMaxThreads = 512;
 constexpr uint32_t kDeltaInf = 64;    // distance across a cell / distribution boundary
 constexpr long long kSpinLimit = 1ll << 22;   // bounded waits
-constexpr int kDeferCap = 4;          // cross-tile hand-offs a forest tile defers (<= 2 occur)
+// Nodes of a forest tile whose range reaches past the tile (their parent needs
+// distances outside it): at most 33 whose nearest larger distance on the right
+// lies outside (their distances strictly decrease from left to right) plus 33
+// whose nearest larger one on the left lies outside and whose right bound does
+// not settle the parent (strictly increasing distances).
+constexpr int kUnresCap = 72;
+constexpr int kTileGroup = 64;        // forest tiles per group of the distance maxima
 
 // status-word flags of the decoupled lookback (top two bits of a u64)
 constexpr uint64_t kFlagAgg = 1ull << 62;
@@ -40,6 +46,7 @@ struct WsLayout {
   size_t dmax;         // u32 [D] max float bits per distribution / group
   size_t scan_status;  // u64 [num_tiles / 2048 + 1] status of the tile-sum scan blocks
   size_t guide_status; // u64 [num_guide_tiles]
+  size_t gmax;         // u32 [num_tiles / kTileGroup] largest distance per group of tiles
   size_t zero_end;
   size_t last;         // i32 [G] last leaf of each non-empty cell (set to -1)
   size_t last_lo;      // u64 [G] lower CDF bound of that leaf
@@ -48,10 +55,10 @@ struct WsLayout {
   size_t tile_first;   // u64 [num_tiles]
   size_t tile_meta;    // u32 [num_tiles]
   size_t tile_dist0;   // i32 [num_tiles]
-  size_t delta;        // u8  [N]
-  size_t other;        // i32 [N] otherBounds of Algorithm 1 (written by every build)
-  size_t items;        // uint4 [num_tiles * kDeferCap] deferred hand-offs per tile
-  size_t item_count;   // i32 [num_tiles]
+  size_t delta;        // u8  [N] distance between leaves j and j + 1
+  size_t tmax;         // u8  [num_tiles] largest distance of each forest tile
+  size_t unres;        // i32 [num_tiles * kUnresCap] nodes left to the merge pass
+  size_t unres_count;  // i32 [num_tiles]
   size_t total;
 };
 
@@ -68,6 +75,8 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   L.scan_status = o; o = align256(o + sizeof(uint64_t) * (size_t)(num_tiles(N) / 2048 + 1));
   L.guide_status = o;
   o = align256(o + sizeof(uint64_t) * (size_t)((G + kGuideTile - 1) / kGuideTile));
+  L.gmax = o;
+  o = align256(o + sizeof(uint32_t) * (size_t)((num_tiles(N) + kTileGroup - 1) / kTileGroup));
   L.zero_end = o;
   L.last = o; o = align256(o + sizeof(int32_t) * (size_t)G);
   L.last_lo = o; o = align256(o + sizeof(uint64_t) * (size_t)G);
@@ -77,9 +86,9 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   L.tile_meta = o; o = align256(o + sizeof(uint32_t) * (size_t)num_tiles(N));
   L.tile_dist0 = o; o = align256(o + sizeof(int32_t) * (size_t)num_tiles(N));
   L.delta = o; o = align256(o + (size_t)N);
-  L.other = o; o = align256(o + sizeof(int32_t) * (size_t)N);
-  L.items = o; o = align256(o + 16 * (size_t)kDeferCap * (size_t)num_tiles(N));
-  L.item_count = o; o = align256(o + sizeof(int32_t) * (size_t)num_tiles(N));
+  L.tmax = o; o = align256(o + (size_t)num_tiles(N));
+  L.unres = o; o = align256(o + sizeof(int32_t) * (size_t)kUnresCap * (size_t)num_tiles(N));
+  L.unres_count = o; o = align256(o + sizeof(int32_t) * (size_t)num_tiles(N));
   L.total = o;
   return L;
 }
