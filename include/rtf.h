@@ -66,6 +66,9 @@ typedef enum rtf_status {
 #define RTF_STATUS_ZERO_TOTAL 0x2u /* a distribution has no positive weight */
 #define RTF_STATUS_TIMEOUT 0x4u    /* a bounded wait inside a kernel ran out */
 #define RTF_STATUS_BAD_PLAN 0x8u   /* batched plan: n_d < 1, m_d outside [0, 31] */
+#define RTF_STATUS_INVARIANT 0x10u /* an internal bound of the forest construction was
+                                      exceeded (cannot happen for a valid build; the
+                                      forest is incomplete if it is set) */
 
 /* rtf_forest.flags */
 #define RTF_FOREST_MARGINAL 0x1 /* the last distribution is the marginal over the
@@ -216,12 +219,15 @@ rtf_status rtf_build(const float *w, int64_t n, int32_t m, rtf_forest *f,
  * The scratch is a fixed 10 MiB array inside the library, held on every GPU
  * that loads the library until the process exits.  It fits n <= 2^20 weights
  * and m <= 16 guide bits; larger sizes return RTF_EWORKSPACE without touching
- * the GPU.  The first call on a device looks up the array's device address
- * with that device current, so make that first call before capturing a
- * stream.  Every call shares the one array and leaves its contents behind
- * (each call clears what must start at zero): calls that overlap on the GPU,
- * from two streams or two threads, race and corrupt each other's results;
- * serialise them.  Nothing here calls cudaMalloc or cudaFree.
+ * the GPU.  The first call in a CUDA context (normally: the first call on a
+ * device) looks up the array's device address with that context current, so
+ * make that first call before capturing a stream.  The address is kept per
+ * context for the rest of the process; it does not survive cudaDeviceReset,
+ * after which this entry point must not be called again in the same process.
+ * Every call shares the one array and leaves its contents behind (each call
+ * clears what must start at zero): calls that overlap on the GPU, from two
+ * streams or two threads, race and corrupt each other's results; serialise
+ * them.  Nothing here calls cudaMalloc or cudaFree.
  */
 rtf_status rtf_build_static(const float *w, int64_t n, int32_t m, rtf_forest *f,
                             void *stream);

@@ -21,6 +21,7 @@ STATUS_BAD_WEIGHT = 0x1
 STATUS_ZERO_TOTAL = 0x2
 STATUS_TIMEOUT = 0x4
 STATUS_BAD_PLAN = 0x8
+STATUS_INVARIANT = 0x10
 FOREST_MARGINAL = 0x1
 SAMPLE_1D = 0
 SAMPLE_2D = 1
@@ -131,7 +132,8 @@ class Forest:
             names = [n for b, n in ((STATUS_BAD_WEIGHT, "bad weight"),
                                     (STATUS_ZERO_TOTAL, "zero total"),
                                     (STATUS_TIMEOUT, "timeout"),
-                                    (STATUS_BAD_PLAN, "bad plan")) if s & b]
+                                    (STATUS_BAD_PLAN, "bad plan"),
+                                    (STATUS_INVARIANT, "internal bound exceeded")) if s & b]
             raise RtfError(f"device status {s:#x}: {', '.join(names)}")
         return 0
 

@@ -2,8 +2,9 @@
 
 rtf_build_static serves callers that cannot allocate device memory: it keeps
 its scratch in a fixed array inside the library.  Called twice in a row
-through the C interface, it must give the same forest, guide table and samples
-as rtf_build with a caller workspace; sizes beyond its limit are refused.
+through the C interface, on different weights of the same size, it must give
+the same forest, guide table and samples as rtf_build with a caller
+workspace; sizes beyond its limit are refused.
 This file is collected last so that a failure here leaves every other test
 already run.
 """
@@ -29,28 +30,38 @@ def _require_gpu():
         pytest.skip("no CUDA device")
 
 
+def static_build(lib, w, n, m, stream):
+    f = api.Forest(1, 0, n, 1 << m, m, DEV)
+    cf = f.c_struct()
+    rc = lib.rtf_build_static(ctypes.c_void_p(w.data_ptr()), n, m, ctypes.byref(cf), stream)
+    assert rc == 0
+    return f
+
+
 def test_static_build_matches_workspace_build_twice_in_a_row():
+    """Per size, two calls in a row on different weights of the same n and m
+    (so that flags or prefixes left in the shared array by the first call
+    would show in the second), each against rtf_build with a workspace."""
     lib = _native.load()
     stream = ctypes.c_void_p(torch.cuda.current_stream(DEV).cuda_stream)
     cases = [(1 << 20, 16, 0, 2.0), (3 * 2048 + 5, 9, 1, 1.0)]
     for n, m, seed, sigma in cases:
-        w = torch.from_numpy(W.lognormal_weights(n, seed=seed, sigma=sigma)).to(DEV)
-        ref = api.rtf_build(w, m)
-        f = api.Forest(1, 0, n, 1 << m, m, DEV)
-        cf = f.c_struct()
-        rc = lib.rtf_build_static(ctypes.c_void_p(w.data_ptr()), n, m, ctypes.byref(cf), stream)
-        assert rc == 0
-        torch.cuda.synchronize()
-        ref.check_status()
-        f.check_status()
-        assert torch.equal(f.nodes, ref.nodes)
-        assert torch.equal(f.guide, ref.guide)
-        assert torch.equal(f.dists, ref.dists)
-        u = api.u32_tensor(W.iid_u32(1 << 18, seed=seed + 7), DEV)
-        i0, p0 = api.rtf_sample(ref, u)
-        i1, p1 = api.rtf_sample(f, u)
-        assert torch.equal(i0, i1)
-        assert torch.equal(p0, p1)
+        for k, (sd, sg) in enumerate(((seed, sigma), (seed + 100, 1.5 * sigma))):
+            w = torch.from_numpy(W.lognormal_weights(n, seed=sd, sigma=sg)).to(DEV)
+            ref = api.rtf_build(w, m)
+            f = static_build(lib, w, n, m, stream)
+            torch.cuda.synchronize()
+            ref.check_status()
+            f.check_status()
+            assert torch.equal(f.nodes, ref.nodes), (n, k)
+            assert torch.equal(f.guide, ref.guide), (n, k)
+            assert torch.equal(f.guide_recs, ref.guide_recs), (n, k)
+            assert torch.equal(f.dists, ref.dists), (n, k)
+            u = api.u32_tensor(W.iid_u32(1 << 18, seed=sd + 7), DEV)
+            i0, p0 = api.rtf_sample(ref, u)
+            i1, p1 = api.rtf_sample(f, u)
+            assert torch.equal(i0, i1)
+            assert torch.equal(p0, p1)
 
 
 def test_static_build_refuses_sizes_beyond_its_array():
