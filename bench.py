@@ -43,15 +43,33 @@ LAUNCHES_PER_STEP_ACC = 7 + 1 + 8 + 8 + 2
 
 
 # DRAM bytes per unit measured by ncu at full size (dram__bytes_read.sum +
-# dram__bytes_write.sum per launch / units per launch; profiles/launches_bench_n24.md).
-# Valid for the kernels as they were captured; set an entry to None when its
-# kernel changes until the capture is repeated.
-DRAM_BYTES_PER_UNIT = {
-    "sample_iid": (37.956e9 + 2.143e9) / (1 << 28),
-    "sample_sorted": (1.358e9 + 2.088e9) / (1 << 28),
-    "backward": None,
-    "build": None,
+# dram__bytes_write.sum per launch / units per launch;
+# profiles/launches_bench_n24.md), with the SHA-256 prefixes of the kernel
+# sources they were captured from.  An entry whose sources have changed since
+# is reported as null until the capture is repeated.
+TRAFFIC_CAPTURES = {
+    "sample_iid": {
+        "bytes_per_unit": (37.956e9 + 2.143e9) / (1 << 28),
+        "sources": {"paper_1901_05423_gb300/csrc/sample.cu": "6550e65c35a91f1c",
+                    "paper_1901_05423_gb300/csrc/sample_common.cuh": "7836d4584a4ff2cf"},
+    },
 }
+
+
+def _sha16(rel: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def traffic_per_unit(kernel: str):
+    """(bytes per unit, "current" | "stale" | "none") of an ncu capture."""
+    cap = TRAFFIC_CAPTURES.get(kernel)
+    if cap is None:
+        return None, "none"
+    if any(_sha16(f) != h for f, h in cap["sources"].items()):
+        return None, "stale"
+    return cap["bytes_per_unit"], "current"
 
 
 def max_over_ranks(ms: float, dist=None, device=None) -> float:
@@ -167,57 +185,102 @@ def make_inputs(sorted_dense=False):
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
 
-def time_oracle(w, u_iid, u_sorted, gx, sample_count=1 << 21):
+def time_oracle(w, u_iid, u_sorted, gx, sample_count=1 << 21, threads=1):
+    """The oracle on a bounded sample of one step: the build of n = 2^24
+    (sequential by definition), index + position of `sample_count` samples of
+    each set (on `threads` host threads, the samples cut into contiguous
+    chunks) and the gradient of `sample_count` samples (sequential); scaled
+    linearly to 2^28 samples per set."""
     from oracle import oracle as orc
+    t_all = time.perf_counter()
     t0 = time.perf_counter()
     st = orc.build(w, 1 << M_BITS)
     t_build = time.perf_counter() - t0
     ui = u_iid[:sample_count]
     us = u_sorted[::max(1, N_S // sample_count)][:sample_count]
     t0 = time.perf_counter()
-    idx_i, _ = orc.sample(st.C, ui)
-    orc.sample(st.C, us)
+    idx_i, _ = orc.sample(st.C, ui, threads=threads)
+    orc.sample(st.C, us, threads=threads)
     t_sample = time.perf_counter() - t0
     t0 = time.perf_counter()
-    orc.grad(w, ui, idx_i, gx[:sample_count])
+    orc.grad_q(st.C, st.S, ui, idx_i, gx[:sample_count])
     t_grad = time.perf_counter() - t0
+    measured = time.perf_counter() - t_all
     scale = N_S / sample_count
     step = t_build + t_sample * scale + t_grad * scale
+    lg = N_S.bit_length() - 1
     return {
         "step_s": step,
+        "measured_s": measured,
+        "scale": scale,
         "value": 2 * N_S / step,
         "build_elem_per_s": N_W / t_build,
-        "sample": (f"oracle build of n=2^24 (timed once), index+position on {sample_count} "
-                   f"i.i.d. + {sample_count} sorted samples and the gradient on {sample_count} "
-                   f"samples, scaled linearly to 2^{N_S.bit_length() - 1} samples per set"),
+        "sample_per_s": 2 * sample_count / t_sample,
+        "sample": (f"oracle build of n=2^24 (timed once, 1 core), index+position on {sample_count} "
+                   f"i.i.d. + {sample_count} sorted samples on {threads} host thread(s), the "
+                   f"gradient on {sample_count} samples (1 core); sampling and gradient scaled "
+                   f"linearly by {scale:g} to 2^{lg} samples per set"),
     }
 
 
+def cpu_baseline(w, u_iid, u_sorted, gx, sample_count=1 << 21):
+    """The oracle on one host core and on all of them (sampling threaded)."""
+    from oracle import oracle as orc
+    cores = orc.host_threads()
+    one = time_oracle(w, u_iid, u_sorted, gx, sample_count, threads=1)
+    allc = time_oracle(w, u_iid, u_sorted, gx, sample_count, threads=cores)
+    return {"value": allc["value"], "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": allc["sample"], "host_cores": os.cpu_count(),
+            "value_1core": one["value"], "sample_1core": one["sample"],
+            "sample_per_s": allc["sample_per_s"], "sample_per_s_1core": one["sample_per_s"],
+            "build_elem_per_s": one["build_elem_per_s"]}
+
+
+def workload_config(world: int, streams: int, sorted_dense: bool = False) -> dict:
+    lg = N_S.bit_length() - 1
+    return {"workload": f"n=2^24 lognormal(0,2) weights, 2^20 guide cells, "
+                        f"2^{lg} iid + 2^{lg} sorted radical-inverse samples"
+                        + (" (the first of the 2^28 set)" if sorted_dense else "")
+                        + ", backward on the iid set",
+            "l2": "inputs larger than L2", "parallelism": f"replicas{world}",
+            "streams": {1: "1", 2: "2: sorted set concurrent with the i.i.d. set and "
+                                    "the backward",
+                        3: "3: sorted set concurrent; backward accumulated per chunk of "
+                           "the i.i.d. set while later chunks are mapped"}[streams]}
+
+
 def reference_arm(args):
+    """The oracle timed on the host cores (rank 0 only).  Each step is the
+    build plus a bounded sample of 2^19 samples per set (sampling on all host
+    cores); `ms_per_step` is that measured step, `value` the throughput of the
+    full step extrapolated from it (scale factor in `extrapolation`)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import oracle as orc
     w, u_iid, u_sorted, gx = make_inputs()
-    times = []
+    cores = orc.host_threads()
+    measured, full = [], []
     res = None
     for it in range(args.warmup + args.steps):
-        res = time_oracle(w, u_iid, u_sorted, gx, sample_count=1 << 19)
+        res = time_oracle(w, u_iid, u_sorted, gx, sample_count=1 << 19, threads=cores)
         if it >= args.warmup:
-            times.append(res["step_s"])
-    step = float(np.mean(times))
+            measured.append(res["measured_s"])
+            full.append(res["step_s"])
+    step = float(np.mean(full))
     value = 2 * N_S / step
-    lg = N_S.bit_length() - 1
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"n=2^24 lognormal(0,2) weights, 2^20 guide cells, "
-                               f"2^{lg} iid + 2^{lg} sorted radical-inverse samples, "
-                               f"backward on the iid set",
-                   "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                         "sample": res["sample"].replace(str(1 << 21), str(1 << 19))},
+        "ms_per_step": float(np.mean(measured)) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(args.gpus, args.streams),
+        "extrapolation": {"timed_samples_per_set": 1 << 19, "scale": res["scale"],
+                          "full_step_ms": step * 1e3,
+                          "value_basis": "samples of the full step (2 x 2^28) per second of "
+                                         "the extrapolated full step"},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": res["sample"], "host_cores": os.cpu_count()},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -466,7 +529,7 @@ def gpu_arm(args):
     dom = "sample_iid"
     achieved = alg[dom] / (avg[dom] * 1e-3) / 1e9
     units = {"build": N_W, "sample_iid": N_S, "sample_sorted": N_S, "backward": N_S}
-    per_unit = DRAM_BYTES_PER_UNIT.get(dom)
+    per_unit, traffic_state = traffic_per_unit(dom)
     traffic = per_unit * units[dom] if per_unit is not None else None
     value = job_throughput(world, 2 * N_S, ms)
     lg = N_S.bit_length() - 1
@@ -475,15 +538,7 @@ def gpu_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": f"n=2^24 lognormal(0,2) weights, 2^20 guide cells, "
-                               f"2^{lg} iid + 2^{lg} sorted radical-inverse samples"
-                               + (" (the first of the 2^28 set)" if args.sorted_dense else "")
-                               + ", backward on the iid set",
-                   "l2": "inputs larger than L2", "parallelism": f"replicas{world}",
-                   "streams": {1: "1", 2: "2: sorted set concurrent with the i.i.d. set and "
-                                           "the backward",
-                               3: "3: sorted set concurrent; backward accumulated per chunk of "
-                                  "the i.i.d. set while later chunks are mapped"}[args.streams]},
+        "config": workload_config(world, args.streams, args.sorted_dense),
         "breakdown_ms": avg,
         "build_elem_per_s": N_W / (alone_ms["build"] * 1e-3),
         "sample_iid_per_s": N_S / (alone_ms["sample_iid"] * 1e-3),
@@ -494,7 +549,7 @@ def gpu_arm(args):
                      # the DRAM bytes ncu measured for this kernel (random node and guide
                      # lines included) against the same peak
                      "traffic_frac": traffic / (avg[dom] * 1e-3) / 1e9 / peak if traffic else None,
-                     "peak_kind": peak_kind},
+                     "traffic_capture": traffic_state, "peak_kind": peak_kind},
         "alone_ms": alone_ms,
         "fractions_of_hbm": {k: alg[k] / (alone_ms[k] * 1e-3) / 1e9 / peak for k in alone_ms},
         "e2e": {"value": job_throughput(world, 2 * N_S, max_over_ranks(e2e_ms, dist, dev)),
@@ -509,10 +564,7 @@ def gpu_arm(args):
                           "backward_vs_forward": extra_backward(dev),
                           "forest_vs_binary_search": extra_methods(dev)}
     if rank == 0 and not args.no_cpu_baseline:
-        cb = time_oracle(w, u_iid, u_sorted, gx)
-        line["cpu_baseline"] = {"value": cb["value"], "unit": "samples/s", "cores": 1,
-                                "kind": "oracle", "sample": cb["sample"],
-                                "build_elem_per_s": cb["build_elem_per_s"]}
+        line["cpu_baseline"] = cpu_baseline(w, u_iid, u_sorted, gx)
     if rank == 0:
         print(json.dumps(line))
     if dist:

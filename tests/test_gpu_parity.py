@@ -38,12 +38,20 @@ def ulp_dist(pos_gpu, pos_ref64):
     return np.abs(a - b)
 
 
-def check_structure(f, ref, elem_off=0, guide_off=0, n=None, cells=None):
+def host_structure(f):
+    """The forest's device arrays copied to the host once: CDF, children,
+    guide table, guide records."""
+    return (f.cdf().cpu().numpy().view(np.uint64), f.children().cpu().numpy(),
+            f.guide.cpu().numpy(), f.guide_records().cpu().numpy())
+
+
+def check_structure(f, ref, elem_off=0, guide_off=0, n=None, cells=None, host=None):
+    host = host_structure(f) if host is None else host
     n = ref.n if n is None else n
     cells = ref.M if cells is None else cells
-    C = f.cdf()[elem_off:elem_off + n].cpu().numpy().view(np.uint64)
-    ch = f.children()[elem_off:elem_off + n].cpu().numpy()
-    g = f.guide[guide_off:guide_off + cells].cpu().numpy()
+    C = host[0][elem_off:elem_off + n]
+    ch = host[1][elem_off:elem_off + n]
+    g = host[2][guide_off:guide_off + cells]
     assert np.array_equal(C, ref.C[:-1]), "CDF"
     bad = np.nonzero((ch != ref.nodes).any(axis=1))[0]
     assert bad.size == 0, f"{bad.size} node records differ, first {bad[:5]}"
@@ -52,7 +60,7 @@ def check_structure(f, ref, elem_off=0, guide_off=0, n=None, cells=None):
     # guide records: a copy of each root's record with the bounds C_{j0-1} and
     # C_{j1+1} of the cell's outer intervals; {C_i, ~i, ~i, C_i, C_{i+1}} for a
     # cell that one interval i covers
-    rec = f.guide_records()[guide_off:guide_off + cells].cpu().numpy()
+    rec = host[3][guide_off:guide_off + cells]
     rec_c = rec[:, 0].view(np.uint64)
     rec_ch = rec[:, 1:2].copy().view(np.int32)
     rec_lo = rec[:, 2].view(np.uint64)
@@ -73,6 +81,36 @@ def check_structure(f, ref, elem_off=0, guide_off=0, n=None, cells=None):
         "guide record children"
     assert np.array_equal(rec_lo, exp_lo), "guide record lower bound"
     assert np.array_equal(rec_hi, exp_hi), "guide record upper bound"
+
+
+def oracle_builds(ws, ms, threads=None):
+    """orc.build of every distribution (a thread pool over the independent
+    builds; the oracle's calls release the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(threads or orc.host_threads()) as ex:
+        return list(ex.map(lambda a: orc.build(a[0], 1 << int(a[1])), zip(ws, ms)))
+
+
+def oracle_tagged(refs, u, dist):
+    """Index and position of every tagged sample through the oracle of its
+    distribution (samples grouped by distribution, a thread pool over the
+    distributions)."""
+    from concurrent.futures import ThreadPoolExecutor
+    order = np.argsort(dist, kind="stable")
+    bounds = np.searchsorted(dist[order], np.arange(len(refs) + 1))
+    ridx = np.empty(u.size, np.int32)
+    rpos = np.empty(u.size, np.float64)
+
+    def run(d):
+        sel = order[bounds[d]:bounds[d + 1]]
+        if sel.size:
+            i, p = orc.sample(refs[d].C, u[sel])
+            ridx[sel] = i
+            rpos[sel] = p
+
+    with ThreadPoolExecutor(orc.host_threads()) as ex:
+        list(ex.map(run, range(len(refs))))
+    return ridx, rpos
 
 
 def check_samples(idx, pos, ridx, rpos):
@@ -267,6 +305,8 @@ def test_full_size_samples(big):
 # ---------------------------------------------------------------------------
 
 def batched_check(w, offsets, ms, samples_per=512, seed=0):
+    """Every distribution's structure against the oracle's, and tagged samples
+    (samples_per per distribution, up to 64 distributions' worth)."""
     sizes = np.diff(offsets)
     f = api.rtf_build_batched(to_dev(w), sizes, ms)
     torch.cuda.synchronize()
@@ -277,17 +317,12 @@ def batched_check(w, offsets, ms, samples_per=512, seed=0):
     dist = rng.integers(0, D, samples_per * min(D, 64), dtype=np.int64).astype(np.int32)
     u = rng.integers(0, 1 << 32, dist.size, dtype=np.uint64).astype(np.uint32)
     idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV), dist_id=to_dev(dist))
-    idx = idx.cpu().numpy()
-    pos = pos.cpu().numpy()
-    check_ds = sorted(set(rng.integers(0, D, 64).tolist()) | {0, D - 1})
-    for d in check_ds:
-        wd = w[offsets[d]:offsets[d + 1]]
-        ref = orc.build(wd, 1 << int(ms[d]))
-        check_structure(f, ref, elem_off=int(offsets[d]), guide_off=int(goff[d]))
-        sel = dist == d
-        if sel.any():
-            ridx, rpos = orc.sample(ref.C, u[sel])
-            check_samples(idx[sel], pos[sel], ridx, rpos)
+    refs = oracle_builds([w[offsets[d]:offsets[d + 1]] for d in range(D)], ms)
+    host = host_structure(f)
+    for d in range(D):
+        check_structure(f, refs[d], elem_off=int(offsets[d]), guide_off=int(goff[d]), host=host)
+    ridx, rpos = oracle_tagged(refs, u, dist)
+    check_samples(idx, pos, ridx, rpos)
     return f
 
 
@@ -302,18 +337,67 @@ def test_batched_small_ragged():
 
 
 def test_batched_ragged_full_config():
-    """16384 distributions, sizes log-uniform in [8, 65536], lognormal(0, 1.5)."""
+    """The ragged workload in full: 16384 distributions, sizes log-uniform in
+    [8, 65536], lognormal(0, 1.5), the autotuned guide bits the benchmark
+    uses, 2^27 samples with uniform distribution ids.  Every distribution's
+    structure and every sample against the oracle; then the batched build and
+    the tagged sampling captured in one CUDA graph and replayed twice give the
+    same bits."""
+    from paper_1901_05423_gb300 import autotune
     w, offsets = W.ragged_batch(16384, seed=0)
     sizes = np.diff(offsets)
-    ms = np.clip(np.round(np.log2(sizes)).astype(int), 3, 16)
-    batched_check(w, offsets, ms, samples_per=1024)
+    ms = autotune.guide_bits_for(sizes, autotune.tune(DEV))
+    D = sizes.size
+    wd = to_dev(w)
+    f = api.rtf_build_batched(wd, sizes, ms)
+    ns = 1 << 27
+    u = W.iid_u32(ns, seed=1)
+    dist = W.dist_ids(ns, D, seed=2)
+    ud, dd = api.u32_tensor(u, DEV), to_dev(dist)
+    idx, pos = api.rtf_sample(f, ud, dist_id=dd)
+    torch.cuda.synchronize()
+    f.check_status()
+    goff = f.guide_offsets
+    refs = oracle_builds([w[offsets[d]:offsets[d + 1]] for d in range(D)], ms)
+    host = host_structure(f)
+    for d in range(D):
+        check_structure(f, refs[d], elem_off=int(offsets[d]), guide_off=int(goff[d]), host=host)
+    ridx, rpos = oracle_tagged(refs, u, dist)
+    check_samples(idx, pos, ridx, rpos)
+    del ridx, rpos
+    # graph capture of build + tagged sampling, replayed
+    f.nodes.zero_()
+    f.guide.zero_()
+    idx2, pos2 = torch.zeros_like(idx), torch.zeros_like(pos)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            api.rtf_build_batched(wd, sizes, ms, forest=f, plan_dev=f._plan_dev)
+            api.rtf_sample(f, ud, dist_id=dd, idx_out=idx2, pos_out=pos2)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        f.check_status()
+        h2 = host_structure(f)
+        assert all(np.array_equal(a, b) for a, b in zip(host, h2))
+        assert torch.equal(idx, idx2)
+        assert torch.equal(pos.view(torch.int32), pos2.view(torch.int32))
+        idx2.zero_()
+        pos2.zero_()
+        f.nodes.zero_()
 
 
 # ---------------------------------------------------------------------------
 # 2-D environment map (marginal + conditionals in one batched build)
 # ---------------------------------------------------------------------------
 
-def env_check(H, Wd, m_row, m_col, n_s, seed=0):
+def env_check(H, Wd, m_row, m_col, n_s, seed=0, stride=1):
+    """The marginal's and every row's structure against the oracle's, and the
+    sample pairs (every `stride`-th, plus the last 4096) against the oracle's
+    component-wise sampling."""
     lum = W.env_map(H, Wd, seed=seed)
     sizes = [Wd] * H + [H]
     ms = [m_col] * H + [m_row]
@@ -321,18 +405,20 @@ def env_check(H, Wd, m_row, m_col, n_s, seed=0):
     torch.cuda.synchronize()
     f.check_status()
     rows, marg = orc.build_env(lum, 1 << m_row, 1 << m_col)
-    check_structure(f, marg, elem_off=H * Wd, guide_off=H << m_col)
+    host = host_structure(f)
+    check_structure(f, marg, elem_off=H * Wd, guide_off=H << m_col, host=host)
+    for r in range(H):
+        check_structure(f, rows[r], elem_off=r * Wd, guide_off=r << m_col, host=host)
     rng = np.random.default_rng(seed)
-    for r in sorted(set(rng.integers(0, H, 16).tolist()) | {0, H - 1}):
-        check_structure(f, rows[r], elem_off=r * Wd, guide_off=r << m_col)
     u = rng.integers(0, 1 << 32, 2 * n_s, dtype=np.uint64).astype(np.uint32)
     idx, pos = api.rtf_sample(f, api.u32_tensor(u, DEV), mode=api.SAMPLE_2D)
     idx = idx.cpu().numpy()
     pos = pos.cpu().numpy()
-    k = min(n_s, 1 << 16)
-    r, c, pr, pc = orc.sample_env(rows, marg, u[0:2 * k:2], u[1:2 * k:2])
-    check_samples(idx[:k, 0], pos[:k, 0], r, pr)
-    check_samples(idx[:k, 1], pos[:k, 1], c, pc)
+    sel = np.unique(np.concatenate([np.arange(0, n_s, stride),
+                                    np.arange(max(0, n_s - 4096), n_s)]))
+    r, c, pr, pc = orc.sample_env(rows, marg, u[2 * sel], u[2 * sel + 1])
+    check_samples(idx[sel, 0], pos[sel, 0], r, pr)
+    check_samples(idx[sel, 1], pos[sel, 1], c, pc)
     return f, lum
 
 
@@ -343,8 +429,10 @@ def test_env_map_small():
 
 def test_env_map_full_config():
     """4096 x 2048 luminance with hot spots; marginal over 2048 rows and 2048
-    conditionals built in one batched launch sequence; 2^26 sample pairs."""
-    env_check(2048, 4096, 12, 12, 1 << 26)
+    conditionals built in one batched launch sequence: every row and the
+    marginal bit for bit; every 16th of the 2^26 sample pairs and the last
+    4096 against the oracle."""
+    env_check(2048, 4096, 12, 12, 1 << 26, stride=16)
 
 
 # ---------------------------------------------------------------------------
