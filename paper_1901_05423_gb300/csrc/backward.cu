@@ -160,11 +160,25 @@ __device__ __forceinline__ dflt qweight_df(uint64_t q, int S) {
   return dflt{scalbnf(v.hi, -S), scalbnf(v.lo, -S)};
 }
 
+// 2^-S as a float, exact for S <= 126; 0 otherwise (the caller then scales
+// with scalbnf).
+__device__ __forceinline__ float pow2_neg(int S) {
+  return (S >= -127 && S <= 126) ? __int_as_float((127 - S) << 23) : 0.0f;
+}
+
+// Reciprocal estimate (relative error below 2^-22, subnormals kept); the
+// residual step of df_div makes the quotient accurate to about 2^-44.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // {a, b} = {A / w', X / w'} for the per-bin sums {A, X} and the quantised
 // weight w' = wh + wl (zero for an empty bin or a zero weight).
 __device__ __forceinline__ void bin_terms(float2 ax, float wh, float wl, dflt* a, dflt* b) {
   if ((ax.x != 0.0f || ax.y != 0.0f) && wh != 0.0f) {
-    const float inv = __frcp_rn(wh);
+    const float inv = rcp_approx(wh);
     *a = df_div(ax.x, wh, wl, inv);
     *b = df_div(ax.y, wh, wl, inv);
   } else {
@@ -303,11 +317,19 @@ __global__ void __launch_bounds__(kBwThreads)
                      const rtf_dist* __restrict__ dists, int D, int64_t N, double* G) {
   __shared__ int dfirst_s, dlast_s;
   __shared__ double part[kBwThreads / 32];
+  __shared__ dflt invT_s;
+  __shared__ double K_s;
   const int64_t t0 = (int64_t)blockIdx.x * kBwTile;
   const int64_t t1 = min(t0 + (int64_t)kBwTile, N);
   if (threadIdx.x == 0) {
-    dfirst_s = find_dist(dists, 0, D - 1, t0);
-    dlast_s = find_dist(dists, dfirst_s, min(D - 1, dfirst_s + kBwTile), t1 - 1);
+    const int df = find_dist(dists, 0, D - 1, t0);
+    dfirst_s = df;
+    dlast_s = find_dist(dists, df, min(D - 1, df + kBwTile), t1 - 1);
+    // 1 / T and 2^S / T of the block's first distribution, once per block (fp64
+    // divisions are slow on this part)
+    const double T = (double)dists[df].total;
+    invT_s = df_from_double(1.0 / T);
+    K_s = ldexp(1.0, dists[df].scale) / T;
   }
   __syncthreads();
   const int dfirst = dfirst_s, dlast = dlast_s;
@@ -318,8 +340,14 @@ __global__ void __launch_bounds__(kBwThreads)
   if (e0 < t1) {
     rtf_dist P = dists[d];
     int64_t end = P.elem_off + P.n;
-    dflt invT = df_from_double(1.0 / (double)P.total);
-    double K = ldexp(1.0, P.scale) / (double)P.total;
+    dflt invT = invT_s;
+    double K = K_s;
+    if (d != dfirst) {
+      invT = df_from_double(1.0 / (double)P.total);
+      K = ldexp(1.0, P.scale) / (double)P.total;
+    }
+    bool marg = (P.flags & kDistMarginal) != 0;
+    float p2 = pow2_neg(P.scale);
     dflt sac = df_zero(), sx = df_zero();
     uint64_t cnext = nodes[e0].cdf;
     const int64_t e1 = min(e0 + (int64_t)kBwPer, t1);
@@ -334,6 +362,8 @@ __global__ void __launch_bounds__(kBwThreads)
         end = P.elem_off + P.n;
         invT = df_from_double(1.0 / (double)P.total);
         K = ldexp(1.0, P.scale) / (double)P.total;
+        marg = (P.flags & kDistMarginal) != 0;
+        p2 = pow2_neg(P.scale);
       }
       const uint64_t c = cnext;
       cnext = (e + 1 < N) ? nodes[e + 1].cdf : 0ull;
@@ -341,7 +371,14 @@ __global__ void __launch_bounds__(kBwThreads)
       const float2 ax = acc[e];
       const uint64_t q = cup - c;
       if ((ax.x != 0.0f || ax.y != 0.0f) && q != 0) {
-        const dflt wq = qweight_df(q, P.scale);
+        // a row weight's q has at most 24 significant bits: w' is one float
+        dflt wq;
+        if (marg) {
+          wq = qweight_df(q, P.scale);
+        } else {
+          const float qf = __ull2float_rn(q);
+          wq = dflt{p2 != 0.0f ? qf * p2 : scalbnf(qf, -P.scale), 0.0f};
+        }
         dflt av, bv;
         bin_terms(ax, wq.hi, wq.lo, &av, &bv);
         sac = df_add(sac, df_mul(av, df_mul(df_from_u64(c), invT)));
