@@ -942,6 +942,321 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
   if (tid < min(nu, kUnresCap)) a.unres[tile * kUnresCap + tid] = (int32_t)(t0 + s.unres[tid]);
 }
 
+// ---------------------------------------------------------------------------
+// forest of one distribution: the same links on a register-resident tile
+// ---------------------------------------------------------------------------
+// Results identical to forest_kernel<false>.  Warp w owns the 128 consecutive
+// leaves [128 w, 128 w + 128) of the tile and lane l the leaves
+// 128 w + 32 k + l (k = 0..3): each k is one coalesced access to 32
+// consecutive weights, distance bytes or records, the exact prefix sum runs on
+// warp shuffles with one block-wide combine, a leaf's right-hand neighbour key
+// comes by shuffle, and the ballots of one k are the bit planes of 32
+// consecutive split positions.  Chunk c = 4 w + k holds positions
+// 32 c + 1 .. 32 c + 32, the right-hand splits of the chunk's leaves; position 0
+// (delta_{t0-1}) lies in no chunk.
+struct LeanShared {
+  alignas(16) uint64_t C[kTile + 2];  // C_{t0-1} .. C_{t1}
+  alignas(16) int32_t child[kTile][2];
+  uint32_t cell_range[kTile];         // cells complete inside the tile: first | last << 16
+  uint8_t d[kTile + 8];               // d[p]: distance at position p
+  // per chunk: gtm[c][t] = positions with a distance > t, for t up to the
+  // chunk's largest finite distance fmax[c]; above it only the boundaries
+  // (infinite distance, mask infm[c]) are larger
+  uint32_t gtm[kChunks][32];
+  uint32_t valid[kChunks];
+  uint32_t infm[kChunks];
+  int32_t fmax[kChunks];
+  uint32_t cmax[kChunks];
+  uint64_t wtot[kForestThreads / 32];
+  uint64_t Kfirst[kForestThreads / 32 + 1];  // key of each warp's first leaf; [16]: of leaf t1
+  uint64_t prefix;
+  uint64_t Kprev;  // key of leaf t0 - 1
+  uint32_t tmax;
+  int nunres;
+  int ncells;
+  int32_t unres[kUnresCap];
+};
+
+// 64-bit warp shuffles
+__device__ __forceinline__ uint64_t shfl_up64(uint64_t x, int d) {
+  return __shfl_up_sync(0xffffffffu, (unsigned long long)x, d);
+}
+__device__ __forceinline__ uint64_t shfl_down64(uint64_t x, int d) {
+  return __shfl_down_sync(0xffffffffu, (unsigned long long)x, d);
+}
+__device__ __forceinline__ uint64_t shfl_idx64(uint64_t x, int l) {
+  return __shfl_sync(0xffffffffu, (unsigned long long)x, l);
+}
+
+// Positions of chunk c with a distance > v (v below kDeltaInf).
+__device__ __forceinline__ uint32_t chunk_gt(const LeanShared& s, int c, uint32_t v) {
+  return ((int)v <= s.fmax[c] && v < 32) ? s.gtm[c][v] : s.infm[c];
+}
+
+// ... with a distance >= v.
+__device__ __forceinline__ uint32_t chunk_ge(const LeanShared& s, int c, uint32_t v) {
+  return v == 0 ? s.valid[c] : chunk_gt(s, c, v - 1);
+}
+
+// Search of chunks c2 = from, from - 1, ... (dir -1, nearest position with a
+// distance > v) or from, from + 1, ... below nchunks (dir +1, nearest with a
+// distance >= v); -1 when no chunk holds one.
+__device__ __forceinline__ int lean_walk(const LeanShared& s, int from, int nchunks, uint32_t v,
+                                         int dir) {
+  for (int c2 = from; c2 >= 0 && c2 < nchunks; c2 += dir) {
+    if (dir < 0 ? s.cmax[c2] > v : s.cmax[c2] >= v) {
+      return dir < 0 ? 32 * c2 + 1 + (31 - __clz(chunk_gt(s, c2, v)))
+                     : 32 * c2 + __ffs(chunk_ge(s, c2, v));
+    }
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_kernel(ForestArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LeanShared& s = *reinterpret_cast<LeanShared*>(smem_raw);
+  const int64_t tile = blockIdx.x;
+  const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
+  const int tn = (int)(t1 - t0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S = a.dists[0].scale;
+  const int lbase = 128 * warp + lane;  // tile-local leaf of k = 0
+
+  // ---- weights, quantisation, prefix sums within the warp's 128 leaves -----
+  float wv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int l = lbase + 32 * k;
+    wv[k] = l < tn ? __ldg(a.w + t0 + l) : 0.0f;
+  }
+  if (tid == 0) {
+    s.nunres = 0;
+    s.ncells = 0;
+    s.tmax = 0;
+    s.prefix = t0 > 0 ? a.tile_prefix[tile] : 0ull;
+  }
+  uint64_t C[4];
+  uint64_t run = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t b = weight_bits(wv[k]);
+    const uint64_t x = (lbase + 32 * k < tn && !weight_bad(b)) ? quantize_bits(b, S) : 0ull;
+    uint64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = shfl_up64(incl, o);
+      if (lane >= o) incl += y;
+    }
+    C[k] = run + incl - x;
+    run += shfl_idx64(incl, 31);
+  }
+  if (lane == 0) s.wtot[warp] = run;
+  __syncthreads();
+  // the warp's offset in the tile, the tile's prefix, C_{t0-1} and C_{t1}
+  uint64_t off = lane < warp ? s.wtot[lane] : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, (unsigned long long)off, o);
+  const uint64_t pre = s.prefix + off;
+  const uint64_t T = a.dists[0].total, R = a.dists[0].recip;
+  const int z = a.dists[0].shift, m = a.dists[0].m;
+  uint64_t K[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    C[k] += pre;
+    K[k] = key_of(C[k], T, R, z);
+    const int l = lbase + 32 * k;
+    if (l < tn) {
+      s.C[l + 1] = C[k];
+      s.child[l][0] = kUnset;
+      s.child[l][1] = kUnset;
+    }
+  }
+  if (lane == 0) s.Kfirst[warp] = K[0];
+  if (tid == 0) {
+    uint64_t tot = 0;
+    for (int k = 0; k < kForestThreads / 32; ++k) tot += s.wtot[k];
+    const uint64_t Ct1 = s.prefix + tot;
+    s.C[tn + 1] = Ct1;
+    s.Kfirst[kForestThreads / 32] = key_of(Ct1, T, R, z);
+    uint64_t Cp = 0;
+    if (t0 > 0) {
+      const uint32_t b = weight_bits(a.w[t0 - 1]);
+      Cp = s.prefix - (weight_bad(b) ? 0ull : quantize_bits(b, S));
+    }
+    s.C[0] = Cp;
+    s.Kprev = key_of(Cp, T, R, z);
+  }
+  __syncthreads();
+
+  // ---- distances and their bit planes ---------------------------------------
+  uint32_t dmx = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int l = lbase + 32 * k;
+    const uint64_t same = shfl_down64(K[k], 1);
+    const uint64_t nextk = k < 3 ? shfl_idx64(K[k < 3 ? k + 1 : k], 0) : s.Kfirst[warp + 1];
+    const uint64_t Kn = lane < 31 ? same : nextk;
+    uint32_t dlt = kDeltaInf;
+    if (l < tn && t0 + l + 1 < a.N && cell_of(K[k], m) == cell_of(Kn, m))
+      dlt = key_distance(K[k], Kn);
+    if (l < tn) {
+      s.d[l + 1] = (uint8_t)dlt;
+      a.delta[t0 + l] = (uint8_t)dlt;
+      dmx = max(dmx, dlt);
+    }
+    const uint32_t v = l < tn ? min(dlt, kDeltaTop) : 0u;
+    const int c = 4 * warp + k;
+    const uint32_t vm = __ballot_sync(0xffffffffu, l < tn);
+    const uint32_t inf = __ballot_sync(0xffffffffu, l < tn && dlt >= kDeltaInf);
+    const uint32_t mx = __reduce_max_sync(0xffffffffu, v);
+    const int fm = (int)__reduce_max_sync(0xffffffffu, (l < tn && dlt < kDeltaInf) ? dlt + 1 : 0u) - 1;
+    uint32_t mine = 0u;
+    for (int t = 0; t <= min(fm, 31); ++t) {
+      const uint32_t mt = __ballot_sync(0xffffffffu, v > (uint32_t)t);
+      if (lane == t) mine = mt;
+    }
+    if (lane <= fm) s.gtm[c][lane] = mine;
+    if (lane == 0) {
+      s.valid[c] = vm;
+      s.infm[c] = inf;
+      s.fmax[c] = fm;
+      s.cmax[c] = mx;
+    }
+  }
+  dmx = __reduce_max_sync(0xffffffffu, dmx);
+  if (lane == 0 && dmx) atomicMax(&s.tmax, dmx);
+  if (tid == 0) {
+    uint32_t d0 = kDeltaInf;
+    if (t0 > 0 && cell_of(s.Kprev, m) == cell_of(K[0], m)) d0 = key_distance(s.Kprev, K[0]);
+    s.d[0] = (uint8_t)d0;
+  }
+  const int nchunks = (tn + 31) >> 5;
+  __syncthreads();
+  if (tid == 0) {
+    a.tmax[tile] = (uint8_t)s.tmax;
+    if (s.tmax) atomicMax(a.gmax + tile / kTileGroup, s.tmax);
+  }
+
+  // ---- links -----------------------------------------------------------------
+  const rtf_dist& P = a.dists[0];
+  // node at position 0 (delta_{t0-1}): its left bound lies outside the tile
+  if (tid == 0) {
+    const uint32_t v = s.d[0];
+    if (v < kDeltaInf) {
+      const int pr = lean_walk(s, 0, nchunks, v, +1);
+      if (pr >= 0 && s.d[pr] == v) {
+        if (pr < tn)
+          s.child[pr][0] = (int32_t)t0;
+        else
+          a.nodes[t1].child[0] = (int32_t)t0;
+      } else {
+        const int slot = atomicAdd(&s.nunres, 1);
+        if (slot < kUnresCap) s.unres[slot] = 0;
+      }
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    const int l = lbase + 32 * k;
+    if (l >= tn) break;
+    const int32_t id = (int32_t)(t0 + l);
+    // leaf l, between positions l and l + 1: child 0 of node l + 1 when the
+    // left distance is larger, else child 1 of node l (for a one-leaf cell,
+    // node l is the cell's root and the leaf its whole tree)
+    const uint32_t dl = s.d[l], dr = s.d[l + 1];
+    if (dl >= kDeltaInf) s.child[l][0] = ~(id > 0 ? id - 1 : 0);  // l starts a cell
+    const bool single = dl >= kDeltaInf && dr >= kDeltaInf;
+    const bool left = dl > dr && !single;
+    const int rec = left ? l + 1 : l;
+    if (rec < tn)
+      s.child[rec][left ? 0 : 1] = ~id;
+    else
+      a.nodes[t1].child[0] = ~id;
+    if (single) s.cell_range[atomicAdd(&s.ncells, 1)] = (uint32_t)l | ((uint32_t)l << 16);
+    // node at position p = l + 1 (the split between leaves l and l + 1)
+    const int p = l + 1;
+    const uint32_t v = dr;
+    if (p > tn - 1 || v >= kDeltaInf) continue;
+    const int c = 4 * warp + k;
+    const uint32_t gt = chunk_gt(s, c, v), ge = chunk_ge(s, c, v);
+    int pl;
+    {
+      const uint32_t msk = gt & ((1u << lane) - 1u);
+      if (msk) {
+        pl = 32 * c + 1 + (31 - __clz(msk));
+      } else {
+        pl = lean_walk(s, c - 1, nchunks, v, -1);
+        if (pl < 0 && s.d[0] > v) pl = 0;
+      }
+    }
+    int pr;
+    {
+      const uint32_t msk = lane < 31 ? (ge & ~((2u << lane) - 1u)) : 0u;
+      pr = msk ? 32 * c + __ffs(msk) : lean_walk(s, c + 1, nchunks, v, +1);
+    }
+    const int32_t nid = (int32_t)(t0 + p);
+    if (pr < 0 || (pl < 0 && s.d[pr] > v)) {
+      const int slot = atomicAdd(&s.nunres, 1);
+      if (slot < kUnresCap) s.unres[slot] = p;
+      continue;
+    }
+    const uint32_t dR = s.d[pr];
+    const uint32_t dL = pl >= 0 ? s.d[pl] : kDeltaInf + 1;
+    if (dL >= kDeltaInf && dR >= kDeltaInf && pl >= 0) {
+      // the top of a cell inside the tile: leaves [pl, pr - 1], root at pl
+      s.child[pl][1] = nid;
+      s.cell_range[atomicAdd(&s.ncells, 1)] = (uint32_t)pl | ((uint32_t)(pr - 1) << 16);
+    } else if (dL > dR) {
+      if (pr < tn)
+        s.child[pr][0] = nid;
+      else
+        a.nodes[t1].child[0] = nid;
+    } else {
+      s.child[pl][1] = nid;
+    }
+  }
+  __syncthreads();
+
+  // ---- guide entries of the cells completed inside the tile -----------------
+  for (int i = tid; i < s.ncells; i += kForestThreads) {
+    const uint32_t r = s.cell_range[i];
+    const int lo = (int)(r & 0xFFFFu), hi = (int)(r >> 16);
+    const int64_t glo = t0 + lo;
+    const uint64_t Clm1 = glo > 0 ? s.C[lo] : 0ull;
+    const uint64_t Chp1 = t0 + hi + 1 == a.N ? T : s.C[hi + 2];
+    const uint64_t Clo = s.C[lo + 1], Chi = s.C[hi + 1];
+    // the top of the cell's tree is its root's child 1 (written in the links)
+    finish_cell(a, P, glo, t0 + hi, key_of(Clo, T, R, z), key_of(Chi, T, R, z), Clm1, Clo, Chi,
+                Chp1, s.child[lo][1]);
+  }
+
+  // ---- node records (lane-strided: each k is 32 consecutive records) ----------
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int l = lbase + 32 * k;
+    if (l >= tn) break;
+    const int32_t c0 = s.child[l][0], c1 = s.child[l][1];
+    const uint64_t Cl = s.C[l + 1];
+    rtf_node* rec = a.nodes + t0 + l;
+    if (c0 != kUnset && c1 != kUnset) {
+      rtf_node r;
+      r.cdf = Cl;
+      r.child[0] = c0;
+      r.child[1] = c1;
+      *rec = r;
+    } else {
+      rec->cdf = Cl;
+      if (c0 != kUnset) rec->child[0] = c0;
+      if (c1 != kUnset) rec->child[1] = c1;
+    }
+  }
+  const int nu = s.nunres;
+  if (tid == 0) {
+    if (nu > kUnresCap) raise_status(a.status, RTF_STATUS_INVARIANT);
+    a.unres_count[tile] = min(nu, kUnresCap);
+  }
+  if (tid < min(nu, kUnresCap)) a.unres[tile * kUnresCap + tid] = (int32_t)(t0 + s.unres[tid]);
+}
+
 // Nearest split j' < j with delta_{j'} > v, or -1 (the array start counts as
 // infinitely far), searched by one warp: splits 32 at a time inside j's tile,
 // then tiles by their largest distance inside j's group of tiles, then groups.
@@ -1259,11 +1574,11 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
       return e;
     forest_kernel<true><<<(unsigned)num_tiles(N), kForestThreads, fsmem, st>>>(fa);
   } else {
-    const size_t fsmem = sizeof(ForestShared<false>);
-    if ((e = cudaFuncSetAttribute(forest_kernel<false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
+    const size_t fsmem = sizeof(LeanShared);
+    if ((e = cudaFuncSetAttribute(forest_lean_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fsmem)))
       return e;
-    forest_kernel<false><<<(unsigned)num_tiles(N), kForestThreads, fsmem, st>>>(fa);
+    forest_lean_kernel<<<(unsigned)num_tiles(N), kForestThreads, fsmem, st>>>(fa);
   }
   {
     const int64_t nt = num_tiles(N);
