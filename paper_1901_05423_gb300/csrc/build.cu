@@ -201,7 +201,8 @@ struct TileSums {
 template <bool SEG>
 __global__ void __launch_bounds__(kScanThreads)
     tile_sum_kernel(const float* __restrict__ w, int64_t Nw, rtf_dist* dists, int Dw,
-                    int64_t n_shared, const uint32_t* dmax, TileSums ts, uint32_t* status) {
+                    int64_t n_shared, const uint32_t* dmax, TileSums ts, uint64_t* tile_prefix,
+                    Counters* ctr, uint32_t* status) {
   __shared__ alignas(16) float wsm[kTile + 4];
   __shared__ uint64_t bar;
   __shared__ int ok_s;
@@ -246,23 +247,40 @@ __global__ void __launch_bounds__(kScanThreads)
     for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
     if ((threadIdx.x & 31) == 0) wtot[threadIdx.x >> 5].s = run;
     __syncthreads();
+    __shared__ int last_s;
+    __shared__ uint64_t btot_s;
     if (threadIdx.x == 0) {
       uint64_t sum = 0;
       for (int k = 0; k < kScanThreads / 32; ++k) sum += wtot[k].s;
-      const bool head0 = t0 == 0;
-      uint32_t meta = head0 ? 3u : 0u;
-      if (t1 == Nw) {
-        if (head0) {
-          finish_dist(dists, 0, sum, S, status);
-        } else {
-          ts.first[tile] = sum;
-          meta |= 4u;
-        }
-      }
       ts.sum[tile] = sum;
-      ts.meta[tile] = meta;
-      ts.dist0[tile] = 0;
+      __threadfence();
+      last_s = atomicAdd(&ctr->scan_done, 1u) == (uint32_t)(gridDim.x - 1);
     }
+    __syncthreads();
+    if (!last_s) return;
+    // the last block to finish: exclusive prefixes of all tile sums and the
+    // distribution's total
+    __threadfence();
+    const int64_t ntiles = gridDim.x;
+    uint64_t carry = 0;
+    for (int64_t c0 = 0; c0 < ntiles; c0 += (int64_t)kScanThreads * kScanPer) {
+      const int64_t b0 = c0 + (int64_t)threadIdx.x * kScanPer;
+      uint64_t v[kScanPer], tsum = 0;
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) {
+        v[k] = b0 + k < ntiles ? __ldcg(ts.sum + b0 + k) : 0ull;
+        tsum += v[k];
+      }
+      uint64_t ex = carry + block_exclusive_u64(tsum, reinterpret_cast<uint64_t*>(wtot), &btot_s);
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) {
+        if (b0 + k < ntiles) tile_prefix[b0 + k] = ex;
+        ex += v[k];
+      }
+      carry += btot_s;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) finish_dist(dists, 0, carry, S, status);
     return;
   }
 
@@ -509,8 +527,9 @@ struct ForestArgs {
   rtf_node* nodes;
   int32_t* guide;
   rtf_guide_rec* guide_recs;
-  int32_t* last;
-  uint64_t* last_lo;
+  int4* fills;
+  uint32_t* fill_count;
+  int64_t fill_cap;
   const uint64_t* tile_prefix;
   const uint32_t* dmax;
   uint8_t* delta;
@@ -526,17 +545,22 @@ __device__ __forceinline__ uint64_t key_for(const rtf_dist& P, uint64_t C) {
   return key_of(C, P.total, P.recip, P.shift);
 }
 
-// Root of a finished cell [lo, hi] (global element indices) of distribution P:
-// guide entry, guide record and last-leaf entries of the cell.  K_lo / K_hi
-// are the keys of leaves lo and hi; C_{lo-1} (0 when lo is the first leaf of
-// the distribution), C_lo, C_hi and C_{hi+1} (T after the last leaf) their
-// CDF bounds.
-__device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist& P, int64_t lo,
-                                            int64_t hi, uint64_t Klo, uint64_t Khi,
+// Root of a finished cell [lo, hi] (global element indices) of distribution P
+// (index d): guide entry and guide record of the cell, and of the cells after
+// it that no key falls into.  K_lo / K_hi are the keys of leaves lo and hi,
+// Knext that of leaf hi + 1 (2^32 after the distribution's last leaf);
+// C_{lo-1} (0 when lo is the first leaf of the distribution), C_lo, C_hi and
+// C_{hi+1} (T after the last leaf) their CDF bounds.  Interval hi covers every
+// cell from c + 1 up to the cell of Knext (the guide entry ~hi of the Cutpoint
+// method, Sec. 3.2, for a cell overlapped by one interval only); runs longer
+// than kFillInline cells are listed for the fill pass.
+__device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist& P, int d,
+                                            int64_t lo, int64_t hi, uint64_t Klo, uint64_t Khi,
                                             uint64_t Clm1, uint64_t Clo, uint64_t Chi,
-                                            uint64_t Chp1, int32_t top) {
+                                            uint64_t Chp1, int32_t top, uint64_t Knext) {
+  const uint64_t M = 1ull << P.m;
   uint64_t c = cell_of(Klo, P.m);
-  if (c >= (1ull << P.m)) return;  // unreachable trailing cell of zero-width bins
+  if (c >= M) return;  // unreachable trailing cell of zero-width bins
   int32_t lo_l = (int32_t)(lo - P.elem_off), hi_l = (int32_t)(hi - P.elem_off);
   uint64_t start = c << (32 - P.m);
   const int64_t gi = P.guide_off + (int64_t)c;
@@ -557,8 +581,32 @@ __device__ __forceinline__ void finish_cell(const ForestArgs& a, const rtf_dist&
     rec.lo = Clm1;
   }
   a.guide_recs[gi] = rec;
-  a.last[gi] = hi_l;
-  a.last_lo[gi] = Chi;
+  const uint64_t cn = min(cell_of(Knext, P.m), M);
+  if (cn <= c + 1) return;
+  const int64_t first = (int64_t)c + 1, count = (int64_t)cn - first;
+  if (count <= kFillInline) {
+    rtf_guide_rec cov;
+    cov.cdf = Chi;
+    cov.child[0] = ~hi_l;
+    cov.child[1] = ~hi_l;
+    cov.lo = Chi;
+    cov.hi = Chp1;
+    for (int64_t g = first; g < (int64_t)cn; ++g) {
+      a.guide[P.guide_off + g] = ~hi_l;
+      a.guide_recs[P.guide_off + g] = cov;
+    }
+    return;
+  }
+  const int64_t pieces = (count + kFillPiece - 1) / kFillPiece;
+  const int64_t slot = atomicAdd(a.fill_count, (uint32_t)pieces);
+  for (int64_t k = 0; k < pieces; ++k) {
+    if (slot + k >= a.fill_cap) {
+      raise_status(a.status, RTF_STATUS_INVARIANT);
+      break;
+    }
+    a.fills[slot + k] = make_int4((int)(P.guide_off + first + k * kFillPiece),
+                                  (int)min(kFillPiece, count - k * kFillPiece), hi_l, d);
+  }
 }
 
 // Lanes of a 32-position chunk whose value (bit planes pl[0..5]) exceeds v
@@ -834,8 +882,9 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
         s.child[p][1] = ~id;
         const uint64_t Clm1 = id > 0 ? s.C[p] : 0ull;
         const uint64_t Chp1 = t0 + p + 1 == P.elem_off + P.n ? P.total : s.C[p + 2];
-        finish_cell(a, P, t0 + p, t0 + p, s.K[p + 1], s.K[p + 1], Clm1, s.C[p + 1], s.C[p + 1],
-                    Chp1, ~id);
+        const uint64_t Knext = t0 + p + 1 == P.elem_off + P.n ? (1ull << 32) : s.K[p + 2];
+        finish_cell(a, P, dd, t0 + p, t0 + p, s.K[p + 1], s.K[p + 1], Clm1, s.C[p + 1],
+                    s.C[p + 1], Chp1, ~id, Knext);
       } else if (dl > dr) {
         if (p + 1 < tn)
           s.child[p + 1][0] = ~id;
@@ -899,8 +948,9 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
       const int32_t lo_id = base_id + pl;
       const uint64_t Clm1 = lo_id > 0 ? s.C[pl] : 0ull;
       const uint64_t Chp1 = t0 + pr == P.elem_off + P.n ? P.total : s.C[pr + 1];
-      finish_cell(a, P, t0 + pl, t0 + pr - 1, s.K[pl + 1], s.K[pr], Clm1, s.C[pl + 1], s.C[pr],
-                  Chp1, id);
+      const uint64_t Knext = t0 + pr == P.elem_off + P.n ? (1ull << 32) : s.K[pr + 1];
+      finish_cell(a, P, dd, t0 + pl, t0 + pr - 1, s.K[pl + 1], s.K[pr], Clm1, s.C[pl + 1],
+                  s.C[pr], Chp1, id, Knext);
     } else if (dl > dr) {
       if (pr < tn)
         s.child[pr][0] = id;
@@ -1224,9 +1274,10 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     const uint64_t Clm1 = glo > 0 ? s.C[lo] : 0ull;
     const uint64_t Chp1 = t0 + hi + 1 == a.N ? T : s.C[hi + 2];
     const uint64_t Clo = s.C[lo + 1], Chi = s.C[hi + 1];
+    const uint64_t Knext = t0 + hi + 1 == a.N ? (1ull << 32) : key_of(Chp1, T, R, z);
     // the top of the cell's tree is its root's child 1 (written in the links)
-    finish_cell(a, P, glo, t0 + hi, key_of(Clo, T, R, z), key_of(Chi, T, R, z), Clm1, Clo, Chi,
-                Chp1, s.child[lo][1]);
+    finish_cell(a, P, 0, glo, t0 + hi, key_of(Clo, T, R, z), key_of(Chi, T, R, z), Clm1, Clo, Chi,
+                Chp1, s.child[lo][1], Knext);
   }
 
   // ---- node records (lane-strided: each k is 32 consecutive records) ----------
@@ -1356,7 +1407,8 @@ __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t
       raise_status(a.status, RTF_STATUS_INVARIANT);
       continue;
     }
-    const rtf_dist P = a.dists[a.D > 1 ? find_dist(a.dists, 0, a.D - 1, p) : 0];
+    const int d = a.D > 1 ? find_dist(a.dists, 0, a.D - 1, p) : 0;
+    const rtf_dist P = a.dists[d];
     const int32_t id = (int32_t)(p - P.elem_off);
     const uint32_t dl = jl >= 0 ? (uint32_t)a.delta[jl] : kDeltaInf;
     const uint32_t dr = a.delta[jr];
@@ -1368,7 +1420,9 @@ __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t
       const uint64_t Clo = a.nodes[lo].cdf, Chi = a.nodes[hi].cdf;
       const uint64_t Clm1 = lo_l > 0 ? a.nodes[lo - 1].cdf : 0ull;
       const uint64_t Chp1 = hi + 1 < P.elem_off + P.n ? a.nodes[hi + 1].cdf : P.total;
-      finish_cell(a, P, lo, hi, key_for(P, Clo), key_for(P, Chi), Clm1, Clo, Chi, Chp1, id);
+      const uint64_t Knext = hi + 1 < P.elem_off + P.n ? key_for(P, Chp1) : (1ull << 32);
+      finish_cell(a, P, d, lo, hi, key_for(P, Clo), key_for(P, Chi), Clm1, Clo, Chi, Chp1, id,
+                  Knext);
     } else if (dl > dr) {
       a.nodes[jr + 1].child[0] = id;
     } else {
@@ -1395,101 +1449,28 @@ cudaError_t launch_wait_probe(uint32_t* status, uint64_t* scratch, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------------
-// guide: cells without keys take the interval of the last key before them
+// fill: the long runs of empty cells listed by finish_cell
 // ---------------------------------------------------------------------------
-constexpr int kGuidePer = kGuideTile / kGuideThreads;  // 4
-
-__global__ void __launch_bounds__(kGuideThreads)
-    guide_kernel(int64_t G, const int32_t* __restrict__ last, const uint64_t* __restrict__ last_lo,
-                 int32_t* guide, rtf_guide_rec* guide_recs, uint64_t* gstatus, Counters* ctr,
-                 uint32_t* status) {
-  __shared__ uint32_t tile_s;
-  __shared__ int32_t wlast[kGuideThreads / 32];
-  __shared__ int32_t carry_s;
-  __shared__ LookbackShared lb;
-  if (threadIdx.x == 0) tile_s = atomicAdd(&ctr->guide_ticket, 1u);
-  __syncthreads();
-  const int64_t tile = tile_s;
-  const int64_t g0 = tile * kGuideTile + (int64_t)threadIdx.x * kGuidePer;
-  const int64_t gend = min(tile * kGuideTile + (int64_t)kGuideTile, G);
-  // the carried value is the index of the last non-empty cell (G < 2^31)
-  bool full[kGuidePer];
-  int32_t tlast = -1;
-#pragma unroll
-  for (int k = 0; k < kGuidePer; ++k) {
-    int64_t g = g0 + k;
-    full[k] = g < gend && last[g] >= 0;
-    if (full[k]) tlast = (int32_t)g;
-  }
-  // last non-empty cell of all threads before this one (warp, then block)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t inc = tlast;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d && inc < 0) inc = o;
-  }
-  if (lane == 31) wlast[warp] = inc;
-  __syncthreads();
-  int32_t before_warp = -1;
-  for (int w2 = 0; w2 < warp; ++w2)
-    if (wlast[w2] >= 0) before_warp = wlast[w2];
-  int32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
-  if (lane == 0) ex = -1;
-  int32_t before = ex >= 0 ? ex : before_warp;
-  int32_t tile_last = -1;
-  for (int w2 = 0; w2 < kGuideThreads / 32; ++w2)
-    if (wlast[w2] >= 0) tile_last = wlast[w2];
-  if (threadIdx.x == 0) {
-    if (tile_last >= 0)
-      st_release_u64(gstatus + tile, kFlagPrefix | (uint32_t)tile_last);
-    else
-      st_release_u64(gstatus + tile, kFlagAgg);
-  }
-  // the incoming carry is needed only when the tile's first cell is empty
-  __shared__ int need_s;
-  if (threadIdx.x == 0) {
-    carry_s = -1;
-    need_s = (g0 < gend && !full[0]) ? 1 : 0;
-  }
-  __syncthreads();
-  if (need_s) {
-    int32_t c = (int32_t)(uint32_t)(block_lookback(gstatus, tile, false, &lb, status) &
-                                     0xffffffffull);
-    if (threadIdx.x == 0) {
-      carry_s = c;
-      if (tile_last < 0) st_release_u64(gstatus + tile, kFlagPrefix | (uint32_t)c);
-    }
-  }
-  __syncthreads();
-  int32_t src = before >= 0 ? before : carry_s;
-  rtf_guide_rec rec;
-  int32_t rec_src = -1;
-#pragma unroll
-  for (int k = 0; k < kGuidePer; ++k) {
-    int64_t g = g0 + k;
-    if (g >= gend) break;
-    if (full[k]) {
-      src = (int32_t)g;
-    } else {
-      if (src < 0) {
-        // cell 0 of a distribution always holds key 0, so this is unreachable;
-        // the record refers to no interval (the sampler returns -1 through it)
-        raise_status(status, RTF_STATUS_BAD_PLAN);
-        rec = rtf_guide_rec{0ull, {INT32_MIN, INT32_MIN}, 0ull, 0ull};
-        rec_src = -1;
-      } else if (src != rec_src) {
-        // the last interval of cell src covers this cell
-        rec_src = src;
-        const int32_t i = last[src];
-        rec.lo = last_lo[src];
-        rec.cdf = rec.lo;
-        rec.child[0] = ~i;
-        rec.child[1] = ~i;
-        rec.hi = guide_recs[src].hi;
-      }
-      guide[g] = rec.child[0];
-      guide_recs[g] = rec;
+// One warp per listed piece (at most kFillPiece cells): every cell of it takes
+// the interval `leaf` of its distribution, {C_i, ~i, ~i, C_i, C_{i+1}}.
+__global__ void __launch_bounds__(256) fill_kernel(ForestArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t cnt = min((int64_t)*a.fill_count, a.fill_cap);
+  for (int64_t i = warp; i < cnt; i += nwarps) {
+    const int4 f = a.fills[i];
+    const rtf_dist& P = a.dists[f.w];
+    const int64_t e = P.elem_off + f.z;
+    rtf_guide_rec cov;
+    cov.cdf = a.nodes[e].cdf;
+    cov.child[0] = ~f.z;
+    cov.child[1] = ~f.z;
+    cov.lo = cov.cdf;
+    cov.hi = (int64_t)f.z + 1 < P.n ? a.nodes[e + 1].cdf : P.total;
+    for (int64_t g = (int64_t)f.x + lane; g < (int64_t)f.x + f.y; g += 32) {
+      a.guide[g] = ~f.z;
+      a.guide_recs[g] = cov;
     }
   }
 }
@@ -1507,8 +1488,6 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   Counters* ctr = reinterpret_cast<Counters*>(base + L.counters);
   uint32_t* dmax = reinterpret_cast<uint32_t*>(base + L.dmax);
   uint64_t* scan_status = reinterpret_cast<uint64_t*>(base + L.scan_status);
-  uint64_t* guide_status = reinterpret_cast<uint64_t*>(base + L.guide_status);
-  int32_t* last = reinterpret_cast<int32_t*>(base + L.last);
   uint64_t* tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
   uint8_t* delta = reinterpret_cast<uint8_t*>(base + L.delta);
   const bool seg = D > 1;
@@ -1517,7 +1496,6 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(base + L.zero_begin, 0, L.zero_end - L.zero_begin, st))) return e;
-  if ((e = cudaMemsetAsync(last, 0xFF, sizeof(int32_t) * (size_t)G, st))) return e;
   if ((e = cudaMemsetAsync(f->status, 0, sizeof(uint32_t), st))) return e;
   init_dists_kernel<<<(D + 255) / 256, 256, 0, st>>>(f->dists, D, offsets, m_arr, goff, marginal,
                                                       n_single, m_single, f->status);
@@ -1536,16 +1514,19 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   ts.first = reinterpret_cast<uint64_t*>(base + L.tile_first);
   ts.meta = reinterpret_cast<uint32_t*>(base + L.tile_meta);
   ts.dist0 = reinterpret_cast<int32_t*>(base + L.tile_dist0);
-  if (seg)
-    tile_sum_kernel<true><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(w, Nw, f->dists, Dw,
-                                                                     n_shared, dmax, ts, f->status);
-  else
-    tile_sum_kernel<false><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(w, Nw, f->dists, Dw,
-                                                                      n_shared, dmax, ts, f->status);
-  const int64_t chunks = (tiles_w + kTileScanChunk - 1) / kTileScanChunk;
-  tile_scan_kernel<<<(unsigned)chunks, kScanThreads, 0, st>>>(ts, tiles_w, f->dists, D, Dw, marginal,
-                                                             n_shared, dmax, scan_status,
-                                                             tile_prefix, ctr, f->status);
+  if (seg) {
+    tile_sum_kernel<true><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(
+        w, Nw, f->dists, Dw, n_shared, dmax, ts, tile_prefix, ctr, f->status);
+    const int64_t chunks = (tiles_w + kTileScanChunk - 1) / kTileScanChunk;
+    tile_scan_kernel<<<(unsigned)chunks, kScanThreads, 0, st>>>(ts, tiles_w, f->dists, D, Dw,
+                                                               marginal, n_shared, dmax,
+                                                               scan_status, tile_prefix, ctr,
+                                                               f->status);
+  } else {
+    // one distribution: the last block of the tile sums also scans them
+    tile_sum_kernel<false><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(
+        w, Nw, f->dists, Dw, n_shared, dmax, ts, tile_prefix, ctr, f->status);
+  }
   ForestArgs fa;
   fa.w = w;
   fa.N = N;
@@ -1557,8 +1538,9 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.nodes = f->nodes;
   fa.guide = f->guide;
   fa.guide_recs = f->guide_recs;
-  fa.last = last;
-  fa.last_lo = reinterpret_cast<uint64_t*>(base + L.last_lo);
+  fa.fills = reinterpret_cast<int4*>(base + L.fills);
+  fa.fill_count = &ctr->fill_count;
+  fa.fill_cap = fill_cap(D, G);
   fa.tile_prefix = tile_prefix;
   fa.dmax = dmax;
   fa.delta = delta;
@@ -1584,10 +1566,12 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
     const int64_t nt = num_tiles(N);
     forest_merge_kernel<<<(unsigned)((nt + 3) / 4), 128, 0, st>>>(fa, nt);
   }
-  const int64_t gtiles = (G + kGuideTile - 1) / kGuideTile;
-  guide_kernel<<<(unsigned)gtiles, kGuideThreads, 0, st>>>(G, last, fa.last_lo, f->guide,
-                                                            f->guide_recs,
-                                                           guide_status, ctr, f->status);
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    fill_kernel<<<(unsigned)(sms > 0 ? 2 * sms : 304), 256, 0, st>>>(fa);
+  }
   return cudaGetLastError();
 }
 

@@ -19,8 +19,6 @@ namespace rtf {
 constexpr int kTile = 2048;           // weights per scan / forest tile
 constexpr int kScanThreads = 256;     // scan kernel: 8 weights per thread
 constexpr int kForestThreads = 512;   // forest kernel: 4 leaves per thread
-constexpr int kGuideTile = 1024;      // guide cells per guide-fill tile
-constexpr int kGuideThreads = 256;    // 4 cells per thread
 constexpr int kMaxThreads = 512;
 constexpr uint32_t kDeltaInf = 64;    // distance across a cell / distribution boundary
 constexpr long long kSpinLimit = 1ll << 22;   // bounded waits
@@ -31,6 +29,11 @@ constexpr long long kSpinLimit = 1ll << 22;   // bounded waits
 // not settle the parent (strictly increasing distances).
 constexpr int kUnresCap = 72;
 constexpr int kTileGroup = 64;        // forest tiles per group of the distance maxima
+// Cells that no key falls into are written by whoever finishes the non-empty
+// cell before them: up to kFillInline at once, longer runs listed in pieces of
+// at most kFillPiece cells for the fill pass.
+constexpr int kFillInline = 16;
+constexpr int64_t kFillPiece = int64_t(1) << 16;
 
 // status-word flags of the decoupled lookback (top two bits of a u64)
 constexpr uint64_t kFlagAgg = 1ull << 62;
@@ -45,11 +48,9 @@ struct WsLayout {
   size_t counters;     // u32 tickets / done counters
   size_t dmax;         // u32 [D] max float bits per distribution / group
   size_t scan_status;  // u64 [num_tiles / 2048 + 1] status of the tile-sum scan blocks
-  size_t guide_status; // u64 [num_guide_tiles]
   size_t gmax;         // u32 [num_tiles / kTileGroup] largest distance per group of tiles
   size_t zero_end;
-  size_t last;         // i32 [G] last leaf of each non-empty cell (set to -1)
-  size_t last_lo;      // u64 [G] lower CDF bound of that leaf
+  size_t fills;        // int4 [fill_cap] runs of empty cells: first cell, count, leaf, dist
   size_t tile_prefix;  // u64 [num_tiles]
   size_t tile_sum;     // u64 [num_tiles]
   size_t tile_first;   // u64 [num_tiles]
@@ -66,6 +67,13 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 
 __host__ __device__ inline int64_t num_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
 
+// Pieces of runs of empty cells the fill pass may receive: each run longer than
+// kFillInline cells is at least kFillInline + 1 cells and splits into at most
+// count / kFillPiece + 1 pieces.
+__host__ __device__ inline int64_t fill_cap(int32_t D, int64_t G) {
+  return G / (kFillInline + 1) + G / kFillPiece + D + 16;
+}
+
 __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   WsLayout L;
   size_t o = 0;
@@ -73,13 +81,10 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   L.counters = o; o += 256;
   L.dmax = o; o = align256(o + sizeof(uint32_t) * (size_t)D);
   L.scan_status = o; o = align256(o + sizeof(uint64_t) * (size_t)(num_tiles(N) / 2048 + 1));
-  L.guide_status = o;
-  o = align256(o + sizeof(uint64_t) * (size_t)((G + kGuideTile - 1) / kGuideTile));
   L.gmax = o;
   o = align256(o + sizeof(uint32_t) * (size_t)((num_tiles(N) + kTileGroup - 1) / kTileGroup));
   L.zero_end = o;
-  L.last = o; o = align256(o + sizeof(int32_t) * (size_t)G);
-  L.last_lo = o; o = align256(o + sizeof(uint64_t) * (size_t)G);
+  L.fills = o; o = align256(o + 16 * (size_t)fill_cap(D, G));
   L.tile_prefix = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
   L.tile_sum = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
   L.tile_first = o; o = align256(o + sizeof(uint64_t) * (size_t)num_tiles(N));
@@ -96,7 +101,7 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
 // counters inside WsLayout::counters
 struct Counters {
   uint32_t scan_ticket;
-  uint32_t guide_ticket;
+  uint32_t fill_count;
   uint32_t scan_done;
   uint32_t pad[61];
 };
