@@ -21,6 +21,7 @@
 //   guide_kernel        guide entries of cells that no key falls into: the
 //                       interval of the last key before them (carry-forward
 //                       scan with a decoupled lookback)
+#include <algorithm>
 #include <cstdint>
 
 #include "rtf_device.cuh"
@@ -215,72 +216,97 @@ __global__ void __launch_bounds__(kScanThreads)
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, Nw);
 
   if (!SEG) {
-    // one distribution: the tile's sum of q (weights read straight from
-    // global memory, 16-byte vectors where aligned); the last tile also
-    // holds the distribution's end (finished here when the tile is also the
-    // first)
-    const int S = dist_scale(dists[0], dmax, 0, n_shared);
-    const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
-    float wv[kScanPer];
-    if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w + e0) & 15) == 0) {
-#pragma unroll
-      for (int h = 0; h < kScanPer / 4; ++h) {
-        const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
-        wv[4 * h] = x.x;
-        wv[4 * h + 1] = x.y;
-        wv[4 * h + 2] = x.z;
-        wv[4 * h + 3] = x.w;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < t1 ? w[e0 + k] : 0.0f;
-    }
-    uint64_t run = 0;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-      if (e0 + k < t1) {
-        const uint32_t b = weight_bits(wv[k]);
-        run += weight_bad(b) ? 0ull : quantize_bits(b, S);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
-    if ((threadIdx.x & 31) == 0) wtot[threadIdx.x >> 5].s = run;
-    __syncthreads();
+    // one distribution, persistent blocks: block b sums the contiguous tiles
+    // [b per, (b + 1) per) (weights straight from global memory, 16-byte
+    // vectors where aligned) and writes each tile's prefix within that range
+    // and the range's total; the last block to finish scans the range totals
+    // into the ranges' prefixes (a tile's prefix is the two added) and
+    // finishes the distribution
     __shared__ int last_s;
     __shared__ uint64_t btot_s;
+    const int S = dist_scale(dists[0], dmax, 0, n_shared);
+    const int64_t ntiles = (Nw + kTile - 1) / kTile;
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(r0 + per, ntiles);
+    uint64_t local = 0;  // sum of the range's tiles so far (thread 0)
+    // the next tile's weights are loaded while the current one is reduced
+    auto load_tile = [&](int64_t tl, float* wv) {
+      const int64_t u0 = tl * kTile, u1 = min(u0 + (int64_t)kTile, Nw);
+      const int64_t e0 = u0 + (int64_t)threadIdx.x * kScanPer;
+      if (e0 + kScanPer <= u1 && (reinterpret_cast<uintptr_t>(w + e0) & 15) == 0) {
+#pragma unroll
+        for (int h = 0; h < kScanPer / 4; ++h) {
+          const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
+          wv[4 * h] = x.x;
+          wv[4 * h + 1] = x.y;
+          wv[4 * h + 2] = x.z;
+          wv[4 * h + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < u1 ? w[e0 + k] : 0.0f;
+      }
+    };
+    float wnext[kScanPer];
+    if (r0 < r1) load_tile(r0, wnext);
+    for (int64_t tl = r0; tl < r1; ++tl) {
+      const int64_t u0 = tl * kTile, u1 = min(u0 + (int64_t)kTile, Nw);
+      const int64_t e0 = u0 + (int64_t)threadIdx.x * kScanPer;
+      float wv[kScanPer];
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) wv[k] = wnext[k];
+      if (tl + 1 < r1) load_tile(tl + 1, wnext);
+      uint64_t run = 0;
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) {
+        if (e0 + k < u1) {
+          const uint32_t b = weight_bits(wv[k]);
+          run += weight_bad(b) ? 0ull : quantize_bits(b, S);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
+      if ((threadIdx.x & 31) == 0) wtot[threadIdx.x >> 5].s = run;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint64_t sum = 0;
+        for (int k = 0; k < kScanThreads / 32; ++k) sum += wtot[k].s;
+        tile_prefix[tl] = local;
+        local += sum;
+      }
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
-      uint64_t sum = 0;
-      for (int k = 0; k < kScanThreads / 32; ++k) sum += wtot[k].s;
-      ts.sum[tile] = sum;
+      ts.sum[blockIdx.x] = local;  // the range's total
       __threadfence();
       last_s = atomicAdd(&ctr->scan_done, 1u) == (uint32_t)(gridDim.x - 1);
     }
     __syncthreads();
     if (!last_s) return;
-    // the last block to finish: exclusive prefixes of all tile sums and the
-    // distribution's total
     __threadfence();
-    const int64_t ntiles = gridDim.x;
+    const int64_t nranges = gridDim.x;
     uint64_t carry = 0;
-    for (int64_t c0 = 0; c0 < ntiles; c0 += (int64_t)kScanThreads * kScanPer) {
+    for (int64_t c0 = 0; c0 < nranges; c0 += (int64_t)kScanThreads * kScanPer) {
       const int64_t b0 = c0 + (int64_t)threadIdx.x * kScanPer;
       uint64_t v[kScanPer], tsum = 0;
 #pragma unroll
       for (int k = 0; k < kScanPer; ++k) {
-        v[k] = b0 + k < ntiles ? __ldcg(ts.sum + b0 + k) : 0ull;
+        v[k] = b0 + k < nranges ? __ldcg(ts.sum + b0 + k) : 0ull;
         tsum += v[k];
       }
       uint64_t ex = carry + block_exclusive_u64(tsum, reinterpret_cast<uint64_t*>(wtot), &btot_s);
 #pragma unroll
       for (int k = 0; k < kScanPer; ++k) {
-        if (b0 + k < ntiles) tile_prefix[b0 + k] = ex;
+        if (b0 + k < nranges) ts.first[b0 + k] = ex;  // prefix of range b0 + k
         ex += v[k];
       }
       carry += btot_s;
       __syncthreads();
     }
-    if (threadIdx.x == 0) finish_dist(dists, 0, carry, S, status);
+    if (threadIdx.x == 0) {
+      finish_dist(dists, 0, carry, S, status);
+      ts.meta[0] = (uint32_t)per;  // tiles per range, for the forest pass
+    }
     return;
   }
 
@@ -531,6 +557,8 @@ struct ForestArgs {
   uint32_t* fill_count;
   int64_t fill_cap;
   const uint64_t* tile_prefix;
+  const uint64_t* range_prefix;  // one distribution: prefix of each range of tiles
+  const uint32_t* range_meta;    // [0]: tiles per range
   const uint32_t* dmax;
   uint8_t* delta;
   uint8_t* tmax;
@@ -1083,7 +1111,8 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     s.nunres = 0;
     s.ncells = 0;
     s.tmax = 0;
-    s.prefix = t0 > 0 ? a.tile_prefix[tile] : 0ull;
+    // the tile's prefix within its range of the tile sums plus the range's prefix
+    s.prefix = t0 > 0 ? a.tile_prefix[tile] + a.range_prefix[tile / a.range_meta[0]] : 0ull;
   }
   uint64_t C[4];
   uint64_t run = 0;
@@ -1523,8 +1552,12 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
                                                                scan_status, tile_prefix, ctr,
                                                                f->status);
   } else {
-    // one distribution: the last block of the tile sums also scans them
-    tile_sum_kernel<false><<<(unsigned)tiles_w, kScanThreads, 0, st>>>(
+    // one distribution: persistent blocks; the last one also scans the sums
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>(tiles_w, (int64_t)(sms > 0 ? sms : 148) * 8);
+    tile_sum_kernel<false><<<(unsigned)grid, kScanThreads, 0, st>>>(
         w, Nw, f->dists, Dw, n_shared, dmax, ts, tile_prefix, ctr, f->status);
   }
   ForestArgs fa;
@@ -1543,6 +1576,8 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.fill_cap = fill_cap(D, G);
   fa.tile_prefix = tile_prefix;
   fa.dmax = dmax;
+  fa.range_prefix = ts.first;
+  fa.range_meta = ts.meta;
   fa.delta = delta;
   fa.tmax = reinterpret_cast<uint8_t*>(base + L.tmax);
   fa.gmax = reinterpret_cast<uint32_t*>(base + L.gmax);
