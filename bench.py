@@ -683,16 +683,18 @@ def extra_ragged(dev, reps=3):
 
 def extra_env_map(dev, reps=3):
     """4096 x 2048 map: marginal + 2048 conditionals in one batched build;
-    2^26 (u1, u2) pairs."""
+    2^26 (u1, u2) pairs; guide bits of the rows and of the marginal from the
+    autotuner (build + 2^26 pairs on this map)."""
     import torch
-    from paper_1901_05423_gb300 import api
+    from paper_1901_05423_gb300 import api, autotune
     from paper_1901_05423_gb300 import workloads as W
-    H, Wd, m = 2048, 4096, 12
-    lum = torch.from_numpy(W.env_map(H, Wd, seed=0).reshape(-1)).to(dev)
-    sizes = [Wd] * H + [H]
-    ms = [m] * (H + 1)
-    f = api.rtf_build_batched(lum, sizes, ms, marginal=True)
+    H, Wd = 2048, 4096
     ns = 1 << 26
+    lum = torch.from_numpy(W.env_map(H, Wd, seed=0).reshape(-1)).to(dev)
+    m_row, m_marg, tuned = autotune.tune_env_bits(lum, H, Wd, ns)
+    sizes = [Wd] * H + [H]
+    ms = [m_row] * H + [m_marg]
+    f = api.rtf_build_batched(lum, sizes, ms, marginal=True)
     u = api.u32_tensor(W.iid_u32(2 * ns, seed=3), dev)
     idx = torch.empty((ns, 2), dtype=torch.int32, device=dev)
     pos = torch.empty((ns, 2), dtype=torch.float32, device=dev)
@@ -711,10 +713,14 @@ def extra_env_map(dev, reps=3):
     f.check_status()
     bms = a.elapsed_time(b) / reps
     sms = b.elapsed_time(c) / reps
-    return {"workload": "env map 4096x2048 + marginal, 2^12 guide cells per row and for the "
-                        "marginal, 2^26 iid (u1,u2) pairs",
+    return {"workload": f"env map 4096x2048 + marginal, 2^{m_row} guide cells per row and "
+                        f"2^{m_marg} for the marginal (autotuned), 2^26 iid (u1,u2) pairs",
+            "guide_bits": {"row": m_row, "marginal": m_marg,
+                           "tuned_ms_build_plus_2^26_pairs": {f"{a},{b}": v
+                                                               for (a, b), v in tuned.items()}},
             "build_ms": bms, "build_elem_per_s": (H * Wd + H) / (bms * 1e-3),
-            "sample_ms": sms, "samples_2d_per_s": ns / (sms * 1e-3)}
+            "sample_ms": sms, "samples_2d_per_s": ns / (sms * 1e-3),
+            "sample_hbm_frac": 24 * ns / (sms * 1e-3) / 1e9 / measured_peaks()[0]}
 
 
 def extra_backward(dev, reps=5):

@@ -157,3 +157,62 @@ def tune_launch_shape(forest, u: torch.Tensor, dist_id: torch.Tensor | None = No
         with open(path, "w") as fh:
             json.dump(cache, fh)
     return kind, best, times
+
+
+def tune_env_bits(lum: torch.Tensor, rows: int, cols: int, pairs_per_build: int,
+                  row_offsets=(-2, -1, 0, 1, 2), marg_offsets=(-1, 0, 1),
+                  probe_pairs: int = 1 << 24, reps: int = 3, seed: int = 0,
+                  use_cache: bool = True) -> tuple[int, int, dict]:
+    """Guide bits of a 2-D map (Sec. 5: one table per row and one over the
+    rows): for each candidate (m_row, m_marginal) around (log2 cols,
+    log2 rows), the batched build and `probe_pairs` 2-D samples are timed on
+    the caller's map `lum` (device float32[rows * cols]); the pair with the
+    smallest build + pairs_per_build samples wins.  Larger tables cost build
+    time and memory and save node loads (a cell that one interval covers needs
+    none).  Returns (m_row, m_marginal, {(m_row, m_marginal): ms}); the choice
+    is cached per GPU model, map shape and pairs_per_build."""
+    device = lum.device
+    path = _cache_path(device, "env_bits")
+    key = f"{rows}x{cols}/{pairs_per_build}"
+    cache = {}
+    if use_cache and os.path.exists(path):
+        with open(path) as fh:
+            cache = json.load(fh)
+        if key in cache:
+            mr, mm = cache[key]
+            return int(mr), int(mm), {}
+    sizes = [cols] * rows + [rows]
+    br = int(round(np.log2(max(cols, 1))))
+    bm = int(round(np.log2(max(rows, 1))))
+    u = api.u32_tensor(W.iid_u32(2 * probe_pairs, seed=seed), device)
+    idx = torch.empty((probe_pairs, 2), dtype=torch.int32, device=device)
+    pos = torch.empty((probe_pairs, 2), dtype=torch.float32, device=device)
+    times = {}
+    for orow in row_offsets:
+        for om in marg_offsets:
+            mr, mm = min(max(br + orow, 0), 20), min(max(bm + om, 0), 20)
+            ms = [mr] * rows + [mm]
+            f = api.rtf_build_batched(lum, sizes, ms, marginal=True)
+            api.rtf_sample(f, u, mode=api.SAMPLE_2D, idx_out=idx, pos_out=pos)
+            torch.cuda.synchronize(device)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            for _ in range(reps):
+                api.rtf_build_batched(lum, sizes, ms, marginal=True, forest=f, plan_dev=f._plan_dev)
+            e[1].record()
+            for _ in range(reps):
+                api.rtf_sample(f, u, mode=api.SAMPLE_2D, idx_out=idx, pos_out=pos)
+            e[2].record()
+            torch.cuda.synchronize(device)
+            f.check_status()
+            tb = e[0].elapsed_time(e[1]) / reps
+            ts = e[1].elapsed_time(e[2]) / reps
+            times[(mr, mm)] = tb + ts * pairs_per_build / probe_pairs
+            del f
+    mr, mm = min(times, key=times.get)
+    if use_cache:
+        cache[key] = [mr, mm]
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as fh:
+            json.dump(cache, fh)
+    return mr, mm, times

@@ -538,10 +538,12 @@ struct ForestShared {
   int dfirst;
   int dprev;
   int nunres;
+  int ncells;
   float wprev;
   uint64_t prefix;
   rtf_dist P0;  // parameters of the tile's first distribution
   int32_t unres[kUnresCap];
+  uint32_t cell_range[kTile];  // cells complete inside the tile: first | last << 16
 };
 
 struct ForestArgs {
@@ -676,6 +678,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
     s.dfirst = df;
     s.dprev = (t0 > 0 && SEG) ? (a.dists[df].elem_off == t0 ? df - 1 : df) : df;
     s.nunres = 0;
+    s.ncells = 0;
     s.tmax = 0;
     s.P0 = a.dists[df];
     s.prefix = t0 > 0 ? a.tile_prefix[tile] : 0ull;
@@ -908,11 +911,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
       if (dl >= kDeltaInf && dr >= kDeltaInf) {
         // a cell of one leaf: the leaf is its root's tree
         s.child[p][1] = ~id;
-        const uint64_t Clm1 = id > 0 ? s.C[p] : 0ull;
-        const uint64_t Chp1 = t0 + p + 1 == P.elem_off + P.n ? P.total : s.C[p + 2];
-        const uint64_t Knext = t0 + p + 1 == P.elem_off + P.n ? (1ull << 32) : s.K[p + 2];
-        finish_cell(a, P, dd, t0 + p, t0 + p, s.K[p + 1], s.K[p + 1], Clm1, s.C[p + 1],
-                    s.C[p + 1], Chp1, ~id, Knext);
+        s.cell_range[atomicAdd(&s.ncells, 1)] = (uint32_t)p | ((uint32_t)p << 16);
       } else if (dl > dr) {
         if (p + 1 < tn)
           s.child[p + 1][0] = ~id;
@@ -973,12 +972,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
     if (dl >= kDeltaInf && dr >= kDeltaInf && pl >= 0) {
       // the top of a cell inside the tile: leaves [pl, pr - 1], root at pl
       s.child[pl][1] = id;
-      const int32_t lo_id = base_id + pl;
-      const uint64_t Clm1 = lo_id > 0 ? s.C[pl] : 0ull;
-      const uint64_t Chp1 = t0 + pr == P.elem_off + P.n ? P.total : s.C[pr + 1];
-      const uint64_t Knext = t0 + pr == P.elem_off + P.n ? (1ull << 32) : s.K[pr + 1];
-      finish_cell(a, P, dd, t0 + pl, t0 + pr - 1, s.K[pl + 1], s.K[pr], Clm1, s.C[pl + 1],
-                  s.C[pr], Chp1, id, Knext);
+      s.cell_range[atomicAdd(&s.ncells, 1)] = (uint32_t)pl | ((uint32_t)(pr - 1) << 16);
     } else if (dl > dr) {
       if (pr < tn)
         s.child[pr][0] = id;
@@ -989,6 +983,23 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
     }
   }
   __syncthreads();
+
+  // ---- guide entries of the cells completed inside the tile -----------------
+  // (by consecutive threads, after the links: done inside the links, a cell's
+  // entries stalled every lane of its warp)
+  for (int i = tid; i < s.ncells; i += kForestThreads) {
+    const uint32_t r = s.cell_range[i];
+    const int lo = (int)(r & 0xFFFFu), hi = (int)(r >> 16);
+    const int dd = SEG ? s.dist[lo] : 0;
+    const rtf_dist& P = SEG ? a.dists[dd] : s.P0;
+    const int64_t end = P.elem_off + P.n;
+    const int64_t glo = t0 + lo;
+    const uint64_t Clm1 = glo > P.elem_off ? s.C[lo] : 0ull;
+    const uint64_t Chp1 = t0 + hi + 1 == end ? P.total : s.C[hi + 2];
+    const uint64_t Knext = t0 + hi + 1 == end ? (1ull << 32) : s.K[hi + 2];
+    finish_cell(a, P, dd, glo, t0 + hi, s.K[lo + 1], s.K[hi + 1], Clm1, s.C[lo + 1], s.C[hi + 1],
+                Chp1, s.child[lo][1], Knext);
+  }
 
   // ---- node records -----------------------------------------------------------
   // Consecutive threads on consecutive records (leaf l = tid + k * blockDim); a

@@ -71,3 +71,34 @@ def test_launch_shape_changes_no_result_and_is_tuned(tmp_path, monkeypatch):
         f.check_status()
     finally:
         api.reset_launch_shape()
+
+
+def test_env_guide_bits_tuner(tmp_path, monkeypatch):
+    """The 2-D map tuner times its candidates around (log2 cols, log2 rows),
+    returns the fastest and caches it; the map built with its choice equals
+    the oracle's structure (rows and marginal)."""
+    from oracle import oracle as orc
+    from paper_1901_05423_gb300 import api, autotune
+    from paper_1901_05423_gb300 import workloads as W
+    monkeypatch.setenv("RTF_CACHE_DIR", str(tmp_path))
+    dev = torch.device("cuda:0")
+    H, Wd = 64, 256
+    lum_h = W.env_map(H, Wd, seed=7)
+    lum = torch.from_numpy(lum_h.reshape(-1)).to(dev)
+    mr, mm, times = autotune.tune_env_bits(lum, H, Wd, 1 << 20, probe_pairs=1 << 16, reps=1)
+    assert (mr, mm) == min(times, key=times.get)
+    assert all(6 <= a <= 10 and 5 <= b <= 7 for a, b in times)
+    assert autotune.tune_env_bits(lum, H, Wd, 1 << 20)[:2] == (mr, mm)  # cached
+    f = api.rtf_build_batched(lum, [Wd] * H + [H], [mr] * H + [mm], marginal=True)
+    torch.cuda.synchronize()
+    f.check_status()
+    rows, marg = orc.build_env(lum_h, 1 << mr, 1 << mm)
+    ch = f.children().cpu().numpy()
+    C = f.cdf().cpu().numpy().view(np.uint64)
+    g = f.guide.cpu().numpy()
+    for r in (0, H // 2, H - 1):
+        assert np.array_equal(C[r * Wd:(r + 1) * Wd], rows[r].C[:-1])
+        assert np.array_equal(ch[r * Wd:(r + 1) * Wd], rows[r].nodes)
+        assert np.array_equal(g[r << mr:(r + 1) << mr], rows[r].guide)
+    assert np.array_equal(ch[H * Wd:], marg.nodes)
+    assert np.array_equal(g[H << mr:], marg.guide)
