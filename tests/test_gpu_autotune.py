@@ -92,7 +92,7 @@ def test_env_guide_bits_tuner(tmp_path, monkeypatch):
     f = api.rtf_build_batched(lum, [Wd] * H + [H], [mr] * H + [mm], marginal=True)
     torch.cuda.synchronize()
     f.check_status()
-    rows, marg = orc.build_env(lum_h, 1 << mr, 1 << mm)
+    rows, marg = orc.build_env(lum_h, 1 << mm, 1 << mr)  # marginal's cells first
     ch = f.children().cpu().numpy()
     C = f.cdf().cpu().numpy().view(np.uint64)
     g = f.guide.cpu().numpy()
