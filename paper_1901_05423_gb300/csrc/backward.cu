@@ -350,6 +350,9 @@ __global__ void __launch_bounds__(kBwThreads)
     float p2 = pow2_neg(P.scale);
     dflt sac = df_zero(), sx = df_zero();
     uint64_t cnext = nodes[e0].cdf;
+    // C_e as a double-float, carried along the run (C_{e+1} = C_e + q_e; a
+    // row's q_e is one exact float): one 64-bit conversion per run
+    dflt Cd = df_from_u64(cnext);
     const int64_t e1 = min(e0 + (int64_t)kBwPer, t1);
     for (int64_t e = e0; e < e1; ++e) {
       if (e >= end) {
@@ -364,26 +367,27 @@ __global__ void __launch_bounds__(kBwThreads)
         K = ldexp(1.0, P.scale) / (double)P.total;
         marg = (P.flags & kDistMarginal) != 0;
         p2 = pow2_neg(P.scale);
+        Cd = df_zero();  // a new distribution starts at C = 0
       }
       const uint64_t c = cnext;
       cnext = (e + 1 < N) ? nodes[e + 1].cdf : 0ull;
       const uint64_t cup = (e + 1 < end) ? cnext : P.total;
       const float2 ax = acc[e];
       const uint64_t q = cup - c;
+      // a row weight's q has at most 24 significant bits: q and w' are exact floats
+      const dflt qd = marg ? df_from_u64(q) : dflt{__ull2float_rn(q), 0.0f};
       if ((ax.x != 0.0f || ax.y != 0.0f) && q != 0) {
-        // a row weight's q has at most 24 significant bits: w' is one float
         dflt wq;
-        if (marg) {
+        if (marg)
           wq = qweight_df(q, P.scale);
-        } else {
-          const float qf = __ull2float_rn(q);
-          wq = dflt{p2 != 0.0f ? qf * p2 : scalbnf(qf, -P.scale), 0.0f};
-        }
+        else
+          wq = dflt{p2 != 0.0f ? qd.hi * p2 : scalbnf(qd.hi, -P.scale), 0.0f};
         dflt av, bv;
         bin_terms(ax, wq.hi, wq.lo, &av, &bv);
-        sac = df_add(sac, df_mul(av, df_mul(df_from_u64(c), invT)));
+        sac = df_add(sac, df_mul(av, df_mul(Cd, invT)));
         sx = df_add(sx, dflt{ax.y, 0.0f});
       }
+      Cd = df_add(Cd, qd);
     }
     contrib = df_to_double(sac) + K * df_to_double(sx);
   }
