@@ -33,13 +33,13 @@ METRIC = "samples/s & build elem/s at n=2^24 (bit-exact); batched vs looped; % H
 N_W = 1 << 24
 M_BITS = 20
 N_S = 1 << 28
-# kernels of this library per step: build 7 (init_dists, scale, tile_sum,
-# tile_scan, forest, forest_merge, guide), sampling 2, backward 4 (scatter in
-# two passes over the halves of the 2^24 bins, bin_total, suffix)
-LAUNCHES_PER_STEP = 13
+# kernels of this library per step: build 6 (init_dists, scale, tile_sum,
+# forest_lean, forest_merge, fill), sampling 2, backward 4 (scatter in two
+# passes over the halves of the 2^24 bins, bin_total, suffix)
+LAUNCHES_PER_STEP = 12
 # with --streams 3 the i.i.d. set is sampled in ACC_CHUNKS chunks and each
 # chunk's terms added by one scatter pass (2^25 samples: under 4 per bin)
-LAUNCHES_PER_STEP_ACC = 7 + 1 + 8 + 8 + 2
+LAUNCHES_PER_STEP_ACC = 6 + 1 + 8 + 8 + 2
 
 
 # DRAM bytes per unit measured by ncu at full size (dram__bytes_read.sum +
@@ -821,6 +821,41 @@ def extra_methods(dev, reps=5):
             "table1_loads": table, "n24_loads": main_loads, **times}
 
 
+def profile_batched():
+    """Profiling aid (no timing, no output line): the batched paths at a size an
+    ncu capture of every pass can hold (about 1 GB on the device): a ragged
+    batch of 4096 distributions (sizes log-uniform in [8, 65536], guide bits
+    round(log2 n)) built three times and 2^25 tagged samples mapped twice; the
+    2048 x 4096 map (2^12 cells per row and for the marginal) built and 2^24
+    pairs mapped twice."""
+    import torch
+    from paper_1901_05423_gb300 import api
+    from paper_1901_05423_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    w_h, off = W.ragged_batch(4096, seed=0)
+    sizes = np.diff(off)
+    ms = np.clip(np.round(np.log2(sizes)).astype(int), 3, 16)
+    w = torch.from_numpy(w_h).to(dev)
+    f = api.rtf_build_batched(w, sizes, ms)
+    for _ in range(2):
+        api.rtf_build_batched(w, sizes, ms, forest=f, plan_dev=f._plan_dev)
+    ns = 1 << 25
+    u = api.u32_tensor(W.iid_u32(ns, seed=1), dev)
+    dist = torch.from_numpy(W.dist_ids(ns, len(sizes), seed=2)).to(dev)
+    for _ in range(2):
+        api.rtf_sample(f, u, dist_id=dist)
+    H, Wd = 2048, 4096
+    lum = torch.from_numpy(W.env_map(H, Wd, seed=0).reshape(-1)).to(dev)
+    fe = api.rtf_build_batched(lum, [Wd] * H + [H], [12] * (H + 1), marginal=True)
+    u2 = api.u32_tensor(W.iid_u32(2 * (1 << 24), seed=3), dev)
+    for _ in range(2):
+        api.rtf_sample(fe, u2, mode=api.SAMPLE_2D)
+    torch.cuda.synchronize()
+    f.check_status()
+    fe.check_status()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -840,7 +875,12 @@ def main():
     ap.add_argument("--samples-log2", type=int, default=28,
                     help="2^k samples per set; the benchmarked workload is k = 28, smaller k "
                          "gives the same structure with fewer samples (profiler captures)")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="profiling aid: only the ragged batch (4096 distributions) and the "
+                         "2-D map paths at a size an ncu capture holds; prints nothing")
     args = ap.parse_args()
+    if args.profile_batched:
+        return profile_batched()
     global N_S
     N_S = 1 << args.samples_log2
     if args.impl == "reference":
