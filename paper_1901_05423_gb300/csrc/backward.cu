@@ -20,7 +20,8 @@
 //                        bin, runs of equal bins inside a warp merged first
 //   bin_total_kernel     G_d = sum_{i in d} Xi_i / w'_i per distribution
 //   suffix_kernel        reverse decoupled-lookback scan of A_i / w'_i per
-//                        distribution (fp32 in the tile, fp64 carry), then
+//                        distribution (double-floats in the tile and in the
+//                        carries between tiles), then
 //                        dL/dw_k = G_d - S_k - X_k / w'_k
 //   add_row_kernel       (2-D) the marginal's gradient dL/dR_r added to every
 //                        weight of row r
@@ -39,8 +40,8 @@ struct BwLayout {
   size_t acc;    // float2 [N]  {A_i, X_i}
   size_t G;      // double [D]
   size_t flags;  // u32 [tiles]
-  size_t carry;  // double [tiles]   sum of a over a tile's first piece
-  size_t incl;   // double [tiles]   that sum plus everything after it
+  size_t carry;  // float2 [tiles]   sum of a over a tile's first piece (double-float)
+  size_t incl;   // float2 [tiles]   that sum plus everything after it
   size_t ticket; // u32
   size_t zero_end;
   size_t R;      // float2 [D]  (2-D: row totals as double-floats)
@@ -138,11 +139,36 @@ __device__ __forceinline__ dflt df_from_double(double x) {
 
 __device__ __forceinline__ float df_to_float(dflt a) { return __fadd_rn(a.hi, a.lo); }
 
-// An integer below 2^63 as a double-float: the nearest float and the float of
-// the exact remainder.
+// Conversions from 64-bit integers without the fp64 unit: on this part 64-bit
+// conversions run on the fp64 pipe, whose rate is a small fraction of the
+// fp32 one, so one conversion per element made the backward's bin totals
+// fp64-bound.  An integer below 2^23 becomes a float exactly by placing it in
+// the significand of 2^23 and subtracting 2^23.
+__device__ __forceinline__ float small_to_float(uint32_t x) {
+  return __fsub_rn(__uint_as_float(0x4B000000u | x), 8388608.0f);
+}
+
+// q exactly, for q with at most 24 significant bits (a quantised weight of a
+// float: floor(w 2^S)).  Horner over 16-bit pieces: every partial value is q
+// shifted right, which keeps at most 24 significant bits, so each step is exact.
+__device__ __forceinline__ float float_of_q24(uint64_t q) {
+  const uint32_t hi = (uint32_t)(q >> 32), lo = (uint32_t)q;
+  float f = small_to_float(hi >> 16);
+  f = __fmaf_rn(f, 65536.0f, small_to_float(hi & 0xFFFFu));
+  f = __fmaf_rn(f, 65536.0f, small_to_float(lo >> 16));
+  return __fmaf_rn(f, 65536.0f, small_to_float(lo & 0xFFFFu));
+}
+
+// An integer below 2^63 as a double-float (relative error about 2^-47): three
+// exact 21-bit pieces added with error-free sums.
 __device__ __forceinline__ dflt df_from_u64(uint64_t x) {
-  const float h = __ull2float_rn(x);
-  return dflt{h, __ll2float_rn((int64_t)(x - __float2ull_rn(h)))};
+  const float a = __fmul_rn(small_to_float((uint32_t)(x >> 42)), 4398046511104.0f);  // 2^42
+  const float b = __fmul_rn(small_to_float((uint32_t)(x >> 21) & 0x1FFFFFu), 2097152.0f);  // 2^21
+  const float c = small_to_float((uint32_t)x & 0x1FFFFFu);
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df_add(dflt{s, e}, dflt{c, 0.0f});
 }
 
 __device__ __forceinline__ dflt df_shfl_down(dflt a, int d) {
@@ -317,8 +343,7 @@ __global__ void __launch_bounds__(kBwThreads)
                      const rtf_dist* __restrict__ dists, int D, int64_t N, double* G) {
   __shared__ int dfirst_s, dlast_s;
   __shared__ double part[kBwThreads / 32];
-  __shared__ dflt invT_s;
-  __shared__ double K_s;
+  __shared__ dflt invT_s, K_s;
   const int64_t t0 = (int64_t)blockIdx.x * kBwTile;
   const int64_t t1 = min(t0 + (int64_t)kBwTile, N);
   if (threadIdx.x == 0) {
@@ -329,22 +354,21 @@ __global__ void __launch_bounds__(kBwThreads)
     // divisions are slow on this part)
     const double T = (double)dists[df].total;
     invT_s = df_from_double(1.0 / T);
-    K_s = ldexp(1.0, dists[df].scale) / T;
+    K_s = df_from_double(ldexp(1.0, dists[df].scale) / T);
   }
   __syncthreads();
   const int dfirst = dfirst_s, dlast = dlast_s;
   const int64_t e0 = t0 + (int64_t)threadIdx.x * kBwPer;
   int d = dfirst;
   if (e0 < t1 && dlast != dfirst) d = find_dist(dists, dfirst, dlast, e0);
-  double contrib = 0.0;
+  dflt contrib = df_zero();
   if (e0 < t1) {
     rtf_dist P = dists[d];
     int64_t end = P.elem_off + P.n;
-    dflt invT = invT_s;
-    double K = K_s;
+    dflt invT = invT_s, K = K_s;
     if (d != dfirst) {
       invT = df_from_double(1.0 / (double)P.total);
-      K = ldexp(1.0, P.scale) / (double)P.total;
+      K = df_from_double(ldexp(1.0, P.scale) / (double)P.total);
     }
     bool marg = (P.flags & kDistMarginal) != 0;
     float p2 = pow2_neg(P.scale);
@@ -356,15 +380,14 @@ __global__ void __launch_bounds__(kBwThreads)
     const int64_t e1 = min(e0 + (int64_t)kBwPer, t1);
     for (int64_t e = e0; e < e1; ++e) {
       if (e >= end) {
-        const double v = df_to_double(sac) + K * df_to_double(sx);
-        if (dlast != dfirst) atomicAdd(G + d, v);
+        if (dlast != dfirst) atomicAdd(G + d, df_to_double(df_add(sac, df_mul(K, sx))));
         sac = df_zero();
         sx = df_zero();
         ++d;
         P = dists[d];
         end = P.elem_off + P.n;
         invT = df_from_double(1.0 / (double)P.total);
-        K = ldexp(1.0, P.scale) / (double)P.total;
+        K = df_from_double(ldexp(1.0, P.scale) / (double)P.total);
         marg = (P.flags & kDistMarginal) != 0;
         p2 = pow2_neg(P.scale);
         Cd = df_zero();  // a new distribution starts at C = 0
@@ -375,7 +398,7 @@ __global__ void __launch_bounds__(kBwThreads)
       const float2 ax = acc[e];
       const uint64_t q = cup - c;
       // a row weight's q has at most 24 significant bits: q and w' are exact floats
-      const dflt qd = marg ? df_from_u64(q) : dflt{__ull2float_rn(q), 0.0f};
+      const dflt qd = marg ? df_from_u64(q) : dflt{float_of_q24(q), 0.0f};
       if ((ax.x != 0.0f || ax.y != 0.0f) && q != 0) {
         dflt wq;
         if (marg)
@@ -389,15 +412,15 @@ __global__ void __launch_bounds__(kBwThreads)
       }
       Cd = df_add(Cd, qd);
     }
-    contrib = df_to_double(sac) + K * df_to_double(sx);
+    contrib = df_add(sac, df_mul(K, sx));
   }
   if (dlast != dfirst) {
-    if (e0 < t1) atomicAdd(G + d, contrib);
+    if (e0 < t1) atomicAdd(G + d, df_to_double(contrib));
     return;
   }
   // the whole block lies in one distribution: the warp's sum in double-float,
   // the block's in fp64
-  dflt v = df_from_double(contrib);
+  dflt v = contrib;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = df_to_double(v);
@@ -409,25 +432,86 @@ __global__ void __launch_bounds__(kBwThreads)
   }
 }
 
+// Block-wide lookback of the reverse scan: the sum of the values published by
+// the tiles after `tile`, the carries (sum over a tile's first piece) of those
+// before the first tile whose inclusive value (its first piece plus
+// everything after it) is published, plus that inclusive value.  Every thread
+// reads one successor's flag per round; the values are double-floats {hi, lo}.
+// Gives up after kSpinLimit rounds without progress (RTF_STATUS_TIMEOUT).
+struct SuffixLookback {
+  int first_prefix, first_invalid;
+  dflt part[kBwThreads / 32];
+  dflt E;
+};
+
+__device__ dflt suffix_lookback(SuffixLookback& sh, int64_t tile, int64_t ntiles,
+                                const uint32_t* flags, const float2* carry, const float2* incl,
+                                uint32_t* status) {
+  dflt E = df_zero();
+  int64_t look = tile + 1;
+  long long spins = 0;
+  while (look < ntiles) {
+    if (threadIdx.x == 0) {
+      sh.first_prefix = kBwThreads;
+      sh.first_invalid = kBwThreads;
+    }
+    __syncthreads();
+    const int64_t idx = look + threadIdx.x;
+    const uint32_t fl = idx < ntiles ? *((volatile uint32_t*)(flags + idx)) : 2u;
+    if (fl == 2) atomicMin(&sh.first_prefix, (int)threadIdx.x);
+    if (fl == 0) atomicMin(&sh.first_invalid, (int)threadIdx.x);
+    __syncthreads();
+    const int pfx = sh.first_prefix, inv = sh.first_invalid;
+    if (inv < pfx) {
+      if (++spins > kSpinLimit) {
+        if (threadIdx.x == 0) raise_status(status, RTF_STATUS_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+      __syncthreads();
+      continue;
+    }
+    __threadfence();
+    dflt x = df_zero();
+    if ((int)threadIdx.x <= pfx && idx < ntiles) {
+      // read through L2 (not L1), where the other blocks' stores are visible
+      const float2 v = __ldcg((int)threadIdx.x < pfx ? carry + idx : incl + idx);
+      x = dflt{v.x, v.y};
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = df_add(x, df_shfl_xor(x, o));
+    if ((threadIdx.x & 31) == 0) sh.part[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      dflt t = df_zero();
+      for (int k = 0; k < kBwThreads / 32; ++k) t = df_add(t, sh.part[k]);
+      sh.E = t;
+    }
+    __syncthreads();
+    E = df_add(E, sh.E);
+    if (pfx < kBwThreads) break;
+    look += kBwThreads;
+  }
+  return E;
+}
+
 // Reverse segmented scan: S_k = sum_{i > k, same distribution} A_i / w'_i, then
 // the gradient.  Tiles are taken from the end by ticket; each tile publishes
 // the sum of a over its first piece (the part of dist(t0) inside the tile)
 // and, once known, that sum plus everything after it.  The lookback is
 // block-wide: every thread reads one successor's flag per round.  Terms and
-// sums inside the tile are double-floats, carries fp64.
+// sums inside the tile and the carries between tiles are double-floats.
 __global__ void __launch_bounds__(kBwThreads)
     suffix_kernel(const float2* __restrict__ acc, const float* __restrict__ w,
                   const float2* __restrict__ R, const rtf_dist* __restrict__ dists, int D,
                   int64_t N, int64_t Nw, const double* __restrict__ G, uint32_t* flags,
-                  double* carry, double* incl, uint32_t* ticket, float* grad_w, float* gradR,
+                  float2* carry, float2* incl, uint32_t* ticket, float* grad_w, float* gradR,
                   uint32_t* status) {
   __shared__ uint32_t tick_s;
   __shared__ int dfirst_s;
   __shared__ float exh_s[kBwThreads], exl_s[kBwThreads];
   __shared__ int exf_s[kBwThreads];
-  __shared__ int first_prefix_s, first_invalid_s;
-  __shared__ double part_s[kBwThreads / 32];
-  __shared__ double E_s;
+  __shared__ SuffixLookback lb_s;
   if (threadIdx.x == 0) tick_s = atomicAdd(ticket, 1u);
   __syncthreads();
   const int64_t ntiles = (N + kBwTile - 1) / kBwTile;
@@ -514,64 +598,22 @@ __global__ void __launch_bounds__(kBwThreads)
     exv = dflt{exh_s[myslot - 1], exl_s[myslot - 1]};
     exf = exf_s[myslot - 1];
   }
-  const double first_piece =
-      df_to_double(dflt{exh_s[kBwThreads - 1], exl_s[kBwThreads - 1]});
+  const dflt first_piece{exh_s[kBwThreads - 1], exl_s[kBwThreads - 1]};
   const bool first_piece_closed = exf_s[kBwThreads - 1] != 0;  // dist(t0) ends in this tile
   const int dlast_tile = find_dist(dists, dfirst, min(D - 1, dfirst + kBwTile), t1 - 1);
   const bool continues = (dists[dlast_tile].elem_off + dists[dlast_tile].n) > t1;
   if (threadIdx.x == 0) {
-    carry[tile] = first_piece;
-    incl[tile] = first_piece;
+    carry[tile] = make_float2(first_piece.hi, first_piece.lo);
+    incl[tile] = make_float2(first_piece.hi, first_piece.lo);
     __threadfence();
     atomicExch(flags + tile, first_piece_closed ? 2u : 1u);
   }
   // block-wide lookback for the sum beyond t1 in the distribution of t1 - 1
-  double E = 0.0;
-  if (continues) {
-    int64_t look = tile + 1;
-    long long spins = 0;
-    while (look < ntiles) {
-      if (threadIdx.x == 0) {
-        first_prefix_s = kBwThreads;
-        first_invalid_s = kBwThreads;
-      }
-      __syncthreads();
-      const int64_t idx = look + threadIdx.x;
-      const uint32_t fl = idx < ntiles ? *((volatile uint32_t*)(flags + idx)) : 2u;
-      if (fl == 2) atomicMin(&first_prefix_s, (int)threadIdx.x);
-      if (fl == 0) atomicMin(&first_invalid_s, (int)threadIdx.x);
-      __syncthreads();
-      const int pfx = first_prefix_s, inv = first_invalid_s;
-      if (inv < pfx) {
-        if (++spins > kSpinLimit) {
-          if (threadIdx.x == 0) raise_status(status, RTF_STATUS_TIMEOUT);
-          break;
-        }
-        __nanosleep(64);
-        __syncthreads();
-        continue;
-      }
-      __threadfence();
-      double x = 0.0;
-      if ((int)threadIdx.x < pfx && idx < ntiles) x = *((volatile double*)(carry + idx));
-      if ((int)threadIdx.x == pfx && idx < ntiles) x = *((volatile double*)(incl + idx));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if ((threadIdx.x & 31) == 0) part_s[threadIdx.x >> 5] = x;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < kBwThreads / 32; ++k) t += part_s[k];
-        E_s = t;
-      }
-      __syncthreads();
-      E += E_s;
-      if (pfx < kBwThreads) break;
-      look += kBwThreads;
-    }
-  }
+  const dflt E = continues ? suffix_lookback(lb_s, tile, ntiles, flags, carry, incl, status)
+                           : df_zero();
   if (threadIdx.x == 0 && !first_piece_closed) {
-    incl[tile] = first_piece + E;
+    const dflt v = df_add(first_piece, E);
+    incl[tile] = make_float2(v.hi, v.lo);
     __threadfence();
     atomicExch(flags + tile, 2u);
   }
@@ -579,9 +621,9 @@ __global__ void __launch_bounds__(kBwThreads)
   // element results, walking the thread's run from the right: until the first
   // tail the suffix continues past the thread (exclusive value, plus the
   // incoming carry when no tail lies to the right inside the tile)
-  const double after = exf ? df_to_double(exv) : df_to_double(exv) + E;
+  const dflt after = exf ? exv : df_add(exv, E);
   dflt inrun = df_zero();
-  dflt base = df_from_double(G[dk[kBwPer - 1]] - after);
+  dflt base = df_sub(df_from_double(G[dk[kBwPer - 1]]), after);
 #pragma unroll
   for (int k = kBwPer - 1; k >= 0; --k) {
     const int64_t e = e0 + k;
@@ -606,14 +648,16 @@ __global__ void __launch_bounds__(kBwThreads)
 __global__ void __launch_bounds__(kBwThreads)
     suffix_single_kernel(const float2* __restrict__ acc, const float* __restrict__ w,
                          const rtf_dist* __restrict__ dists, int64_t N,
-                         const double* __restrict__ G, uint32_t* flags, double* carry,
-                         double* incl, uint32_t* ticket, float* grad_w, uint32_t* status) {
+                         const double* __restrict__ G, uint32_t* flags, float2* carry,
+                         float2* incl, uint32_t* ticket, float* grad_w, uint32_t* status) {
   __shared__ uint32_t tick_s;
   __shared__ dflt wtot_s[kBwThreads / 32];
-  __shared__ int first_prefix_s, first_invalid_s;
-  __shared__ double part_s[kBwThreads / 32];
-  __shared__ double E_s;
-  if (threadIdx.x == 0) tick_s = atomicAdd(ticket, 1u);
+  __shared__ SuffixLookback lb_s;
+  __shared__ dflt G_s;
+  if (threadIdx.x == 0) {
+    tick_s = atomicAdd(ticket, 1u);
+    G_s = df_from_double(G[0]);  // once per block (fp64 is slow on this part)
+  }
   __syncthreads();
   const int64_t ntiles = (N + kBwTile - 1) / kBwTile;
   const int64_t tile = ntiles - 1 - (int64_t)tick_s;
@@ -667,66 +711,24 @@ __global__ void __launch_bounds__(kBwThreads)
     if (k > wid) exv = df_add(exv, wtot_s[k]);
     tile_tot = df_add(tile_tot, wtot_s[k]);
   }
-  const double tile_tot_d = df_to_double(tile_tot);
   const bool last_tile = t1 == N;  // the distribution's last element lies here
   if (threadIdx.x == 0) {
-    carry[tile] = tile_tot_d;
-    incl[tile] = tile_tot_d;
+    carry[tile] = make_float2(tile_tot.hi, tile_tot.lo);
+    incl[tile] = make_float2(tile_tot.hi, tile_tot.lo);
     __threadfence();
     atomicExch(flags + tile, last_tile ? 2u : 1u);
   }
   // block-wide lookback for the sum beyond t1 in the distribution of t1 - 1
-  double E = 0.0;
-  if (!last_tile) {
-    int64_t look = tile + 1;
-    long long spins = 0;
-    while (look < ntiles) {
-      if (threadIdx.x == 0) {
-        first_prefix_s = kBwThreads;
-        first_invalid_s = kBwThreads;
-      }
-      __syncthreads();
-      const int64_t idx = look + threadIdx.x;
-      const uint32_t fl = idx < ntiles ? *((volatile uint32_t*)(flags + idx)) : 2u;
-      if (fl == 2) atomicMin(&first_prefix_s, (int)threadIdx.x);
-      if (fl == 0) atomicMin(&first_invalid_s, (int)threadIdx.x);
-      __syncthreads();
-      const int pfx = first_prefix_s, inv = first_invalid_s;
-      if (inv < pfx) {
-        if (++spins > kSpinLimit) {
-          if (threadIdx.x == 0) raise_status(status, RTF_STATUS_TIMEOUT);
-          break;
-        }
-        __nanosleep(64);
-        __syncthreads();
-        continue;
-      }
-      __threadfence();
-      double x = 0.0;
-      if ((int)threadIdx.x < pfx && idx < ntiles) x = *((volatile double*)(carry + idx));
-      if ((int)threadIdx.x == pfx && idx < ntiles) x = *((volatile double*)(incl + idx));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if ((threadIdx.x & 31) == 0) part_s[threadIdx.x >> 5] = x;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < kBwThreads / 32; ++k) t += part_s[k];
-        E_s = t;
-      }
-      __syncthreads();
-      E += E_s;
-      if (pfx < kBwThreads) break;
-      look += kBwThreads;
-    }
-  }
+  const dflt E = last_tile ? df_zero()
+                           : suffix_lookback(lb_s, tile, ntiles, flags, carry, incl, status);
   if (!last_tile && threadIdx.x == 0) {
-    incl[tile] = tile_tot_d + E;
+    const dflt v = df_add(tile_tot, E);
+    incl[tile] = make_float2(v.hi, v.lo);
     __threadfence();
     atomicExch(flags + tile, 2u);
   }
   if (e0 >= t1) return;
-  const dflt base = df_from_double(G[0] - (df_to_double(exv) + E));
+  const dflt base = df_sub(df_sub(G_s, exv), E);
   dflt inrun = df_zero();
   float gk[kBwPer];
 #pragma unroll
@@ -837,8 +839,8 @@ cudaError_t launch_backward_finish(const rtf_forest* f, const float* w, int mode
   const bool two_d = mode == RTF_SAMPLE_2D;
   double* G = reinterpret_cast<double*>(p.base + L.G);
   uint32_t* flags = reinterpret_cast<uint32_t*>(p.base + L.flags);
-  double* carry = reinterpret_cast<double*>(p.base + L.carry);
-  double* incl = reinterpret_cast<double*>(p.base + L.incl);
+  float2* carry = reinterpret_cast<float2*>(p.base + L.carry);
+  float2* incl = reinterpret_cast<float2*>(p.base + L.incl);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(p.base + L.ticket);
   float2* R = reinterpret_cast<float2*>(p.base + L.R);
   float* gradR = reinterpret_cast<float*>(p.base + L.gradR);
