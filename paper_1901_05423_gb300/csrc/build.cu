@@ -1044,10 +1044,15 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
 // 32 c + 1 .. 32 c + 32, the right-hand splits of the chunk's leaves; position 0
 // (delta_{t0-1}) lies in no chunk.
 struct LeanShared {
-  alignas(16) uint64_t C[kTile + 2];  // C_{t0-1} .. C_{t1}
+  // C_{t0-1} .. C_{t1} at Cbuf[1 .. tn + 2] (the CDF of tile-local leaf l at
+  // index l + 2, so that each thread's four values form two aligned 16-byte
+  // stores); read through C = Cbuf + 1
+  alignas(16) uint64_t Cbuf[kTile + 4];
   alignas(16) int32_t child[kTile][2];
   uint32_t cell_range[kTile];         // cells complete inside the tile: first | last << 16
-  uint8_t d[kTile + 8];               // d[p]: distance at position p
+  // distance at position p at dbuf[p + 3] (each thread's four distances form
+  // one aligned 4-byte store); read through d = dbuf + 3
+  alignas(4) uint8_t dbuf[kTile + 12];
   // per chunk: gtm[c][t] = positions with a distance > t, for t up to the
   // chunk's largest finite distance fmax[c]; above it only the boundaries
   // (infinite distance, mask infm[c]) are larger
@@ -1104,19 +1109,28 @@ __device__ __forceinline__ int lean_walk(const LeanShared& s, int from, int nchu
 __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_kernel(ForestArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LeanShared& s = *reinterpret_cast<LeanShared*>(smem_raw);
+  uint64_t* const sC = s.Cbuf + 1;  // sC[p]: C of tile-local leaf p - 1
+  uint8_t* const sd = s.dbuf + 3;   // sd[p]: distance at position p
   const int64_t tile = blockIdx.x;
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
   const int tn = (int)(t1 - t0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int S = a.dists[0].scale;
-  const int lbase = 128 * warp + lane;  // tile-local leaf of k = 0
+  const int lbase = 128 * warp + lane;  // lane-strided: tile-local leaf of k = 0
+  const int lb = 4 * tid;               // blocked: the thread's leaves lb .. lb + 3
 
-  // ---- weights, quantisation, prefix sums within the warp's 128 leaves -----
+  // ---- weights, quantisation, prefix sums (blocked: four consecutive leaves
+  // per thread, one 16-byte load, one warp scan of the thread totals) --------
   float wv[4];
+  if (lb + 4 <= tn && (reinterpret_cast<uintptr_t>(a.w) & 15) == 0) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(a.w + t0) + tid);
+    wv[0] = x.x;
+    wv[1] = x.y;
+    wv[2] = x.z;
+    wv[3] = x.w;
+  } else {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int l = lbase + 32 * k;
-    wv[k] = l < tn ? __ldg(a.w + t0 + l) : 0.0f;
+    for (int k = 0; k < 4; ++k) wv[k] = lb + k < tn ? __ldg(a.w + t0 + lb + k) : 0.0f;
   }
   if (tid == 0) {
     s.nunres = 0;
@@ -1126,27 +1140,26 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     s.prefix = t0 > 0 ? a.tile_prefix[tile] + a.range_prefix[tile / a.range_meta[0]] : 0ull;
   }
   uint64_t C[4];
-  uint64_t run = 0;
+  uint64_t tot = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const uint32_t b = weight_bits(wv[k]);
-    const uint64_t x = (lbase + 32 * k < tn && !weight_bad(b)) ? quantize_bits(b, S) : 0ull;
-    uint64_t incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t y = shfl_up64(incl, o);
-      if (lane >= o) incl += y;
-    }
-    C[k] = run + incl - x;
-    run += shfl_idx64(incl, 31);
+    C[k] = tot;  // exclusive within the thread
+    tot += (lb + k < tn && !weight_bad(b)) ? quantize_bits(b, S) : 0ull;
   }
-  if (lane == 0) s.wtot[warp] = run;
+  uint64_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = shfl_up64(incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s.wtot[warp] = incl;
   __syncthreads();
   // the warp's offset in the tile, the tile's prefix, C_{t0-1} and C_{t1}
   uint64_t off = lane < warp ? s.wtot[lane] : 0ull;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, (unsigned long long)off, o);
-  const uint64_t pre = s.prefix + off;
+  const uint64_t pre = s.prefix + off + (incl - tot);
   const uint64_t T = a.dists[0].total, R = a.dists[0].recip;
   const int z = a.dists[0].shift, m = a.dists[0].m;
   uint64_t K[4];
@@ -1154,71 +1167,111 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
   for (int k = 0; k < 4; ++k) {
     C[k] += pre;
     K[k] = key_of(C[k], T, R, z);
-    const int l = lbase + 32 * k;
-    if (l < tn) {
-      s.C[l + 1] = C[k];
-      s.child[l][0] = kUnset;
-      s.child[l][1] = kUnset;
+  }
+  if (lb + 4 <= tn) {
+    ulonglong2* cv = reinterpret_cast<ulonglong2*>(sC + lb + 1);
+    cv[0] = make_ulonglong2(C[0], C[1]);
+    cv[1] = make_ulonglong2(C[2], C[3]);
+    int4* ch = reinterpret_cast<int4*>(&s.child[lb][0]);
+    ch[0] = make_int4(kUnset, kUnset, kUnset, kUnset);
+    ch[1] = make_int4(kUnset, kUnset, kUnset, kUnset);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (lb + k < tn) {
+        sC[lb + k + 1] = C[k];
+        s.child[lb + k][0] = kUnset;
+        s.child[lb + k][1] = kUnset;
+      }
     }
   }
   if (lane == 0) s.Kfirst[warp] = K[0];
   if (tid == 0) {
-    uint64_t tot = 0;
-    for (int k = 0; k < kForestThreads / 32; ++k) tot += s.wtot[k];
-    const uint64_t Ct1 = s.prefix + tot;
-    s.C[tn + 1] = Ct1;
+    uint64_t tt = 0;
+    for (int k = 0; k < kForestThreads / 32; ++k) tt += s.wtot[k];
+    const uint64_t Ct1 = s.prefix + tt;
+    sC[tn + 1] = Ct1;
     s.Kfirst[kForestThreads / 32] = key_of(Ct1, T, R, z);
     uint64_t Cp = 0;
     if (t0 > 0) {
       const uint32_t b = weight_bits(a.w[t0 - 1]);
       Cp = s.prefix - (weight_bad(b) ? 0ull : quantize_bits(b, S));
     }
-    s.C[0] = Cp;
+    sC[0] = Cp;
     s.Kprev = key_of(Cp, T, R, z);
   }
   __syncthreads();
 
-  // ---- distances and their bit planes ---------------------------------------
+  // ---- distances (blocked: positions lb + 1 .. lb + 4, one 4-byte store) ----
   uint32_t dmx = 0;
+  {
+    const uint64_t below = shfl_down64(K[0], 1);  // key of leaf lb + 4 (lanes 0..30)
+    const uint64_t K4 = lane < 31 ? below : s.Kfirst[warp + 1];
+    uint32_t packed = 0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int l = lbase + 32 * k;
-    const uint64_t same = shfl_down64(K[k], 1);
-    const uint64_t nextk = k < 3 ? shfl_idx64(K[k < 3 ? k + 1 : k], 0) : s.Kfirst[warp + 1];
-    const uint64_t Kn = lane < 31 ? same : nextk;
-    uint32_t dlt = kDeltaInf;
-    if (l < tn && t0 + l + 1 < a.N && cell_of(K[k], m) == cell_of(Kn, m))
-      dlt = key_distance(K[k], Kn);
-    if (l < tn) {
-      s.d[l + 1] = (uint8_t)dlt;
-      a.delta[t0 + l] = (uint8_t)dlt;
-      dmx = max(dmx, dlt);
+    for (int k = 0; k < 4; ++k) {
+      const int l = lb + k;
+      const uint64_t Kn = k < 3 ? K[k < 3 ? k + 1 : k] : K4;
+      uint32_t dlt = kDeltaInf;
+      if (l < tn && t0 + l + 1 < a.N && cell_of(K[k], m) == cell_of(Kn, m))
+        dlt = key_distance(K[k], Kn);
+      if (l < tn) {
+        packed |= dlt << (8 * k);
+        dmx = max(dmx, dlt);  // the boundaries included: the merge pass searches for them
+      }
     }
-    const uint32_t v = l < tn ? min(dlt, kDeltaTop) : 0u;
-    const int c = 4 * warp + k;
-    const uint32_t vm = __ballot_sync(0xffffffffu, l < tn);
-    const uint32_t inf = __ballot_sync(0xffffffffu, l < tn && dlt >= kDeltaInf);
-    const uint32_t mx = __reduce_max_sync(0xffffffffu, v);
-    const int fm = (int)__reduce_max_sync(0xffffffffu, (l < tn && dlt < kDeltaInf) ? dlt + 1 : 0u) - 1;
-    uint32_t mine = 0u;
-    for (int t = 0; t <= min(fm, 31); ++t) {
-      const uint32_t mt = __ballot_sync(0xffffffffu, v > (uint32_t)t);
-      if (lane == t) mine = mt;
-    }
-    if (lane <= fm) s.gtm[c][lane] = mine;
-    if (lane == 0) {
-      s.valid[c] = vm;
-      s.infm[c] = inf;
-      s.fmax[c] = fm;
-      s.cmax[c] = mx;
+    *reinterpret_cast<uint32_t*>(sd + lb + 1) = packed;
+    if (lb + 4 <= tn) {
+      *reinterpret_cast<uint32_t*>(a.delta + t0 + lb) = packed;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (lb + k < tn) a.delta[t0 + lb + k] = (uint8_t)(packed >> (8 * k));
     }
   }
   dmx = __reduce_max_sync(0xffffffffu, dmx);
   if (lane == 0 && dmx) atomicMax(&s.tmax, dmx);
+  // the warp's chunks 4 warp .. 4 warp + 3 hold exactly its own 128 positions
+  __syncwarp();
+
+  // ---- threshold masks of the chunks (lane-strided: lane = position - 1 - 32 c)
+  // from the six bit planes of min(d, 33): lane t compares every position
+  // with t, bit plane by bit plane (t < 32, so its bit 5 is 0)
+  uint32_t lt_mask[5];  // all ones where bit b of this lane's t is set
+#pragma unroll
+  for (int b = 0; b < 5; ++b) lt_mask[b] = ((lane >> b) & 1) ? 0xffffffffu : 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int l = lbase + 32 * k;
+    const int c = 4 * warp + k;
+    const uint32_t dlt = l < tn ? sd[l + 1] : 0u;
+    const uint32_t v = l < tn ? min(dlt, kDeltaTop) : 0u;
+    const uint32_t vm = __ballot_sync(0xffffffffu, l < tn);
+    const uint32_t inf = __ballot_sync(0xffffffffu, l < tn && dlt >= kDeltaInf);
+    const int fm = (int)__reduce_max_sync(0xffffffffu, (l < tn && dlt < kDeltaInf) ? dlt + 1 : 0u) - 1;
+    if (fm >= 0) {
+      uint32_t pl[6];
+#pragma unroll
+      for (int b = 0; b < 6; ++b) pl[b] = __ballot_sync(0xffffffffu, (v >> b) & 1u);
+      uint32_t g = pl[5], e = vm & ~pl[5];
+#pragma unroll
+      for (int b = 4; b >= 0; --b) {
+        g |= e & pl[b] & ~lt_mask[b];
+        e &= ~(pl[b] ^ lt_mask[b]);
+      }
+      if (lane <= fm) s.gtm[c][lane] = g;
+    }
+    if (lane == 0) {
+      s.valid[c] = vm;
+      s.infm[c] = inf;
+      s.fmax[c] = fm;
+      s.cmax[c] = inf ? kDeltaTop : (uint32_t)max(fm, 0);
+    }
+  }
   if (tid == 0) {
     uint32_t d0 = kDeltaInf;
     if (t0 > 0 && cell_of(s.Kprev, m) == cell_of(K[0], m)) d0 = key_distance(s.Kprev, K[0]);
-    s.d[0] = (uint8_t)d0;
+    sd[0] = (uint8_t)d0;
   }
   const int nchunks = (tn + 31) >> 5;
   __syncthreads();
@@ -1231,10 +1284,10 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
   const rtf_dist& P = a.dists[0];
   // node at position 0 (delta_{t0-1}): its left bound lies outside the tile
   if (tid == 0) {
-    const uint32_t v = s.d[0];
+    const uint32_t v = sd[0];
     if (v < kDeltaInf) {
       const int pr = lean_walk(s, 0, nchunks, v, +1);
-      if (pr >= 0 && s.d[pr] == v) {
+      if (pr >= 0 && sd[pr] == v) {
         if (pr < tn)
           s.child[pr][0] = (int32_t)t0;
         else
@@ -1252,7 +1305,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     // leaf l, between positions l and l + 1: child 0 of node l + 1 when the
     // left distance is larger, else child 1 of node l (for a one-leaf cell,
     // node l is the cell's root and the leaf its whole tree)
-    const uint32_t dl = s.d[l], dr = s.d[l + 1];
+    const uint32_t dl = sd[l], dr = sd[l + 1];
     if (dl >= kDeltaInf) s.child[l][0] = ~(id > 0 ? id - 1 : 0);  // l starts a cell
     const bool single = dl >= kDeltaInf && dr >= kDeltaInf;
     const bool left = dl > dr && !single;
@@ -1275,7 +1328,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
         pl = 32 * c + 1 + (31 - __clz(msk));
       } else {
         pl = lean_walk(s, c - 1, nchunks, v, -1);
-        if (pl < 0 && s.d[0] > v) pl = 0;
+        if (pl < 0 && sd[0] > v) pl = 0;
       }
     }
     int pr;
@@ -1284,13 +1337,13 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
       pr = msk ? 32 * c + __ffs(msk) : lean_walk(s, c + 1, nchunks, v, +1);
     }
     const int32_t nid = (int32_t)(t0 + p);
-    if (pr < 0 || (pl < 0 && s.d[pr] > v)) {
+    if (pr < 0 || (pl < 0 && sd[pr] > v)) {
       const int slot = atomicAdd(&s.nunres, 1);
       if (slot < kUnresCap) s.unres[slot] = p;
       continue;
     }
-    const uint32_t dR = s.d[pr];
-    const uint32_t dL = pl >= 0 ? s.d[pl] : kDeltaInf + 1;
+    const uint32_t dR = sd[pr];
+    const uint32_t dL = pl >= 0 ? sd[pl] : kDeltaInf + 1;
     if (dL >= kDeltaInf && dR >= kDeltaInf && pl >= 0) {
       // the top of a cell inside the tile: leaves [pl, pr - 1], root at pl
       s.child[pl][1] = nid;
@@ -1311,9 +1364,9 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     const uint32_t r = s.cell_range[i];
     const int lo = (int)(r & 0xFFFFu), hi = (int)(r >> 16);
     const int64_t glo = t0 + lo;
-    const uint64_t Clm1 = glo > 0 ? s.C[lo] : 0ull;
-    const uint64_t Chp1 = t0 + hi + 1 == a.N ? T : s.C[hi + 2];
-    const uint64_t Clo = s.C[lo + 1], Chi = s.C[hi + 1];
+    const uint64_t Clm1 = glo > 0 ? sC[lo] : 0ull;
+    const uint64_t Chp1 = t0 + hi + 1 == a.N ? T : sC[hi + 2];
+    const uint64_t Clo = sC[lo + 1], Chi = sC[hi + 1];
     const uint64_t Knext = t0 + hi + 1 == a.N ? (1ull << 32) : key_of(Chp1, T, R, z);
     // the top of the cell's tree is its root's child 1 (written in the links)
     finish_cell(a, P, 0, glo, t0 + hi, key_of(Clo, T, R, z), key_of(Chi, T, R, z), Clm1, Clo, Chi,
@@ -1326,7 +1379,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     const int l = lbase + 32 * k;
     if (l >= tn) break;
     const int32_t c0 = s.child[l][0], c1 = s.child[l][1];
-    const uint64_t Cl = s.C[l + 1];
+    const uint64_t Cl = sC[l + 1];
     rtf_node* rec = a.nodes + t0 + l;
     if (c0 != kUnset && c1 != kUnset) {
       rtf_node r;
