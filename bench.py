@@ -514,9 +514,11 @@ def gpu_arm(args):
 
     peak, peak_kind = measured_peaks()
     avg = {k: float(np.mean(v)) for k, v in part.items()}
-    # algorithmic bytes per launch
+    # algorithmic bytes per launch; the build reads w three times (the largest
+    # exponent, the tile sums, the forest pass) and writes each node record
+    # (16 B), guide entry (4 B) and guide record (32 B) once
     alg = {
-        "build": 28 * N_W + 4 * (1 << M_BITS),
+        "build": 28 * N_W + 36 * (1 << M_BITS),
         "sample_iid": 12 * N_S,
         "sample_sorted": 12 * N_S,
         "backward": 16 * N_S + 24 * N_W,
@@ -674,7 +676,7 @@ def extra_ragged(dev, reps=3):
         "batched_build_ms": batched_ms, "looped_build_ms": looped_ms,
         "batched_over_looped": looped_ms / batched_ms,
         "build_elem_per_s": N / (batched_ms * 1e-3),
-        "build_hbm_frac": (28 * N + 4 * int(goff[-1])) / (batched_ms * 1e-3) / 1e9 / measured_peaks()[0],
+        "build_hbm_frac": (28 * N + 36 * int(goff[-1])) / (batched_ms * 1e-3) / 1e9 / measured_peaks()[0],
         "graph_build_plus_sample_ms": graph_ms,
         "samples_per_s_in_graph": ns / (graph_ms * 1e-3),
         "guide_bits_table": {str(k): int(v) for k, v in table.items()},
@@ -719,6 +721,8 @@ def extra_env_map(dev, reps=3):
                            "tuned_ms_build_plus_2^26_pairs": {f"{a},{b}": v
                                                                for (a, b), v in tuned.items()}},
             "build_ms": bms, "build_elem_per_s": (H * Wd + H) / (bms * 1e-3),
+            "build_hbm_frac": (28 * (H * Wd + H) + 36 * (H << m_row) + 36 * (1 << m_marg))
+                              / (bms * 1e-3) / 1e9 / measured_peaks()[0],
             "sample_ms": sms, "samples_2d_per_s": ns / (sms * 1e-3),
             "sample_hbm_frac": 24 * ns / (sms * 1e-3) / 1e9 / measured_peaks()[0]}
 
