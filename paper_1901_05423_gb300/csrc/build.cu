@@ -36,11 +36,29 @@ __device__ __forceinline__ float4 ld_weights4(const float4* p) { return __ldg(p)
 // ---------------------------------------------------------------------------
 // init
 // ---------------------------------------------------------------------------
+// Thread d < D fills dists[d]; thread t < ntiles also writes tile_dist0[t],
+// the distribution that holds element t kTile (the last d with offsets[d] <=
+// t kTile), by bisection over the offsets: the passes that follow start their
+// searches there instead of at distribution 0.
 __global__ void init_dists_kernel(rtf_dist* dists, int D, const int64_t* offsets,
                                   const int32_t* m_arr, const int64_t* goff, int marginal,
-                                  int64_t n_single, int m_single, uint32_t* status) {
-  int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= D) return;
+                                  int64_t n_single, int m_single, int32_t* tile_dist0,
+                                  int64_t ntiles, uint32_t* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ntiles && offsets != nullptr) {
+    const int64_t e = i * kTile;
+    int lo = 0, hi = D - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (offsets[mid] <= e)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    tile_dist0[i] = lo;
+  }
+  if (i >= D) return;
+  const int d = (int)i;
   rtf_dist P;
   if (offsets == nullptr) {
     P.elem_off = 0;
@@ -81,7 +99,8 @@ constexpr int kScaleTile = kScaleThreads * kScalePer;
 template <bool SEG>
 __global__ void __launch_bounds__(kScaleThreads)
     scale_kernel(const float* __restrict__ w, int64_t Nw, const rtf_dist* __restrict__ dists,
-                 int Dw, uint32_t* dmax, uint32_t* status) {
+                 int Dw, const int32_t* __restrict__ tile_dist0, uint32_t* dmax,
+                 uint32_t* status) {
   __shared__ uint32_t smax[SEG ? kScaleTile + 1 : 1];
   __shared__ int dfirst_s;
   __shared__ uint32_t red[kScaleThreads / 32];
@@ -122,13 +141,13 @@ __global__ void __launch_bounds__(kScaleThreads)
     return;
   }
   // segmented: the block's elements span distributions dfirst..dlast
-  if (threadIdx.x == 0) dfirst_s = find_dist(dists, 0, Dw - 1, c0);
+  if (threadIdx.x == 0) dfirst_s = tile_dist0[c0 / kTile];
   for (int k = threadIdx.x; k <= kScaleTile; k += kScaleThreads) smax[k] = 0u;
   __syncthreads();
   const int dfirst = dfirst_s;
   if (e0 < c1) {
     int hi = min(Dw - 1, dfirst + kScaleTile);
-    int d = find_dist(dists, dfirst, hi, e0);
+    int d = find_dist(dists, tile_dist0[e0 / kTile], hi, e0);
     int64_t next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
     uint32_t run = 0;
     const int64_t e1 = min(e0 + (int64_t)kScalePer, c1);
@@ -150,7 +169,8 @@ __global__ void __launch_bounds__(kScaleThreads)
   }
   if (bad) raise_status(status, RTF_STATUS_BAD_WEIGHT);
   __syncthreads();
-  const int dlast = (c1 > c0) ? find_dist(dists, dfirst, min(Dw - 1, dfirst + kScaleTile), c1 - 1)
+  const int dlast = (c1 > c0) ? find_dist(dists, tile_dist0[(c1 - 1) / kTile],
+                                          min(Dw - 1, dfirst + kScaleTile), c1 - 1)
                               : dfirst;
   for (int d = dfirst + (int)threadIdx.x; d <= dlast; d += kScaleThreads) {
     uint32_t v = smax[d - dfirst];
@@ -311,7 +331,7 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 
   if (threadIdx.x == 0) {
-    dfirst_s = find_dist(dists, 0, Dw - 1, t0);
+    dfirst_s = ts.dist0[tile];  // written by init_dists_kernel
     meta_s = 0;
   }
   const int wo = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
@@ -392,7 +412,6 @@ __global__ void __launch_bounds__(kScanThreads)
   if (threadIdx.x == 0) {
     ts.sum[tile] = btot.s;
     ts.meta[tile] = meta_s | (btot.f ? 1u : 0u) | (head0 ? 2u : 0u);
-    ts.dist0[tile] = dfirst;
   }
 }
 
@@ -567,6 +586,7 @@ struct ForestArgs {
   uint32_t* gmax;
   int32_t* unres;
   int32_t* unres_count;
+  const int32_t* tile_dist0;  // distribution of each tile's first element (batches)
   uint32_t* status;
 };
 
@@ -674,7 +694,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
   const int lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) {
-    const int df = SEG ? find_dist(a.dists, 0, a.D - 1, t0) : 0;
+    const int df = SEG ? a.tile_dist0[tile] : 0;
     s.dfirst = df;
     s.dprev = (t0 > 0 && SEG) ? (a.dists[df].elem_off == t0 ? df - 1 : df) : df;
     s.nunres = 0;
@@ -1500,7 +1520,7 @@ __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t
       raise_status(a.status, RTF_STATUS_INVARIANT);
       continue;
     }
-    const int d = a.D > 1 ? find_dist(a.dists, 0, a.D - 1, p) : 0;
+    const int d = a.D > 1 ? find_dist(a.dists, a.tile_dist0[p / kTile], a.D - 1, p) : 0;
     const rtf_dist P = a.dists[d];
     const int32_t id = (int32_t)(p - P.elem_off);
     const uint32_t dl = jl >= 0 ? (uint32_t)a.delta[jl] : kDeltaInf;
@@ -1590,16 +1610,19 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   cudaError_t e;
   if ((e = cudaMemsetAsync(base + L.zero_begin, 0, L.zero_end - L.zero_begin, st))) return e;
   if ((e = cudaMemsetAsync(f->status, 0, sizeof(uint32_t), st))) return e;
-  init_dists_kernel<<<(D + 255) / 256, 256, 0, st>>>(f->dists, D, offsets, m_arr, goff, marginal,
-                                                      n_single, m_single, f->status);
+  int32_t* tile_dist0 = reinterpret_cast<int32_t*>(base + L.tile_dist0);
+  const int64_t ntiles_seg = seg ? num_tiles(N) : 0;
+  init_dists_kernel<<<(unsigned)((std::max<int64_t>(D, ntiles_seg) + 255) / 256), 256, 0, st>>>(
+      f->dists, D, offsets, m_arr, goff, marginal, n_single, m_single, tile_dist0, ntiles_seg,
+      f->status);
   const int64_t nscale = (Nw + kScaleTile - 1) / kScaleTile;
   if (marginal || !seg) {
     // one group: a plain block max into dmax[0]
-    scale_kernel<false><<<(unsigned)nscale, kScaleThreads, 0, st>>>(w, Nw, f->dists, Dw, dmax,
-                                                                    f->status);
+    scale_kernel<false><<<(unsigned)nscale, kScaleThreads, 0, st>>>(w, Nw, f->dists, Dw,
+                                                                    tile_dist0, dmax, f->status);
   } else {
-    scale_kernel<true><<<(unsigned)nscale, kScaleThreads, 0, st>>>(w, Nw, f->dists, Dw, dmax,
-                                                                   f->status);
+    scale_kernel<true><<<(unsigned)nscale, kScaleThreads, 0, st>>>(w, Nw, f->dists, Dw,
+                                                                   tile_dist0, dmax, f->status);
   }
   const int64_t tiles_w = num_tiles(Nw);
   TileSums ts;
@@ -1647,6 +1670,7 @@ cudaError_t launch_build(const float* w, int64_t N, int64_t Nw, int D, int margi
   fa.gmax = reinterpret_cast<uint32_t*>(base + L.gmax);
   fa.unres = reinterpret_cast<int32_t*>(base + L.unres);
   fa.unres_count = reinterpret_cast<int32_t*>(base + L.unres_count);
+  fa.tile_dist0 = tile_dist0;
   fa.status = f->status;
   if (seg) {
     const size_t fsmem = sizeof(ForestShared<true>);
