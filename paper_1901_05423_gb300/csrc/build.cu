@@ -151,14 +151,33 @@ __global__ void __launch_bounds__(kScaleThreads)
     int64_t next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
     uint32_t run = 0;
     const int64_t e1 = min(e0 + (int64_t)kScalePer, c1);
-    for (int64_t e = e0; e < e1; ++e) {
+    // the thread's weights first, as 16-byte vectors where aligned
+    float wv[kScalePer];
+    if (e0 + kScalePer <= c1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+      const float4* p = reinterpret_cast<const float4*>(w + e0);
+#pragma unroll
+      for (int k = 0; k < kScalePer / 4; ++k) {
+        const float4 v = ld_weights4(p + k);
+        wv[4 * k] = v.x;
+        wv[4 * k + 1] = v.y;
+        wv[4 * k + 2] = v.z;
+        wv[4 * k + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScalePer; ++k) wv[k] = e0 + k < c1 ? w[e0 + k] : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < kScalePer; ++k) {
+      const int64_t e = e0 + k;
+      if (e >= e1) break;
       if (e >= next) {
         if (run) atomicMax(&smax[d - dfirst], run);
         run = 0;
         ++d;
         next = d + 1 < Dw ? dists[d + 1].elem_off : INT64_MAX;
       }
-      uint32_t b = weight_bits(w[e]);
+      uint32_t b = weight_bits(wv[k]);
       if (weight_bad(b)) {
         bad = 1;
       } else {
@@ -415,8 +434,7 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
-constexpr int kTileScanPer = 8;
-constexpr int kTileScanChunk = kScanThreads * kTileScanPer;  // tiles per scan block
+constexpr int kTileScanPer = kTileScanChunk / kScanThreads;
 
 // Decoupled-lookback segmented scan of the tile sums (a distribution's head
 // restarts the sum): the prefix of every tile's first piece, and the totals of

@@ -20,6 +20,7 @@ constexpr int kTile = 2048;           // weights per scan / forest tile
 constexpr int kScanThreads = 256;     // scan kernel: 8 weights per thread
 constexpr int kForestThreads = 512;   // forest kernel: 4 leaves per thread
 constexpr int kMaxThreads = 512;
+constexpr int kTileScanChunk = 512;   // tile sums per block of the segmented tile scan
 constexpr uint32_t kDeltaInf = 64;    // distance across a cell / distribution boundary
 constexpr long long kSpinLimit = 1ll << 22;   // bounded waits
 // Nodes of a forest tile whose range reaches past the tile (their parent needs
@@ -47,7 +48,7 @@ struct WsLayout {
   size_t zero_begin;   // start of the region zero-filled by every build
   size_t counters;     // u32 tickets / done counters
   size_t dmax;         // u32 [D] max float bits per distribution / group
-  size_t scan_status;  // u64 [num_tiles / 2048 + 1] status of the tile-sum scan blocks
+  size_t scan_status;  // u64 [num_tiles / kTileScanChunk + 1] status of the tile-sum scan blocks
   size_t gmax;         // u32 [num_tiles / kTileGroup] largest distance per group of tiles
   size_t zero_end;
   size_t fills;        // int4 [fill_cap] runs of empty cells: first cell, count, leaf, dist
@@ -80,7 +81,8 @@ __host__ __device__ inline WsLayout ws_layout(int64_t N, int32_t D, int64_t G) {
   L.zero_begin = o;
   L.counters = o; o += 256;
   L.dmax = o; o = align256(o + sizeof(uint32_t) * (size_t)D);
-  L.scan_status = o; o = align256(o + sizeof(uint64_t) * (size_t)(num_tiles(N) / 2048 + 1));
+  L.scan_status = o;
+  o = align256(o + sizeof(uint64_t) * (size_t)(num_tiles(N) / kTileScanChunk + 1));
   L.gmax = o;
   o = align256(o + sizeof(uint32_t) * (size_t)((num_tiles(N) + kTileGroup - 1) / kTileGroup));
   L.zero_end = o;
