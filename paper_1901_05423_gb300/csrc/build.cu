@@ -701,12 +701,27 @@ __device__ __forceinline__ void compare_planes(const uint32_t* pl, uint32_t v, u
 #define RTF_FOREST_MINB 3
 #endif
 
+struct LeanShared;
+template <bool ONE>
+__device__ __forceinline__ void lean_tile(const ForestArgs& a, LeanShared& s, const rtf_dist& P,
+                                          int dd);
+
 template <bool SEG>
 __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel(ForestArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForestShared<SEG>& s = *reinterpret_cast<ForestShared<SEG>*>(smem_raw);
   const int64_t tile = blockIdx.x;
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
+  if (SEG) {
+    // a tile inside one distribution (most tiles of a batch of large
+    // distributions) takes the one-distribution path
+    const int df = a.tile_dist0[tile];
+    const rtf_dist& P = a.dists[df];
+    if ((P.flags & kDistMarginal) == 0 && P.elem_off <= t0 && t1 <= P.elem_off + P.n) {
+      lean_tile<false>(a, *reinterpret_cast<LeanShared*>(smem_raw), P, df);
+      return;
+    }
+  }
   const int tn = (int)(t1 - t0);
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -1109,6 +1124,9 @@ struct LeanShared {
   int32_t unres[kUnresCap];
 };
 
+static_assert(sizeof(LeanShared) <= sizeof(ForestShared<true>),
+              "the batched forest kernel's shared memory holds the one-distribution tile");
+
 // 64-bit warp shuffles
 __device__ __forceinline__ uint64_t shfl_up64(uint64_t x, int d) {
   return __shfl_up_sync(0xffffffffu, (unsigned long long)x, d);
@@ -1144,16 +1162,21 @@ __device__ __forceinline__ int lean_walk(const LeanShared& s, int from, int nchu
   return -1;
 }
 
-__global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_kernel(ForestArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  LeanShared& s = *reinterpret_cast<LeanShared*>(smem_raw);
+// One tile inside one distribution P (index dd, not the marginal of a 2-D
+// map).  ONE: the build of a single distribution (P = dists[0] over the whole
+// array; the tile sums came in ranges); otherwise a tile of a batch, whose
+// prefix within P is in tile_prefix.
+template <bool ONE>
+__device__ __forceinline__ void lean_tile(const ForestArgs& a, LeanShared& s, const rtf_dist& P,
+                                          int dd) {
   uint64_t* const sC = s.Cbuf + 1;  // sC[p]: C of tile-local leaf p - 1
   uint8_t* const sd = s.dbuf + 3;   // sd[p]: distance at position p
   const int64_t tile = blockIdx.x;
   const int64_t t0 = tile * kTile, t1 = min(t0 + (int64_t)kTile, a.N);
   const int tn = (int)(t1 - t0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int S = a.dists[0].scale;
+  const int S = P.scale;
+  const int64_t eoff = ONE ? 0 : P.elem_off, eend = ONE ? a.N : P.elem_off + P.n;
   const int lbase = 128 * warp + lane;  // lane-strided: tile-local leaf of k = 0
   const int lb = 4 * tid;               // blocked: the thread's leaves lb .. lb + 3
 
@@ -1175,7 +1198,9 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     s.ncells = 0;
     s.tmax = 0;
     // the tile's prefix within its range of the tile sums plus the range's prefix
-    s.prefix = t0 > 0 ? a.tile_prefix[tile] + a.range_prefix[tile / a.range_meta[0]] : 0ull;
+    s.prefix = !ONE ? a.tile_prefix[tile]
+               : t0 > 0 ? a.tile_prefix[tile] + a.range_prefix[tile / a.range_meta[0]]
+                        : 0ull;
   }
   uint64_t C[4];
   uint64_t tot = 0;
@@ -1198,8 +1223,8 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, (unsigned long long)off, o);
   const uint64_t pre = s.prefix + off + (incl - tot);
-  const uint64_t T = a.dists[0].total, R = a.dists[0].recip;
-  const int z = a.dists[0].shift, m = a.dists[0].m;
+  const uint64_t T = P.total, R = P.recip;
+  const int z = P.shift, m = P.m;
   uint64_t K[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -1231,7 +1256,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     sC[tn + 1] = Ct1;
     s.Kfirst[kForestThreads / 32] = key_of(Ct1, T, R, z);
     uint64_t Cp = 0;
-    if (t0 > 0) {
+    if (t0 > eoff) {
       const uint32_t b = weight_bits(a.w[t0 - 1]);
       Cp = s.prefix - (weight_bad(b) ? 0ull : quantize_bits(b, S));
     }
@@ -1251,7 +1276,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
       const int l = lb + k;
       const uint64_t Kn = k < 3 ? K[k < 3 ? k + 1 : k] : K4;
       uint32_t dlt = kDeltaInf;
-      if (l < tn && t0 + l + 1 < a.N && cell_of(K[k], m) == cell_of(Kn, m))
+      if (l < tn && t0 + l + 1 < eend && cell_of(K[k], m) == cell_of(Kn, m))
         dlt = key_distance(K[k], Kn);
       if (l < tn) {
         packed |= dlt << (8 * k);
@@ -1308,7 +1333,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
   }
   if (tid == 0) {
     uint32_t d0 = kDeltaInf;
-    if (t0 > 0 && cell_of(s.Kprev, m) == cell_of(K[0], m)) d0 = key_distance(s.Kprev, K[0]);
+    if (t0 > eoff && cell_of(s.Kprev, m) == cell_of(K[0], m)) d0 = key_distance(s.Kprev, K[0]);
     sd[0] = (uint8_t)d0;
   }
   const int nchunks = (tn + 31) >> 5;
@@ -1319,7 +1344,6 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
   }
 
   // ---- links -----------------------------------------------------------------
-  const rtf_dist& P = a.dists[0];
   // node at position 0 (delta_{t0-1}): its left bound lies outside the tile
   if (tid == 0) {
     const uint32_t v = sd[0];
@@ -1327,9 +1351,9 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
       const int pr = lean_walk(s, 0, nchunks, v, +1);
       if (pr >= 0 && sd[pr] == v) {
         if (pr < tn)
-          s.child[pr][0] = (int32_t)t0;
+          s.child[pr][0] = (int32_t)(t0 - eoff);
         else
-          a.nodes[t1].child[0] = (int32_t)t0;
+          a.nodes[t1].child[0] = (int32_t)(t0 - eoff);
       } else {
         const int slot = atomicAdd(&s.nunres, 1);
         if (slot < kUnresCap) s.unres[slot] = 0;
@@ -1339,7 +1363,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
   for (int k = 0; k < 4; ++k) {
     const int l = lbase + 32 * k;
     if (l >= tn) break;
-    const int32_t id = (int32_t)(t0 + l);
+    const int32_t id = (int32_t)(t0 + l - eoff);
     // leaf l, between positions l and l + 1: child 0 of node l + 1 when the
     // left distance is larger, else child 1 of node l (for a one-leaf cell,
     // node l is the cell's root and the leaf its whole tree)
@@ -1374,7 +1398,7 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
       const uint32_t msk = lane < 31 ? (ge & ~((2u << lane) - 1u)) : 0u;
       pr = msk ? 32 * c + __ffs(msk) : lean_walk(s, c + 1, nchunks, v, +1);
     }
-    const int32_t nid = (int32_t)(t0 + p);
+    const int32_t nid = (int32_t)(t0 + p - eoff);
     if (pr < 0 || (pl < 0 && sd[pr] > v)) {
       const int slot = atomicAdd(&s.nunres, 1);
       if (slot < kUnresCap) s.unres[slot] = p;
@@ -1402,12 +1426,12 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     const uint32_t r = s.cell_range[i];
     const int lo = (int)(r & 0xFFFFu), hi = (int)(r >> 16);
     const int64_t glo = t0 + lo;
-    const uint64_t Clm1 = glo > 0 ? sC[lo] : 0ull;
-    const uint64_t Chp1 = t0 + hi + 1 == a.N ? T : sC[hi + 2];
+    const uint64_t Clm1 = glo > eoff ? sC[lo] : 0ull;
+    const uint64_t Chp1 = t0 + hi + 1 == eend ? T : sC[hi + 2];
     const uint64_t Clo = sC[lo + 1], Chi = sC[hi + 1];
-    const uint64_t Knext = t0 + hi + 1 == a.N ? (1ull << 32) : key_of(Chp1, T, R, z);
+    const uint64_t Knext = t0 + hi + 1 == eend ? (1ull << 32) : key_of(Chp1, T, R, z);
     // the top of the cell's tree is its root's child 1 (written in the links)
-    finish_cell(a, P, 0, glo, t0 + hi, key_of(Clo, T, R, z), key_of(Chi, T, R, z), Clm1, Clo, Chi,
+    finish_cell(a, P, dd, glo, t0 + hi, key_of(Clo, T, R, z), key_of(Chi, T, R, z), Clm1, Clo, Chi,
                 Chp1, s.child[lo][1], Knext);
   }
 
@@ -1437,6 +1461,11 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
     a.unres_count[tile] = min(nu, kUnresCap);
   }
   if (tid < min(nu, kUnresCap)) a.unres[tile * kUnresCap + tid] = (int32_t)(t0 + s.unres[tid]);
+}
+
+__global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_kernel(ForestArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  lean_tile<true>(a, *reinterpret_cast<LeanShared*>(smem_raw), a.dists[0], 0);
 }
 
 // Nearest split j' < j with delta_{j'} > v, or -1 (the array start counts as
