@@ -36,6 +36,11 @@ constexpr int kSmemGuideMaxBits = 10;  // 32 KB of guide records in shared memor
 // Samples per thread of the sampler with a distribution id per sample (their
 // descents in lockstep).  GB300, 16384 ragged distributions, 2^27 samples:
 // 5.83 ms with 4, 6.24 ms with 2.
+// Minimum resident blocks per SM asked of the register allocator for the 2-D
+// sampler (0: no bound).
+#ifndef RTF_2D_MINB
+#define RTF_2D_MINB 0
+#endif
 #ifndef RTF_TAGGED_K
 #define RTF_TAGGED_K 4
 #endif
@@ -805,7 +810,7 @@ __global__ void __launch_bounds__(kSampleThreads)
 // 2-D: the row through the marginal (last distribution) with u1, the column
 // through that row's distribution with u2 (Sec. 5).
 template <bool BS>
-__global__ void __launch_bounds__(kSampleThreads)
+__global__ void __launch_bounds__(kSampleThreads, RTF_2D_MINB)
     sample_2d_kernel(const rtf_node* __restrict__ nodes, const rtf_guide_rec* __restrict__ guide,
                      const rtf_dist* __restrict__ dists, int D, const uint2* __restrict__ u,
                      int64_t count, int2* __restrict__ idx_out, float2* __restrict__ pos_out) {
