@@ -1468,101 +1468,160 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
   lean_tile<true>(a, *reinterpret_cast<LeanShared*>(smem_raw), a.dists[0], 0);
 }
 
-// Nearest split j' < j with delta_{j'} > v, or -1 (the array start counts as
-// infinitely far), searched by one warp: splits 32 at a time inside j's tile,
-// then tiles by their largest distance inside j's group of tiles, then groups.
-__device__ int64_t find_left(const ForestArgs& a, int64_t j, uint32_t v) {
-  const int lane = threadIdx.x & 31;
-  const unsigned full = 0xffffffffu;
-  auto scan_splits = [&](int64_t hi, int64_t lo) -> int64_t {  // positions hi down to lo
-    for (int64_t pos = hi; pos >= lo; pos -= 32) {
-      const int64_t x = pos - lane;
-      const unsigned m = __ballot_sync(full, x >= lo && a.delta[x] > v);
-      if (m) return pos - (__ffs(m) - 1);
-    }
-    return -1;
-  };
-  auto scan_tiles = [&](int64_t hi, int64_t lo) -> int64_t {
-    for (int64_t t = hi; t >= lo; t -= 32) {
-      const int64_t x = t - lane;
-      const unsigned m = __ballot_sync(full, x >= lo && a.tmax[x] > v);
-      if (m) return t - (__ffs(m) - 1);
-    }
-    return -1;
-  };
-  const int64_t T = j / kTile;
-  int64_t r = scan_splits(j - 1, T * kTile);
-  if (r >= 0) return r;
-  const int64_t G = T / kTileGroup;
-  int64_t t = scan_tiles(T - 1, G * kTileGroup);
-  if (t < 0) {
-    int64_t g = -1;
-    for (int64_t gg = G - 1; gg >= 0 && g < 0; gg -= 32) {
-      const int64_t x = gg - lane;
-      const unsigned m = __ballot_sync(full, x >= 0 && a.gmax[x] > v);
-      if (m) g = gg - (__ffs(m) - 1);
-    }
-    if (g < 0) return -1;
-    t = scan_tiles(g * kTileGroup + kTileGroup - 1, g * kTileGroup);
-  }
-  return scan_splits(min(t * kTile + kTile, a.N) - 1, t * kTile);
+// Byte k (0..15) of a 16-byte word held as two 64-bit halves.
+__device__ __forceinline__ uint32_t byte_of(uint64_t w0, uint64_t w1, int k) {
+  return (uint32_t)((k < 8 ? w0 >> (8 * k) : w1 >> (8 * (k - 8))) & 0xFFu);
 }
 
-// Nearest split j' > j with delta_{j'} >= v (the last split, delta_{N-1}, is
-// a boundary and ends every search).
-__device__ int64_t find_right(const ForestArgs& a, int64_t j, uint32_t v, int64_t ntiles) {
-  const int lane = threadIdx.x & 31;
-  const unsigned full = 0xffffffffu;
-  auto scan_splits = [&](int64_t lo, int64_t hi) -> int64_t {  // positions lo up to hi
-    for (int64_t pos = lo; pos <= hi; pos += 32) {
-      const int64_t x = pos + lane;
-      const unsigned m = __ballot_sync(full, x <= hi && a.delta[x] >= v);
-      if (m) return pos + (__ffs(m) - 1);
+// Searches of one thread over a byte array (the distances per split, or the
+// largest distance per tile), read as aligned 16-byte words: the nearest
+// position in [lo, hi] to hi (scan_down) or to lo (scan_up) whose byte exceeds
+// v (or is at least v when GE), or -1.  Both arrays are allocated in whole
+// 256-byte units, so a word that straddles hi stays inside the allocation.
+template <bool GE>
+__device__ int64_t scan_down(const uint8_t* b, int64_t hi, int64_t lo, uint32_t v) {
+  int64_t pos = hi;
+  while (pos >= lo) {
+    const int64_t w = pos & ~int64_t(15);
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(b + w));
+    const uint64_t w0 = x.x | ((uint64_t)x.y << 32), w1 = x.z | ((uint64_t)x.w << 32);
+    const int64_t stop = w > lo ? w : lo;
+    for (int64_t q = pos; q >= stop; --q) {
+      const uint32_t by = byte_of(w0, w1, (int)(q - w));
+      if (GE ? by >= v : by > v) return q;
     }
-    return -1;
-  };
-  auto scan_tiles = [&](int64_t lo, int64_t hi) -> int64_t {
-    for (int64_t t = lo; t <= hi; t += 32) {
-      const int64_t x = t + lane;
-      const unsigned m = __ballot_sync(full, x <= hi && a.tmax[x] >= v);
-      if (m) return t + (__ffs(m) - 1);
-    }
-    return -1;
-  };
-  const int64_t T = j / kTile;
-  int64_t r = scan_splits(j + 1, min(T * kTile + kTile, a.N) - 1);
-  if (r >= 0) return r;
-  const int64_t G = T / kTileGroup;
-  const int64_t ngroups = (ntiles + kTileGroup - 1) / kTileGroup;
-  int64_t t = scan_tiles(T + 1, min(G * kTileGroup + kTileGroup, ntiles) - 1);
-  if (t < 0) {
-    int64_t g = -1;
-    for (int64_t gg = G + 1; gg < ngroups && g < 0; gg += 32) {
-      const int64_t x = gg + lane;
-      const unsigned m = __ballot_sync(full, x < ngroups && a.gmax[x] >= v);
-      if (m) g = gg + (__ffs(m) - 1);
-    }
-    if (g < 0) return -1;  // cannot happen: delta_{N-1} is a boundary
-    t = scan_tiles(g * kTileGroup, min(g * kTileGroup + kTileGroup, ntiles) - 1);
+    pos = w - 1;
   }
-  return scan_splits(t * kTile, min(t * kTile + kTile, a.N) - 1);
+  return -1;
 }
 
-// The nodes whose range crosses a tile edge: one warp per tile, one node at a
-// time; the two bounding splits come from the global distances, then the link
+template <bool GE>
+__device__ int64_t scan_up(const uint8_t* b, int64_t lo, int64_t hi, uint32_t v) {
+  int64_t pos = lo;
+  while (pos <= hi) {
+    const int64_t w = pos & ~int64_t(15);
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(b + w));
+    const uint64_t w0 = x.x | ((uint64_t)x.y << 32), w1 = x.z | ((uint64_t)x.w << 32);
+    const int64_t stop = w + 15 < hi ? w + 15 : hi;
+    for (int64_t q = pos; q <= stop; ++q) {
+      const uint32_t by = byte_of(w0, w1, (int)(q - w));
+      if (GE ? by >= v : by > v) return q;
+    }
+    pos = w + 16;
+  }
+  return -1;
+}
+
+// The searches of the merge pass, one node per thread: the splits of j's
+// tile, then the tiles of its group of kTileGroup tiles by their largest
+// distance; a search that leaves the group returns -1 with *out set, and the
+// warp then finds the group (group_left / group_right, 32 groups per step).
+// Left: nearest split j' < j with delta_{j'} > v (the array start counts as
+// infinitely far).  Right: nearest j' > j with delta_{j'} >= v (the last
+// split, delta_{N-1}, is a boundary and ends every search).
+__device__ int64_t left_in_group(const ForestArgs& a, int64_t j, uint32_t v, bool* out) {
+  *out = false;
+  const int64_t T = j / kTile;
+  const int64_t r = scan_down<false>(a.delta, j - 1, T * kTile, v);
+  if (r >= 0) return r;
+  const int64_t G = T / kTileGroup;
+  const int64_t t = scan_down<false>(a.tmax, T - 1, G * kTileGroup, v);
+  if (t < 0) {
+    *out = G > 0;
+    return -1;
+  }
+  return scan_down<false>(a.delta, min(t * kTile + kTile, a.N) - 1, t * kTile, v);
+}
+
+__device__ int64_t right_in_group(const ForestArgs& a, int64_t j, uint32_t v, int64_t ntiles,
+                                  bool* out) {
+  *out = false;
+  const int64_t T = j / kTile;
+  const int64_t r = scan_up<true>(a.delta, j + 1, min(T * kTile + kTile, a.N) - 1, v);
+  if (r >= 0) return r;
+  const int64_t G = T / kTileGroup;
+  const int64_t t = scan_up<true>(a.tmax, T + 1, min(G * kTileGroup + kTileGroup, ntiles) - 1, v);
+  if (t < 0) {
+    *out = true;
+    return -1;
+  }
+  return scan_up<true>(a.delta, t * kTile, min(t * kTile + kTile, a.N) - 1, v);
+}
+
+// The nearest split in group g (known to hold one): its tiles by their
+// largest distance, then that tile's splits.
+__device__ int64_t left_in(const ForestArgs& a, int64_t g, uint32_t v) {
+  const int64_t t = scan_down<false>(a.tmax, g * kTileGroup + kTileGroup - 1, g * kTileGroup, v);
+  return t < 0 ? -1 : scan_down<false>(a.delta, min(t * kTile + kTile, a.N) - 1, t * kTile, v);
+}
+
+__device__ int64_t right_in(const ForestArgs& a, int64_t g, uint32_t v, int64_t ntiles) {
+  const int64_t t =
+      scan_up<true>(a.tmax, g * kTileGroup, min(g * kTileGroup + kTileGroup, ntiles) - 1, v);
+  return t < 0 ? -1 : scan_up<true>(a.delta, t * kTile, min(t * kTile + kTile, a.N) - 1, v);
+}
+
+// Warp-wide: nearest group g < G with gmax > v (left) or g > G with gmax >= v
+// (right), 32 groups per step; -1 when none.
+__device__ int64_t group_left(const ForestArgs& a, int64_t G, uint32_t v) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t gg = G - 1; gg >= 0; gg -= 32) {
+    const int64_t x = gg - lane;
+    const unsigned m = __ballot_sync(0xffffffffu, x >= 0 && a.gmax[x] > v);
+    if (m) return gg - (__ffs(m) - 1);
+  }
+  return -1;
+}
+
+__device__ int64_t group_right(const ForestArgs& a, int64_t G, uint32_t v, int64_t ngroups) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t gg = G + 1; gg < ngroups; gg += 32) {
+    const int64_t x = gg + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, x < ngroups && a.gmax[x] >= v);
+    if (m) return gg + (__ffs(m) - 1);
+  }
+  return -1;
+}
+
+// The nodes whose range crosses a tile edge: one warp per tile, one node per
+// lane; the two bounding splits come from the global distances, then the link
 // (or the cell's root and guide entry) is written as inside a tile.
 __global__ void __launch_bounds__(128) forest_merge_kernel(ForestArgs a, int64_t ntiles) {
   const int64_t tile = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (tile >= ntiles) return;
+  if (tile >= ntiles) return;  // whole warps leave together
   const int lane = threadIdx.x & 31;
   const int cnt = a.unres_count[tile];
-  for (int k = 0; k < cnt; ++k) {
-    const int64_t p = a.unres[tile * kUnresCap + k];  // node p: the split between p-1 and p
-    const int64_t j = p - 1;
-    const uint32_t v = a.delta[j];
-    const int64_t jl = find_left(a, j, v);
-    const int64_t jr = find_right(a, j, v, ntiles);
-    if (lane != 0) continue;
+  const int64_t ngroups = (ntiles + kTileGroup - 1) / kTileGroup;
+  for (int base = 0; base < cnt; base += 32) {
+    const int k = base + lane;
+    const bool act = k < cnt;
+    int64_t p = 0, j = 0, jl = -1, jr = -1;
+    uint32_t v = 0;
+    bool outl = false, outr = false;
+    if (act) {
+      p = a.unres[tile * kUnresCap + k];  // node p: the split between p-1 and p
+      j = p - 1;
+      v = a.delta[j];
+      jl = left_in_group(a, j, v, &outl);
+      jr = right_in_group(a, j, v, ntiles, &outr);
+    }
+    // searches that left their group of tiles: the groups, warp-wide, one
+    // lane's search at a time
+    for (unsigned m = __ballot_sync(0xffffffffu, outl); m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const int64_t G = __shfl_sync(0xffffffffu, (long long)(j / kTile / kTileGroup), src);
+      const uint32_t vs = __shfl_sync(0xffffffffu, v, src);
+      const int64_t g = group_left(a, G, vs);
+      if (lane == src) jl = g < 0 ? -1 : left_in(a, g, v);
+    }
+    for (unsigned m = __ballot_sync(0xffffffffu, outr); m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const int64_t G = __shfl_sync(0xffffffffu, (long long)(j / kTile / kTileGroup), src);
+      const uint32_t vs = __shfl_sync(0xffffffffu, v, src);
+      const int64_t g = group_right(a, G, vs, ngroups);
+      if (lane == src) jr = g < 0 ? -1 : right_in(a, g, v, ntiles);
+    }
+    if (!act) continue;
     if (jr < 0) {
       raise_status(a.status, RTF_STATUS_INVARIANT);
       continue;

@@ -274,6 +274,27 @@ def test_full_size_structure_bit_exact(big):
     check_structure(f, ref)
 
 
+@pytest.mark.parametrize("m", [0, 2, 5])
+def test_cells_spanning_groups_of_tiles(m):
+    """Cells of 2^16 to 2^22 leaves span up to 32 groups of 64 tiles: the merge
+    pass's searches leave their group (the warp-wide group search) for the
+    tops of those cells, on both sides; the structure bit for bit.  A batch of
+    the same weights cut into two distributions takes the segmented path."""
+    n = (1 << 22) + 4097
+    w = W.lognormal_weights(n, seed=40 + m, sigma=2.0)
+    f = api.rtf_build(to_dev(w), m)
+    torch.cuda.synchronize()
+    f.check_status()
+    check_structure(f, orc.build(w, 1 << m))
+    cut = (1 << 21) + 1000
+    fb = api.rtf_build_batched(to_dev(w), [cut, n - cut], [m, m])
+    torch.cuda.synchronize()
+    fb.check_status()
+    host = host_structure(fb)
+    check_structure(fb, orc.build(w[:cut], 1 << m), host=host)
+    check_structure(fb, orc.build(w[cut:], 1 << m), elem_off=cut, guide_off=1 << m, host=host)
+
+
 def test_full_size_samples(big):
     """Both sample sets at full size through the same launch configuration as
     the benchmark; the oracle checks every 64th sample of each."""
