@@ -1468,46 +1468,58 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_lean_k
   lean_tile<true>(a, *reinterpret_cast<LeanShared*>(smem_raw), a.dists[0], 0);
 }
 
-// Byte k (0..15) of a 16-byte word held as two 64-bit halves.
-__device__ __forceinline__ uint32_t byte_of(uint64_t w0, uint64_t w1, int k) {
-  return (uint32_t)((k < 8 ? w0 >> (8 * k) : w1 >> (8 * (k - 8))) & 0xFFu);
+// Byte lanes first..last (0..3) of a 32-bit word.
+__device__ __forceinline__ uint32_t byte_range(int first, int last) {
+  return (0xFFFFFFFFu << (8 * first)) & (0xFFFFFFFFu >> (8 * (3 - last)));
+}
+
+// Bytes of a word that exceed v (or are at least v when GE), as 0xFF per byte;
+// vv holds v in all four bytes.
+template <bool GE>
+__device__ __forceinline__ uint32_t bytes_above(uint32_t x, uint32_t vv) {
+  return GE ? __vcmpgeu4(x, vv) : __vcmpgtu4(x, vv);
 }
 
 // Searches of one thread over a byte array (the distances per split, or the
-// largest distance per tile), read as aligned 16-byte words: the nearest
-// position in [lo, hi] to hi (scan_down) or to lo (scan_up) whose byte exceeds
-// v (or is at least v when GE), or -1.  Both arrays are allocated in whole
-// 256-byte units, so a word that straddles hi stays inside the allocation.
+// largest distance per tile), read as aligned 16-byte words and compared four
+// bytes at a time: the nearest position in [lo, hi] to hi (scan_down) or to
+// lo (scan_up) whose byte exceeds v (or is at least v when GE), or -1.  Both
+// arrays are allocated in whole 256-byte units, so a word that straddles hi
+// stays inside the allocation.  v < 256.
 template <bool GE>
 __device__ int64_t scan_down(const uint8_t* b, int64_t hi, int64_t lo, uint32_t v) {
-  int64_t pos = hi;
-  while (pos >= lo) {
-    const int64_t w = pos & ~int64_t(15);
+  const uint32_t vv = v * 0x01010101u;
+  for (int64_t w = hi & ~int64_t(15); w + 15 >= lo && w >= 0; w -= 16) {
     const uint4 x = __ldg(reinterpret_cast<const uint4*>(b + w));
-    const uint64_t w0 = x.x | ((uint64_t)x.y << 32), w1 = x.z | ((uint64_t)x.w << 32);
-    const int64_t stop = w > lo ? w : lo;
-    for (int64_t q = pos; q >= stop; --q) {
-      const uint32_t by = byte_of(w0, w1, (int)(q - w));
-      if (GE ? by >= v : by > v) return q;
+    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      const int64_t base = w + 4 * i;
+      if (base > hi || base + 3 < lo) continue;
+      const int first = base < lo ? (int)(lo - base) : 0;
+      const int last = base + 3 > hi ? (int)(hi - base) : 3;
+      const uint32_t m = bytes_above<GE>(xs[i], vv) & byte_range(first, last);
+      if (m) return base + (31 - __clz(m)) / 8;
     }
-    pos = w - 1;
   }
   return -1;
 }
 
 template <bool GE>
 __device__ int64_t scan_up(const uint8_t* b, int64_t lo, int64_t hi, uint32_t v) {
-  int64_t pos = lo;
-  while (pos <= hi) {
-    const int64_t w = pos & ~int64_t(15);
+  const uint32_t vv = v * 0x01010101u;
+  for (int64_t w = lo & ~int64_t(15); w <= hi; w += 16) {
     const uint4 x = __ldg(reinterpret_cast<const uint4*>(b + w));
-    const uint64_t w0 = x.x | ((uint64_t)x.y << 32), w1 = x.z | ((uint64_t)x.w << 32);
-    const int64_t stop = w + 15 < hi ? w + 15 : hi;
-    for (int64_t q = pos; q <= stop; ++q) {
-      const uint32_t by = byte_of(w0, w1, (int)(q - w));
-      if (GE ? by >= v : by > v) return q;
+    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t base = w + 4 * i;
+      if (base > hi || base + 3 < lo) continue;
+      const int first = base < lo ? (int)(lo - base) : 0;
+      const int last = base + 3 > hi ? (int)(hi - base) : 3;
+      const uint32_t m = bytes_above<GE>(xs[i], vv) & byte_range(first, last);
+      if (m) return base + (__ffs(m) - 1) / 8;
     }
-    pos = w + 16;
   }
   return -1;
 }
