@@ -373,46 +373,74 @@ __global__ void __launch_bounds__(kBwThreads)
     bool marg = (P.flags & kDistMarginal) != 0;
     float p2 = pow2_neg(P.scale);
     dflt sac = df_zero(), sx = df_zero();
-    uint64_t cnext = nodes[e0].cdf;
-    // C_e as a double-float, carried along the run (C_{e+1} = C_e + q_e; a
-    // row's q_e is one exact float): one 64-bit conversion per run
-    dflt Cd = df_from_u64(cnext);
-    const int64_t e1 = min(e0 + (int64_t)kBwPer, t1);
-    for (int64_t e = e0; e < e1; ++e) {
-      if (e >= end) {
-        if (dlast != dfirst) atomicAdd(G + d, df_to_double(df_add(sac, df_mul(K, sx))));
-        sac = df_zero();
-        sx = df_zero();
-        ++d;
-        P = dists[d];
-        end = P.elem_off + P.n;
-        invT = df_from_double(1.0 / (double)P.total);
-        K = df_from_double(ldexp(1.0, P.scale) / (double)P.total);
-        marg = (P.flags & kDistMarginal) != 0;
-        p2 = pow2_neg(P.scale);
-        Cd = df_zero();  // a new distribution starts at C = 0
+    if (dlast == dfirst && e0 + kBwPer <= t1 && !marg) {
+      // the usual case, a whole run inside one distribution of float
+      // weights: every load of the run issued first (the bound C_{e0+kBwPer}
+      // is T past the distribution's end)
+      uint64_t c[kBwPer + 1];
+#pragma unroll
+      for (int k = 0; k < kBwPer; ++k) c[k] = nodes[e0 + k].cdf;
+      c[kBwPer] = e0 + kBwPer < end ? nodes[e0 + kBwPer].cdf : P.total;
+      float2 ax[kBwPer];
+#pragma unroll
+      for (int k = 0; k < kBwPer; ++k) ax[k] = acc[e0 + k];
+      dflt Cd = df_from_u64(c[0]);
+#pragma unroll
+      for (int k = 0; k < kBwPer; ++k) {
+        const uint64_t q = c[k + 1] - c[k];
+        const float qf = float_of_q24(q);
+        if ((ax[k].x != 0.0f || ax[k].y != 0.0f) && q != 0) {
+          const float wq = p2 != 0.0f ? qf * p2 : scalbnf(qf, -P.scale);
+          dflt av, bv;
+          bin_terms(ax[k], wq, 0.0f, &av, &bv);
+          sac = df_add(sac, df_mul(av, df_mul(Cd, invT)));
+          sx = df_add(sx, dflt{ax[k].y, 0.0f});
+        }
+        Cd = df_add(Cd, dflt{qf, 0.0f});
       }
-      const uint64_t c = cnext;
-      cnext = (e + 1 < N) ? nodes[e + 1].cdf : 0ull;
-      const uint64_t cup = (e + 1 < end) ? cnext : P.total;
-      const float2 ax = acc[e];
-      const uint64_t q = cup - c;
-      // a row weight's q has at most 24 significant bits: q and w' are exact floats
-      const dflt qd = marg ? df_from_u64(q) : dflt{float_of_q24(q), 0.0f};
-      if ((ax.x != 0.0f || ax.y != 0.0f) && q != 0) {
-        dflt wq;
-        if (marg)
-          wq = qweight_df(q, P.scale);
-        else
-          wq = dflt{p2 != 0.0f ? qd.hi * p2 : scalbnf(qd.hi, -P.scale), 0.0f};
-        dflt av, bv;
-        bin_terms(ax, wq.hi, wq.lo, &av, &bv);
-        sac = df_add(sac, df_mul(av, df_mul(Cd, invT)));
-        sx = df_add(sx, dflt{ax.y, 0.0f});
+      contrib = df_add(sac, df_mul(K, sx));
+    } else {
+      uint64_t cnext = nodes[e0].cdf;
+      // C_e as a double-float, carried along the run (C_{e+1} = C_e + q_e; a
+      // row's q_e is one exact float): one 64-bit conversion per run
+      dflt Cd = df_from_u64(cnext);
+      const int64_t e1 = min(e0 + (int64_t)kBwPer, t1);
+      for (int64_t e = e0; e < e1; ++e) {
+        if (e >= end) {
+          if (dlast != dfirst) atomicAdd(G + d, df_to_double(df_add(sac, df_mul(K, sx))));
+          sac = df_zero();
+          sx = df_zero();
+          ++d;
+          P = dists[d];
+          end = P.elem_off + P.n;
+          invT = df_from_double(1.0 / (double)P.total);
+          K = df_from_double(ldexp(1.0, P.scale) / (double)P.total);
+          marg = (P.flags & kDistMarginal) != 0;
+          p2 = pow2_neg(P.scale);
+          Cd = df_zero();  // a new distribution starts at C = 0
+        }
+        const uint64_t c = cnext;
+        cnext = (e + 1 < N) ? nodes[e + 1].cdf : 0ull;
+        const uint64_t cup = (e + 1 < end) ? cnext : P.total;
+        const float2 ax = acc[e];
+        const uint64_t q = cup - c;
+        // a row weight's q has at most 24 significant bits: q and w' are exact floats
+        const dflt qd = marg ? df_from_u64(q) : dflt{float_of_q24(q), 0.0f};
+        if ((ax.x != 0.0f || ax.y != 0.0f) && q != 0) {
+          dflt wq;
+          if (marg)
+            wq = qweight_df(q, P.scale);
+          else
+            wq = dflt{p2 != 0.0f ? qd.hi * p2 : scalbnf(qd.hi, -P.scale), 0.0f};
+          dflt av, bv;
+          bin_terms(ax, wq.hi, wq.lo, &av, &bv);
+          sac = df_add(sac, df_mul(av, df_mul(Cd, invT)));
+          sx = df_add(sx, dflt{ax.y, 0.0f});
+        }
+        Cd = df_add(Cd, qd);
       }
-      Cd = df_add(Cd, qd);
+      contrib = df_add(sac, df_mul(K, sx));
     }
-    contrib = df_add(sac, df_mul(K, sx));
   }
   if (dlast != dfirst) {
     if (e0 < t1) atomicAdd(G + d, df_to_double(contrib));
