@@ -1085,17 +1085,20 @@ __global__ void __launch_bounds__(kForestThreads, RTF_FOREST_MINB) forest_kernel
 }
 
 // ---------------------------------------------------------------------------
-// forest of one distribution: the same links on a register-resident tile
+// forest of a tile inside one distribution
 // ---------------------------------------------------------------------------
-// Results identical to forest_kernel<false>.  Warp w owns the 128 consecutive
-// leaves [128 w, 128 w + 128) of the tile and lane l the leaves
-// 128 w + 32 k + l (k = 0..3): each k is one coalesced access to 32
-// consecutive weights, distance bytes or records, the exact prefix sum runs on
-// warp shuffles with one block-wide combine, a leaf's right-hand neighbour key
-// comes by shuffle, and the ballots of one k are the bit planes of 32
-// consecutive split positions.  Chunk c = 4 w + k holds positions
-// 32 c + 1 .. 32 c + 32, the right-hand splits of the chunk's leaves; position 0
-// (delta_{t0-1}) lies in no chunk.
+// The same links as forest_kernel, for a tile whose leaves all belong to one
+// distribution (every tile of a one-distribution build, most tiles of a
+// batch).  Warp w owns the 128 consecutive leaves [128 w, 128 w + 128) of the
+// tile.  The weights, the prefix sums, the keys and the distances are blocked:
+// thread i holds leaves 4 i .. 4 i + 3 (one 16-byte load of weights, one warp
+// scan of the thread totals and one block-wide combine, one 4-byte store of
+// distances).  The masks, the links and the records are lane-strided: lane l
+// holds leaves 128 w + 32 k + l (k = 0..3), so that the ballots of one k are
+// the bit planes of 32 consecutive split positions and each k writes 32
+// consecutive records.  Chunk c = 4 w + k holds positions 32 c + 1 .. 32 c + 32,
+// the right-hand splits of the chunk's leaves; position 0 (delta_{t0-1}) lies
+// in no chunk.
 struct LeanShared {
   // C_{t0-1} .. C_{t1} at Cbuf[1 .. tn + 2] (the CDF of tile-local leaf l at
   // index l + 2, so that each thread's four values form two aligned 16-byte
