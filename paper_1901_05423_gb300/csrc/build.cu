@@ -349,8 +349,54 @@ __global__ void __launch_bounds__(kScanThreads)
     return;
   }
 
+  {
+    // a tile inside one distribution (most tiles of a batch of large
+    // distributions): only its total, from 16-byte loads of the weights; a
+    // head can only be at t0 and an end only at t1
+    const int d0 = ts.dist0[tile];  // written by init_dists_kernel
+    const rtf_dist& P = dists[d0];
+    const int64_t pend = P.elem_off + P.n;
+    if (P.elem_off <= t0 && t1 <= pend) {
+      const int S = dist_scale(P, dmax, d0, n_shared);
+      const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
+      float wv[kScanPer];
+      if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+#pragma unroll
+        for (int h = 0; h < kScanPer / 4; ++h) {
+          const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
+          wv[4 * h] = x.x;
+          wv[4 * h + 1] = x.y;
+          wv[4 * h + 2] = x.z;
+          wv[4 * h + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < t1 ? w[e0 + k] : 0.0f;
+      }
+      uint64_t run = 0;
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) {
+        const uint32_t b = weight_bits(wv[k]);
+        if (e0 + k < t1 && !weight_bad(b)) run += quantize_bits(b, S);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xffffffffu, run, o);
+      if ((threadIdx.x & 31) == 0) wtot[threadIdx.x >> 5].s = run;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint64_t tot = 0;
+        for (int k = 0; k < kScanThreads / 32; ++k) tot += wtot[k].s;
+        const bool head0 = P.elem_off == t0, ends = t1 == pend;
+        ts.sum[tile] = tot;
+        ts.meta[tile] = (head0 ? 3u : 0u) | (ends && !head0 ? 4u : 0u);
+        if (ends && head0) finish_dist(dists, d0, tot, S, status);
+        if (ends && !head0) ts.first[tile] = tot;
+      }
+      return;
+    }
+  }
   if (threadIdx.x == 0) {
-    dfirst_s = ts.dist0[tile];  // written by init_dists_kernel
+    dfirst_s = ts.dist0[tile];
     meta_s = 0;
   }
   const int wo = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
