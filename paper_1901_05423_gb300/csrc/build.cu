@@ -108,7 +108,19 @@ __global__ void __launch_bounds__(kScaleThreads)
   const int64_t c1 = min(c0 + (int64_t)kScaleTile, Nw);
   const int64_t e0 = c0 + (int64_t)threadIdx.x * kScalePer;
   uint32_t bad = 0;
-  if (!SEG) {
+  // one maximum for the whole block: one distribution (or one shared group),
+  // or a block of a batch whose weights all belong to one distribution
+  bool one = !SEG;
+  uint32_t* target = dmax;
+  if (SEG) {
+    const int d0 = tile_dist0[c0 / kTile];
+    const rtf_dist& P = dists[d0];
+    if (P.elem_off <= c0 && c1 <= P.elem_off + P.n) {
+      one = true;
+      target = dmax + d0;
+    }
+  }
+  if (one) {
     uint32_t mx = 0;
     if (e0 + kScalePer <= c1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
       const float4* p = reinterpret_cast<const float4*>(w + e0);
@@ -135,7 +147,7 @@ __global__ void __launch_bounds__(kScaleThreads)
     if (threadIdx.x < 32) {
       uint32_t v = threadIdx.x < kScaleThreads / 32 ? red[threadIdx.x] : 0u;
       v = __reduce_max_sync(0xffffffffu, v);
-      if (threadIdx.x == 0 && v) atomicMax(dmax, v);
+      if (threadIdx.x == 0 && v) atomicMax(target, v);
     }
     if (bad) raise_status(status, RTF_STATUS_BAD_WEIGHT);
     return;
