@@ -49,8 +49,8 @@ LAUNCHES_PER_STEP_ACC = 6 + 1 + 8 + 8 + 2
 # is reported as null until the capture is repeated.
 TRAFFIC_CAPTURES = {
     "sample_iid": {
-        "bytes_per_unit": (37.956e9 + 2.143e9) / (1 << 28),
-        "sources": {"paper_1901_05423_gb300/csrc/sample.cu": "6550e65c35a91f1c",
+        "bytes_per_unit": (37.960e9 + 2.144e9) / (1 << 28),
+        "sources": {"paper_1901_05423_gb300/csrc/sample.cu": "cadb9701cb6d872d",
                     "paper_1901_05423_gb300/csrc/sample_common.cuh": "7836d4584a4ff2cf"},
     },
 }
