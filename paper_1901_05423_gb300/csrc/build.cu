@@ -364,27 +364,29 @@ __global__ void __launch_bounds__(kScanThreads)
   {
     // a tile inside one distribution (most tiles of a batch of large
     // distributions): only its total, from 16-byte loads of the weights; a
-    // head can only be at t0 and an end only at t1
+    // head can only be at t0 and an end only at t1.  The weights are loaded
+    // before the distribution's parameters are looked up, so that the two
+    // latencies overlap.
+    const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
+    float wv[kScanPer];
+    if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+#pragma unroll
+      for (int h = 0; h < kScanPer / 4; ++h) {
+        const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
+        wv[4 * h] = x.x;
+        wv[4 * h + 1] = x.y;
+        wv[4 * h + 2] = x.z;
+        wv[4 * h + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < t1 ? w[e0 + k] : 0.0f;
+    }
     const int d0 = ts.dist0[tile];  // written by init_dists_kernel
     const rtf_dist& P = dists[d0];
     const int64_t pend = P.elem_off + P.n;
     if (P.elem_off <= t0 && t1 <= pend) {
       const int S = dist_scale(P, dmax, d0, n_shared);
-      const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
-      float wv[kScanPer];
-      if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
-#pragma unroll
-        for (int h = 0; h < kScanPer / 4; ++h) {
-          const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
-          wv[4 * h] = x.x;
-          wv[4 * h + 1] = x.y;
-          wv[4 * h + 2] = x.z;
-          wv[4 * h + 3] = x.w;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < t1 ? w[e0 + k] : 0.0f;
-      }
       uint64_t run = 0;
 #pragma unroll
       for (int k = 0; k < kScanPer; ++k) {
