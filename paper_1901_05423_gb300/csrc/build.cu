@@ -6,7 +6,7 @@
 //   init_dists_kernel   per-distribution parameters from the plan
 //   scale_kernel        validation and max exponent (one read of w)
 //   tile_sum_kernel     segmented sums of the integer weights per tile (second
-//                       read of w, staged by a bulk copy); totals of the
+//                       read of w, 16-byte loads); totals of the
 //                       distributions that lie inside one tile
 //   tile_scan_kernel    decoupled-lookback segmented scan of the tile sums:
 //                       the prefix of every tile, the totals T (and key
@@ -246,7 +246,7 @@ struct TileSums {
   int32_t* dist0;    // distribution of t0
 };
 
-// Tile sums of q (second read of w, staged by a bulk copy).  Distributions that
+// Tile sums of q (second read of w, 16-byte loads).  Distributions that
 // begin and end inside the tile are finished here; the tile's first piece,
 // whose distribution began in an earlier tile, waits for the scan of the tile
 // sums.
@@ -255,9 +255,6 @@ __global__ void __launch_bounds__(kScanThreads)
     tile_sum_kernel(const float* __restrict__ w, int64_t Nw, rtf_dist* dists, int Dw,
                     int64_t n_shared, const uint32_t* dmax, TileSums ts, uint64_t* tile_prefix,
                     Counters* ctr, uint32_t* status) {
-  __shared__ alignas(16) float wsm[kTile + 4];
-  __shared__ uint64_t bar;
-  __shared__ int ok_s;
   __shared__ int dfirst_s;
   __shared__ SegPair wtot[kScanThreads / 32];
   __shared__ SegPair btot;
@@ -361,27 +358,27 @@ __global__ void __launch_bounds__(kScanThreads)
     return;
   }
 
+  // the thread's run of kScanPer consecutive weights, loaded before the
+  // tile's distribution is looked up, so that the two latencies overlap
+  const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
+  float wv[kScanPer];
+  if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+#pragma unroll
+    for (int h = 0; h < kScanPer / 4; ++h) {
+      const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
+      wv[4 * h] = x.x;
+      wv[4 * h + 1] = x.y;
+      wv[4 * h + 2] = x.z;
+      wv[4 * h + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < t1 ? w[e0 + k] : 0.0f;
+  }
   {
     // a tile inside one distribution (most tiles of a batch of large
-    // distributions): only its total, from 16-byte loads of the weights; a
-    // head can only be at t0 and an end only at t1.  The weights are loaded
-    // before the distribution's parameters are looked up, so that the two
-    // latencies overlap.
-    const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
-    float wv[kScanPer];
-    if (e0 + kScanPer <= t1 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
-#pragma unroll
-      for (int h = 0; h < kScanPer / 4; ++h) {
-        const float4 x = ld_weights4(reinterpret_cast<const float4*>(w + e0) + h);
-        wv[4 * h] = x.x;
-        wv[4 * h + 1] = x.y;
-        wv[4 * h + 2] = x.z;
-        wv[4 * h + 3] = x.w;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < kScanPer; ++k) wv[k] = e0 + k < t1 ? w[e0 + k] : 0.0f;
-    }
+    // distributions): only its total; a head can only be at t0 and an end
+    // only at t1
     const int d0 = ts.dist0[tile];  // written by init_dists_kernel
     const rtf_dist& P = dists[d0];
     const int64_t pend = P.elem_off + P.n;
@@ -413,11 +410,9 @@ __global__ void __launch_bounds__(kScanThreads)
     dfirst_s = ts.dist0[tile];
     meta_s = 0;
   }
-  const int wo = stage_weights(wsm, w, t0, t1, &bar, &ok_s, status);
+  __syncthreads();
   const int dfirst = dfirst_s;
 
-  // per-thread run of kScanPer consecutive weights
-  const int64_t e0 = t0 + (int64_t)threadIdx.x * kScanPer;
   uint64_t incl[kScanPer];
   int dk[kScanPer];
   uint32_t headmask = 0;
@@ -454,7 +449,7 @@ __global__ void __launch_bounds__(kScanThreads)
           headmask |= 1u << k;
           run = 0;
         }
-        const uint32_t b = weight_bits(wsm[wo + (e - t0)]);
+        const uint32_t b = weight_bits(wv[k]);
         q = weight_bad(b) ? 0ull : quantize_bits(b, S);
         if (e + 1 == min(next, Nw)) lastmask |= 1u << k;
       }

@@ -2,8 +2,7 @@
 //
 // Exact integer arithmetic of the fixed-point reading of the paper's CDF
 // (Sec. 1), the keys of Algorithm 1 (Sec. 3.2) in the 32-bit sample domain,
-// bulk-copy (TMA) staging of weight tiles into shared memory with bounded
-// mbarrier waits, and a few warp/block scan primitives.
+// the bounded lookback waits, and a few warp/block scan primitives.
 #pragma once
 
 #include <cstdint>
@@ -254,87 +253,6 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// ---------------------------------------------------------------------------
-// bulk copy (TMA, non-tensor) global -> shared with an mbarrier
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-      "[%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Bounded wait for phase `parity` of the barrier; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// Stage w[t0, t1) into shared memory `dst` (kTile + 4 floats): the 16-byte
-// aligned middle by one bulk copy, the (at most 3 + 3) weights before and
-// after it by plain loads.  Weight t0 + j lands at dst[o + j] for the returned
-// offset o in 0..3, which puts the bulk copy on a 16-byte boundary in shared
-// memory as well.  Called by all threads.  If the copy does not complete
-// within the bounded wait, RTF_STATUS_TIMEOUT is raised (after a second
-// bounded wait for the copy in flight) and *flag is 0.
-__device__ inline int stage_weights(float* dst, const float* w, int64_t t0, int64_t t1,
-                                    uint64_t* bar, int* flag, uint32_t* status) {
-  const float* src = w + t0;
-  const int cnt = (int)(t1 - t0);
-  const int mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
-  const int head = min((4 - mis) & 3, cnt);
-  const int body = (cnt - head) & ~3;
-  const int o = mis;
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    if (body > 0) {
-      mbar_arrive_expect_tx(bar, (uint32_t)body * 4u);
-      bulk_g2s(dst + o + head, src + head, (uint32_t)body * 4u, bar);
-    }
-  }
-  for (int k = (int)threadIdx.x; k < head; k += blockDim.x) dst[o + k] = src[k];
-  for (int k = head + body + (int)threadIdx.x; k < cnt; k += blockDim.x) dst[o + k] = src[k];
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (body > 0 && !mbar_wait(bar, 0)) {
-      raise_status(status, RTF_STATUS_TIMEOUT);
-      mbar_wait(bar, 0);
-      ok = 0;
-    }
-    *flag = ok;
-  }
-  __syncthreads();
-  return o;
 }
 
 // ---------------------------------------------------------------------------
