@@ -1164,13 +1164,11 @@ struct LeanShared {
   // distance at position p at dbuf[p + 3] (each thread's four distances form
   // one aligned 4-byte store); read through d = dbuf + 3
   alignas(4) uint8_t dbuf[kTile + 12];
-  // per chunk: gtm[c][t] = positions with a distance > t, for t up to the
-  // chunk's largest finite distance fmax[c]; above it only the boundaries
-  // (infinite distance, mask infm[c]) are larger
+  // per chunk: gtm[c][t] = positions with a distance > t (t = 0..31; above
+  // the chunk's largest finite distance only the boundaries, infm[c])
   uint32_t gtm[kChunks][32];
   uint32_t valid[kChunks];
   uint32_t infm[kChunks];
-  int32_t fmax[kChunks];
   uint32_t cmax[kChunks];
   uint64_t wtot[kForestThreads / 32];
   uint64_t Kfirst[kForestThreads / 32 + 1];  // key of each warp's first leaf; [16]: of leaf t1
@@ -1198,7 +1196,7 @@ __device__ __forceinline__ uint64_t shfl_idx64(uint64_t x, int l) {
 
 // Positions of chunk c with a distance > v (v below kDeltaInf).
 __device__ __forceinline__ uint32_t chunk_gt(const LeanShared& s, int c, uint32_t v) {
-  return ((int)v <= s.fmax[c] && v < 32) ? s.gtm[c][v] : s.infm[c];
+  return v < 32 ? s.gtm[c][v] : s.infm[c];
 }
 
 // ... with a distance >= v.
@@ -1370,22 +1368,23 @@ __device__ __forceinline__ void lean_tile(const ForestArgs& a, LeanShared& s, co
     const uint32_t vm = __ballot_sync(0xffffffffu, l < tn);
     const uint32_t inf = __ballot_sync(0xffffffffu, l < tn && dlt >= kDeltaInf);
     const int fm = (int)__reduce_max_sync(0xffffffffu, (l < tn && dlt < kDeltaInf) ? dlt + 1 : 0u) - 1;
+    uint32_t g = inf;  // no finite distance: only the boundaries exceed any t
     if (fm >= 0) {
       uint32_t pl[6];
 #pragma unroll
       for (int b = 0; b < 6; ++b) pl[b] = __ballot_sync(0xffffffffu, (v >> b) & 1u);
-      uint32_t g = pl[5], e = vm & ~pl[5];
+      uint32_t e = vm & ~pl[5];
+      g = pl[5];
 #pragma unroll
       for (int b = 4; b >= 0; --b) {
         g |= e & pl[b] & ~lt_mask[b];
         e &= ~(pl[b] ^ lt_mask[b]);
       }
-      if (lane <= fm) s.gtm[c][lane] = g;
     }
+    s.gtm[c][lane] = g;
     if (lane == 0) {
       s.valid[c] = vm;
       s.infm[c] = inf;
-      s.fmax[c] = fm;
       s.cmax[c] = inf ? kDeltaTop : (uint32_t)max(fm, 0);
     }
   }
