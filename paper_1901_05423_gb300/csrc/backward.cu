@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(kBwThreads)
 // piece; a block inside one distribution reduces first and adds once).
 __global__ void __launch_bounds__(kBwThreads)
     bin_total_kernel(const float2* __restrict__ acc, const rtf_node* __restrict__ nodes,
-                     const rtf_dist* __restrict__ dists, int D, int64_t N, double* G) {
+                     const float* __restrict__ w, const rtf_dist* __restrict__ dists, int D,
+                     int64_t N, double* G) {
   __shared__ int dfirst_s, dlast_s;
   __shared__ double part[kBwThreads / 32];
   __shared__ dflt invT_s, K_s;
@@ -375,22 +376,34 @@ __global__ void __launch_bounds__(kBwThreads)
     dflt sac = df_zero(), sx = df_zero();
     if (dlast == dfirst && e0 + kBwPer <= t1 && !marg) {
       // the usual case, a whole run inside one distribution of float
-      // weights: every load of the run issued first (the bound C_{e0+kBwPer}
-      // is T past the distribution's end)
-      uint64_t c[kBwPer + 1];
+      // weights: every load of the run issued first; the quantised weights
+      // w' = q 2^-S come from the weights (4 bytes each, instead of the CDF
+      // differences from the 16-byte node records), C only at the run's start
+      const uint64_t c0 = nodes[e0].cdf;
+      float wv[kBwPer];
+      if ((reinterpret_cast<uintptr_t>(w + e0) & 15) == 0) {
 #pragma unroll
-      for (int k = 0; k < kBwPer; ++k) c[k] = nodes[e0 + k].cdf;
-      c[kBwPer] = e0 + kBwPer < end ? nodes[e0 + kBwPer].cdf : P.total;
+        for (int h = 0; h < kBwPer / 4; ++h) {
+          const float4 x = reinterpret_cast<const float4*>(w + e0)[h];
+          wv[4 * h] = x.x;
+          wv[4 * h + 1] = x.y;
+          wv[4 * h + 2] = x.z;
+          wv[4 * h + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kBwPer; ++k) wv[k] = w[e0 + k];
+      }
       float2 ax[kBwPer];
 #pragma unroll
       for (int k = 0; k < kBwPer; ++k) ax[k] = acc[e0 + k];
-      dflt Cd = df_from_u64(c[0]);
+      const float pS = pow2_neg(-P.scale);  // 2^S, or 0 outside the float exponent range
+      dflt Cd = df_from_u64(c0);
 #pragma unroll
       for (int k = 0; k < kBwPer; ++k) {
-        const uint64_t q = c[k + 1] - c[k];
-        const float qf = float_of_q24(q);
-        if ((ax[k].x != 0.0f || ax[k].y != 0.0f) && q != 0) {
-          const float wq = p2 != 0.0f ? qf * p2 : scalbnf(qf, -P.scale);
+        const float wq = quantized_weight(wv[k], P.scale);
+        const float qf = pS != 0.0f ? wq * pS : scalbnf(wq, P.scale);  // q, exact
+        if ((ax[k].x != 0.0f || ax[k].y != 0.0f) && wq != 0.0f) {
           dflt av, bv;
           bin_terms(ax[k], wq, 0.0f, &av, &bv);
           sac = df_add(sac, df_mul(av, df_mul(Cd, invT)));
@@ -879,7 +892,8 @@ cudaError_t launch_backward_finish(const rtf_forest* f, const float* w, int mode
         f->dists, D - 1, R);
   }
   const int64_t tiles = (N + kBwTile - 1) / kBwTile;
-  bin_total_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, f->nodes, f->dists, D, N, G);
+  bin_total_kernel<<<(unsigned)tiles, kBwThreads, 0, st>>>(p.acc, f->nodes, w, f->dists, D, N,
+                                                          G);
   const bool vec_ok = (reinterpret_cast<uintptr_t>(w) & 15) == 0 &&
                       (reinterpret_cast<uintptr_t>(grad_w) & 15) == 0;
   if (D == 1 && !two_d && vec_ok)
