@@ -357,6 +357,35 @@ def test_batched_small_ragged():
     batched_check(w, offsets, ms)
 
 
+def test_batched_tile_aligned_boundaries():
+    """Distribution boundaries on tile edges (2048 weights) and next to them,
+    distributions of exactly one or several tiles, hundreds of one-to-three
+    weight distributions inside one tile, leading and trailing zero weights:
+    the cases of the single-distribution paths of the batched scale, tile-sum
+    and forest passes (a head only at t0, an end only at t1) and of the table
+    of each tile's first distribution; every structure against the oracle."""
+    rng = np.random.default_rng(11)
+    sizes = [2048, 2048, 4096, 1, 2047, 2049, 6144, 3, 2045, 4096 + 2048]
+    sizes += list(rng.integers(1, 4, 400))
+    cum = int(np.sum(sizes))
+    sizes.append(2048 - cum % 2048 + 2048)  # realign the next boundary on a tile edge
+    sizes += [2048, 1, 1, 2046, 8192, 2049, 2047]
+    sizes = np.array(sizes, np.int64)
+    parts = []
+    for i, n in enumerate(sizes):
+        x = W.lognormal_weights(int(n), seed=200 + i, sigma=1.5)
+        if n > 8 and i % 3 == 0:
+            x[:2] = 0.0  # leading zero-width bins
+        if n > 8 and i % 3 == 1:
+            x[-3:] = 0.0  # trailing zero-width bins (keys equal to 2^32)
+        parts.append(x)
+    w = np.concatenate(parts).astype(np.float32)
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    assert (offsets % 2048 == 0).sum() >= 8
+    ms = np.clip(np.round(np.log2(sizes)).astype(int) + rng.integers(-2, 3, sizes.size), 0, 14)
+    batched_check(w, offsets, ms)
+
+
 def test_batched_ragged_full_config():
     """The ragged workload in full: 16384 distributions, sizes log-uniform in
     [8, 65536], lognormal(0, 1.5), the autotuned guide bits the benchmark
