@@ -1304,13 +1304,13 @@ __device__ __forceinline__ void lean_tile(const ForestArgs& a, LeanShared& s, co
       }
     }
   }
-  if (lane == 0) s.Kfirst[warp] = K[0];
+  if (ONE && lane == 0) s.Kfirst[warp] = K[0];
   if (tid == 0) {
     uint64_t tt = 0;
     for (int k = 0; k < kForestThreads / 32; ++k) tt += s.wtot[k];
     const uint64_t Ct1 = s.prefix + tt;
     sC[tn + 1] = Ct1;
-    s.Kfirst[kForestThreads / 32] = key_of(Ct1, T, R, z);
+    if (ONE) s.Kfirst[kForestThreads / 32] = key_of(Ct1, T, R, z);
     uint64_t Cp = 0;
     if (t0 > eoff) {
       const uint32_t b = weight_bits(a.w[t0 - 1]);
@@ -1319,13 +1319,20 @@ __device__ __forceinline__ void lean_tile(const ForestArgs& a, LeanShared& s, co
     sC[0] = Cp;
     s.Kprev = key_of(Cp, T, R, z);
   }
-  __syncthreads();
+  // The key of leaf lb + 4 is the next lane's first key; for lane 31 it is the
+  // next warp's first key, passed through shared memory across a barrier
+  // (ONE), or, in a tile of a batch, the key of the thread's own running sum
+  // past its four leaves (the C of the next warp's first leaf, C_{t1} for the
+  // last warp), which saves the barrier (measured: faster for the batches,
+  // whose tiles hold more cells; slower for one distribution, where the kept
+  // sums spill under the three-block register cap).
+  if (ONE) __syncthreads();
 
   // ---- distances (blocked: positions lb + 1 .. lb + 4, one 4-byte store) ----
   uint32_t dmx = 0;
   {
-    const uint64_t below = shfl_down64(K[0], 1);  // key of leaf lb + 4 (lanes 0..30)
-    const uint64_t K4 = lane < 31 ? below : s.Kfirst[warp + 1];
+    uint64_t K4 = shfl_down64(K[0], 1);
+    if (lane == 31) K4 = ONE ? s.Kfirst[warp + 1] : key_of(pre + tot, T, R, z);
     uint32_t packed = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
