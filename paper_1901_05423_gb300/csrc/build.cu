@@ -3,24 +3,31 @@
 // Sec. 3.2) for one or many distributions at once (Sec. 5).
 //
 // Kernels, in launch order:
-//   init_dists_kernel   per-distribution parameters from the plan
+//   init_dists_kernel   per-distribution parameters from the plan; for a
+//                       batch also the distribution of each tile's first
+//                       element
 //   scale_kernel        validation and max exponent (one read of w)
-//   tile_sum_kernel     segmented sums of the integer weights per tile (second
-//                       read of w, 16-byte loads); totals of the
-//                       distributions that lie inside one tile
-//   tile_scan_kernel    decoupled-lookback segmented scan of the tile sums:
-//                       the prefix of every tile, the totals T (and key
+//   tile_sum_kernel     sums of the integer weights per tile (second read of
+//                       w): for one distribution persistent blocks over
+//                       ranges of tiles, the last one scanning the range
+//                       totals; for a batch segmented sums, and the totals of
+//                       the distributions that lie inside one tile
+//   tile_scan_kernel    (batch) decoupled-lookback segmented scan of the tile
+//                       sums: the prefix of every tile, the totals T (and key
 //                       reciprocals) of the distributions that cross tiles; in
 //                       marginal mode the last block also scans the row totals
-//   forest_kernel       C_j, keys K_j, distances, Algorithm 1 inside each tile
-//                       in shared memory; node records, roots, guide entries
-//                       of non-empty cells; the tile's slice of the global
-//                       otherBounds (third read of w)
-//   forest_merge_kernel the hand-offs across tile edges: Algorithm 1 continued
-//                       through the global otherBounds
-//   guide_kernel        guide entries of cells that no key falls into: the
-//                       interval of the last key before them (carry-forward
-//                       scan with a decoupled lookback)
+//   forest_lean_kernel  (one distribution) and forest_kernel (batch): per
+//                       2048-leaf tile C_j, keys K_j, distances, the links from
+//                       the nearest larger distances, node records, the roots
+//                       and guide entries of the cells that end inside the
+//                       tile and of up to 16 empty cells after each (third
+//                       read of w); forest_kernel sends a tile that lies
+//                       inside one distribution down the same path as
+//                       forest_lean_kernel
+//   forest_merge_kernel the nodes whose bounding splits lie outside their tile,
+//                       found in the global distance bytes with the largest
+//                       distance per tile and per group of tiles
+//   fill_kernel         the longer runs of cells that no key falls into
 #include <algorithm>
 #include <cstdint>
 

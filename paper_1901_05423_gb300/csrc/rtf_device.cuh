@@ -373,8 +373,7 @@ __device__ inline uint32_t block_exclusive_u32(uint32_t x, uint32_t* warp_tot, u
 // per round, so one round covers blockDim tiles.  Returns, to every thread,
 // the sum of the values from tile-1 back to and including the nearest tile
 // that published a prefix (`sum` = true), or that prefix's value alone
-// (`sum` = false: the carry-forward scans, where an aggregate carries no
-// value).  Waits are bounded; on expiry RTF_STATUS_TIMEOUT is raised and the
+// (`sum` = false).  Waits are bounded; on expiry RTF_STATUS_TIMEOUT is raised and the
 // partial result returned.
 struct LookbackShared {
   int first_prefix;
